@@ -1,0 +1,344 @@
+"""Pins for the CPU oracle against what the paper and the mathematics fix.
+
+Each pin is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign, a transposed operand, a wrong index set) fails it:
+  * restriction sets against the grid topology, computed here independently
+  * X~ = A^{-1} B, G~ = -C A^{-1} and S~ = S when Q^(m) covers every face
+    (Eq. dec_fac, Eq. schur_compl, dense brute force)
+  * Galerkin orthogonality and energy minimality of the restricted solve
+    (Proposition min_energy)
+  * own-face solves with diagonal K: three independent 2x2 systems (Cramer)
+  * ILU(0) = exact LU when the pattern has no fill (tridiagonal / dense)
+  * exact blocks => FGMRES converges in 1 iteration (Eq. inv_A_fac), <= 2 with
+    the block upper-triangular variant; identity preconditioner => the dense solution
+  * the dynamic technique adds exactly the largest prolonged-residual entries
+    (Eq. prol_res), recomputed here with dense algebra
+  * the two-sided S~ built on the transposed system is S~^T (F/G role swap)
+  * adjoint gradient against central finite differences of dense solves
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+import workloads as W
+
+
+def full_tensor(n=(3, 3, 2), seed=11, **kw):
+    s = W.Stream(seed)
+    Ne = int(np.prod(n))
+    m = np.exp(s.normal(Ne))
+    q = s.normal(4 * Ne).reshape(Ne, 4)
+    return W.assemble(*n, W.rotated_K(m, 0.1, q), **kw)
+
+
+def iso(n=(3, 3, 2), seed=5, sigma=1.0, **kw):
+    Ne = int(np.prod(n))
+    return W.assemble(*n, W.iso_K(np.exp(sigma * W.Stream(seed).normal(Ne))), **kw)
+
+
+def all_faces_q(sysd):
+    Ne, Nf = sysd.Ne, sysd.Nf
+    qptr = np.arange(Ne + 1, dtype=np.int64) * Nf
+    qidx = np.tile(np.arange(Nf, dtype=np.int32), Ne)
+    return qptr, qidx
+
+
+def sets_of(qptr, qidx):
+    return [list(qidx[qptr[m]:qptr[m + 1]]) for m in range(len(qptr) - 1)]
+
+
+# ------------------------------------------------------------ restriction sets
+def topo_sets(sysd, mode):
+    """Restriction sets from the grid topology (cell -> faces, face -> cells)."""
+    out = []
+    live = ~sysd.face_dir  # prescribed faces carry no B entry
+    for m in range(sysd.Ne):
+        own = {f for f in sysd.cell_faces[m] if live[f]}
+        if mode == "own":
+            out.append(sorted(own))
+        elif mode == "nbr":
+            q = set(own)
+            for f in own:
+                for e2 in sysd.face_cells[f]:
+                    if e2 >= 0 and e2 != m:
+                        q |= {g for g in sysd.cell_faces[e2] if live[g]}
+            out.append(sorted(q))
+    return out
+
+
+@pytest.mark.parametrize("mode", ["own", "nbr"])
+def test_static_sets_match_topology(mode):
+    sysd = full_tensor((4, 3, 3))
+    qptr, qidx = O.qsets(mode, sysd.A, sysd.B, sysd.C)
+    assert sets_of(qptr, qidx) == topo_sets(sysd, mode)
+
+
+def test_nbr_sizes_interior():
+    sysd = iso((5, 5, 5))
+    qptr, _ = O.qsets("nbr", sysd.A, sysd.B, sysd.C)
+    s = np.diff(qptr)
+    centre = 2 + 5 * (2 + 5 * 2)
+    assert s[centre] == 36  # 6 own + 6 neighbours x 5 far faces
+
+
+def test_crow_and_thresh_sets():
+    sysd = iso((4, 4, 3))
+    qptr, qidx = O.qsets("crow", sysd.A, sysd.B, sysd.C)
+    Cd = sysd.C.dense()
+    assert sets_of(qptr, qidx) == [list(np.nonzero(Cd[m])[0]) for m in range(sysd.Ne)]
+    Ad = sysd.A.dense()
+    own = topo_sets(sysd, "own")
+    for thr in (0.0, 0.05, 0.4, 10.0):
+        qptr, qidx = O.qsets("thresh", sysd.A, sysd.B, sysd.C, thr)
+        ref = []
+        for m in range(sysd.Ne):
+            q = set(own[m])
+            for i in own[m]:
+                q |= {j for j in np.nonzero(Ad[i])[0] if abs(Ad[i, j]) >= thr * abs(Ad[i, i])}
+            ref.append(sorted(q))
+        assert sets_of(qptr, qidx) == ref
+    qptr, qidx = O.qsets("thresh", sysd.A, sysd.B, sysd.C, 10.0)
+    assert sets_of(qptr, qidx) == own
+
+
+# ------------------------------------------------------------ local solves
+@pytest.mark.parametrize("maker", [full_tensor, iso])
+def test_all_faces_restriction_is_exact(maker):
+    sysd = maker()
+    Ad, Bd, Cd, Dd = (M.dense() for M in (sysd.A, sysd.B, sysd.C, sysd.D))
+    qptr, qidx = all_faces_q(sysd)
+    x, g = O.local_solves(sysd.A, sysd.B, sysd.C, qptr, qidx, True, True)
+    X = x.reshape(sysd.Ne, sysd.Nf).T  # column m
+    G = g.reshape(sysd.Ne, sysd.Nf)    # row m
+    Xref = np.linalg.solve(Ad, Bd)
+    Gref = -Cd @ np.linalg.inv(Ad)
+    np.testing.assert_allclose(X, Xref, atol=1e-10 * np.abs(Xref).max())
+    np.testing.assert_allclose(G, Gref, atol=1e-10 * np.abs(Gref).max())
+    Sref = Dd - Cd @ Xref
+    for form in (0, 1):
+        S = O.schur(form, sysd.A, sysd.C, sysd.D, qptr, qidx, x, g).to_scipy().toarray()
+        np.testing.assert_allclose(S, Sref, atol=1e-10 * np.abs(Sref).max())
+
+
+def test_galerkin_orthogonality_and_energy_minimality():
+    # Proposition (min_energy): R (b - A R^T x) = 0 and x minimises ||A^{-1}b - R^T x||_{-A}
+    sysd = full_tensor((3, 3, 3))
+    Ad, Bd = sysd.A.dense(), sysd.B.dense()
+    qptr, qidx = O.qsets("nbr", sysd.A, sysd.B, sysd.C)
+    x, _ = O.local_solves(sysd.A, sysd.B, sysd.C, qptr, qidx)
+    rng = np.random.default_rng(1)
+    Mspd = -Ad
+    for m in range(sysd.Ne):
+        q = qidx[qptr[m]:qptr[m + 1]]
+        xt = np.zeros(sysd.Nf)
+        xt[q] = x[qptr[m]:qptr[m + 1]]
+        r = Bd[:, m] - Ad @ xt
+        assert np.abs(r[q]).max() <= 1e-12 * max(np.abs(r).max(), np.abs(Bd[:, m]).max())
+        ex = np.linalg.solve(Ad, Bd[:, m])
+        e0 = ex - xt
+        base = e0 @ Mspd @ e0
+        for _ in range(3):
+            d = np.zeros(sysd.Nf)
+            d[q] = rng.normal(size=q.size) * 1e-3 * np.abs(xt).max()
+            e1 = e0 - d
+            assert e1 @ Mspd @ e1 > base
+
+
+def test_own_faces_diagonal_K_closed_form():
+    # isotropic K, own faces: A^(m) splits into three 2x2 axis blocks
+    sysd = W.config1()
+    Ad = sysd.A.to_scipy().tolil()
+    Bd = sysd.B.to_scipy().tocsc()
+    qptr, qidx = O.qsets("own", sysd.A, sysd.B, sysd.C)
+    x, _ = O.local_solves(sysd.A, sysd.B, sysd.C, qptr, qidx)
+    for m in range(0, sysd.Ne, 7):
+        faces = list(sysd.cell_faces[m])
+        for a in range(3):
+            f0, f1 = faces[2 * a], faces[2 * a + 1]
+            live = [f for f in (f0, f1) if not sysd.face_dir[f]]
+            if len(live) == 2:
+                a11, a12, a22 = Ad[f0, f0], Ad[f0, f1], Ad[f1, f1]
+                b1, b2 = Bd[f0, m], Bd[f1, m]
+                det = a11 * a22 - a12 * a12
+                ref = {f0: (b1 * a22 - a12 * b2) / det, f1: (a11 * b2 - a12 * b1) / det}
+            else:
+                f = live[0]
+                ref = {f: Bd[f, m] / Ad[f, f]}
+            q = list(qidx[qptr[m]:qptr[m + 1]])
+            for f, v in ref.items():
+                assert x[qptr[m] + q.index(f)] == pytest.approx(v, rel=1e-12)
+
+
+# ------------------------------------------------------------ ILU(0)
+def dense_ilu0(M):
+    """Textbook ILU(0) on a dense array restricted to M's pattern (IKJ)."""
+    A = M.copy()
+    P = M != 0
+    n = A.shape[0]
+    for i in range(1, n):
+        for k in range(i):
+            if not P[i, k]:
+                continue
+            A[i, k] /= A[k, k]
+            for j in range(k + 1, n):
+                if P[i, j]:
+                    A[i, j] -= A[i, k] * A[k, j]
+    return A
+
+
+def test_ilu0_exact_when_no_fill():
+    n = 30
+    rng = np.random.default_rng(2)
+    T = sp.diags([rng.uniform(-1, 0, n - 1), rng.uniform(3, 4, n), rng.uniform(-1, 0, n - 1)],
+                 [-1, 0, 1], format="csr")
+    lu = O.ilu0(T)
+    r = rng.normal(size=n)
+    np.testing.assert_allclose(O.ilu0_solve(T, lu, r), np.linalg.solve(T.toarray(), r), rtol=1e-12)
+    Dn = rng.normal(size=(12, 12)) + 12 * np.eye(12)
+    Dm = O.Mat.of(sp.csr_matrix(Dn))
+    lu = O.ilu0(Dm)
+    np.testing.assert_allclose(O.ilu0_solve(Dm, lu, r[:12]), np.linalg.solve(Dn, r[:12]), rtol=1e-11)
+
+
+def test_ilu0_matches_textbook_on_sparse_pattern():
+    sysd = full_tensor((3, 2, 2))
+    M = sysd.A.to_scipy()
+    lu = O.ilu0(sysd.A)
+    ref = dense_ilu0(M.toarray())
+    got = sp.csr_matrix((lu, sysd.A.col, sysd.A.rowptr), shape=M.shape).toarray()
+    mask = M.toarray() != 0
+    np.testing.assert_allclose(got[mask], ref[mask], rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------------------ apply + FGMRES
+def dense_mat(a):
+    """CSR with every entry stored: ILU(0) on it is the exact LU factorisation."""
+    n = a.shape[0]
+    return O.Mat(n, a.shape[1], np.arange(n + 1) * a.shape[1], np.tile(np.arange(a.shape[1]), n), a.ravel())
+
+
+@pytest.mark.parametrize("maker", [full_tensor, iso])
+def test_exact_blocks_converge_in_one_iteration(maker):
+    sysd = maker()
+    Ad, Bd, Cd, Dd = (M.dense() for M in (sysd.A, sysd.B, sysd.C, sysd.D))
+    S = Dd - Cd @ np.linalg.solve(Ad, Bd)
+    b = W.Stream(3).normal(sysd.n)
+    P = O.Prec(sysd.A, sysd.B, sysd.C, sysd.D, S=dense_mat(S), Ma=dense_mat(Ad), variant=0)
+    r = O.fgmres(P, b, 50, 1e-10, 20)
+    assert r["converged"] and r["iters"] == 1
+    P2 = O.Prec(sysd.A, sysd.B, sysd.C, sysd.D, S=dense_mat(S), Ma=dense_mat(Ad), variant=1)
+    r2 = O.fgmres(P2, b, 50, 1e-10, 20)
+    assert r2["converged"] and r2["iters"] <= 2
+    xd = np.linalg.solve(sysd.full_scipy().toarray(), b)
+    np.testing.assert_allclose(r["x"], xd, atol=1e-8 * np.abs(xd).max())
+
+
+def test_apply_matches_block_ldu_inverse():
+    # Eq. (EDFA_prec) with exact blocks equals the inverse of the block system (Eq. inv_A_fac)
+    sysd = full_tensor((2, 2, 2))
+    Ad, Bd, Cd, Dd = (M.dense() for M in (sysd.A, sysd.B, sysd.C, sysd.D))
+    S = Dd - Cd @ np.linalg.solve(Ad, Bd)
+    P = O.Prec(sysd.A, sysd.B, sysd.C, sysd.D, S=dense_mat(S), Ma=dense_mat(Ad))
+    Minv = np.linalg.inv(sysd.full_scipy().toarray())
+    for k in range(3):
+        r = W.Stream(10 + k).normal(sysd.n)
+        np.testing.assert_allclose(P.apply(r), Minv @ r, atol=1e-9 * np.abs(Minv @ r).max())
+
+
+def test_identity_preconditioner_is_gmres():
+    sysd = iso((3, 2, 2))
+    b = W.Stream(4).normal(sysd.n)
+    P = O.Prec(sysd.A, sysd.B, sysd.C, sysd.D, identity=True)
+    r = O.fgmres(P, b, 200, 1e-11, 400)
+    assert r["converged"]
+    xd = np.linalg.solve(sysd.full_scipy().toarray(), b)
+    np.testing.assert_allclose(r["x"], xd, atol=1e-8 * np.abs(xd).max())
+    assert np.all(np.diff(r["hist"]) <= 1e-14)  # GMRES residual is non-increasing within a cycle
+
+
+def test_edfa_pipeline_converges_and_bigger_sets_help():
+    # qualitative behaviour of Sec. 4: a larger restriction set gives fewer iterations
+    sysd = full_tensor((6, 6, 6))
+    it = {}
+    for mode in ("own", "nbr"):
+        r = O.edfa_pipeline(sysd, mode=mode, rtol=1e-8, maxit=600)
+        assert r["converged"] and r["true_rel"] <= 1e-8
+        it[mode] = r["iters"]
+    assert it["nbr"] < it["own"]
+
+
+# ------------------------------------------------------------ dynamic technique
+def test_dynamic_first_step_adds_largest_residual_entries():
+    sysd = full_tensor((3, 3, 3), seed=21)
+    Ad, Cd = sysd.A.dense(), sysd.C.dense()
+    for n_add in (1, 3):
+        qptr, qidx = O.qsets_dynamic(sysd.A, sysd.C, n_add, n_add, 1)
+        for m in range(sysd.Ne):
+            q0 = list(np.nonzero(Cd[m])[0])
+            M = -Ad[np.ix_(q0, q0)]
+            g = np.linalg.solve(M, Cd[m, q0])
+            r = Cd[m].copy()
+            r += Ad[:, q0] @ g  # prolonged residual, Eq. (prol_res)
+            cand = [j for j in range(sysd.Nf) if j not in q0 and np.any(Ad[j, q0] != 0)]
+            order = sorted(cand, key=lambda j: (-abs(r[j]), j))
+            ref = sorted(q0 + order[:n_add])
+            assert list(qidx[qptr[m]:qptr[m + 1]]) == ref
+    qptr0, qidx0 = O.qsets_dynamic(sysd.A, sysd.C, 2, 0, 5)
+    qptr1, qidx1 = O.qsets("crow", sysd.A, sysd.B, sysd.C)
+    assert np.array_equal(qptr0, qptr1) and np.array_equal(qidx0, qidx1)
+
+
+def test_dynamic_growth_bounds():
+    sysd = full_tensor((3, 3, 2), seed=22)
+    base, _ = O.qsets("crow", sysd.A, sysd.B, sysd.C)
+    for n_add, n_ent, it_max in ((2, 6, 10), (4, 6, 1), (1, 5, 3)):
+        qptr, qidx = O.qsets_dynamic(sysd.A, sysd.C, n_add, n_ent, it_max)
+        grown = np.diff(qptr) - np.diff(base)
+        assert grown.max() <= min(n_ent, n_add * it_max)
+        assert grown.min() >= 0
+
+
+# ------------------------------------------------------------ transpose / adjoint
+def test_two_sided_schur_of_transposed_system_is_transpose():
+    # On [A C^T; B^T D^T] the roles of F~ and G~ swap; with the same Q^(m) the
+    # two-sided S~ is the transpose of the original one.
+    sysd = full_tensor((3, 3, 2))
+    qptr, qidx = O.qsets("nbr", sysd.A, sysd.B, sysd.C)
+    x, g = O.local_solves(sysd.A, sysd.B, sysd.C, qptr, qidx, True, True)
+    S = O.schur(1, sysd.A, sysd.C, sysd.D, qptr, qidx, x, g).to_scipy().toarray()
+    Bt = O.Mat.of(sysd.C.to_scipy().T.tocsr())
+    Ct = O.Mat.of(sysd.B.to_scipy().T.tocsr())
+    Dt = O.Mat.of(sysd.D.to_scipy().T.tocsr())
+    xt, gt = O.local_solves(sysd.A, Bt, Ct, qptr, qidx, True, True)
+    St = O.schur(1, sysd.A, Ct, Dt, qptr, qidx, xt, gt).to_scipy().toarray()
+    np.testing.assert_allclose(St, S.T, atol=1e-12 * np.abs(S).max())
+
+
+def test_adjoint_gradient_matches_finite_differences():
+    n = (4, 3, 3)
+    Ne = int(np.prod(n))
+    logk = W.Stream(31).normal(Ne)
+    obs = np.array([1, 7, 20, 33])
+
+    def solve(lk):
+        s = W.assemble(*n, W.iso_K(np.exp(lk)))
+        M = s.full_scipy().toarray()
+        return s, M, np.linalg.solve(M, s.f_phys)
+
+    def loss(lk):
+        s, _, u = solve(lk)
+        return np.sum(u[s.Nf + obs] ** 2)
+
+    s, M, u = solve(logk)
+    dLdu = np.zeros(s.n)
+    dLdu[s.Nf + obs] = 2 * u[s.Nf + obs]
+    lam = np.linalg.solve(M.T, dLdu)
+    g = O.adjoint_grad(s, u, lam, logk)
+    h = 1e-6
+    for e in (0, 5, 17, 35):
+        lp, lm = logk.copy(), logk.copy()
+        lp[e] += h
+        lm[e] -= h
+        fd = (loss(lp) - loss(lm)) / (2 * h)
+        assert g[e] == pytest.approx(fd, rel=1e-6, abs=1e-12)

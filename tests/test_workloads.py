@@ -1,0 +1,246 @@
+"""Pins for the seeded workload generator (MHFE(RT0)-FV assembly, Sec. 2).
+
+Each check compares the assembled blocks with something the paper or the
+mathematics fixes independently of the generator's code: the closed-form
+brick elemental matrix, a quadrature of Eq. (B_ij) with the RT0 fields,
+exactness of the scheme for linear and 1-D layered pressure fields, the
+sign/symmetry properties of Sec. 2.3 and the per-row non-zero rules behind
+Table 1.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rt0_field(face, pt, lo, h):
+    """RT0 basis field of local face `face` (x-,x+,y-,y+,z-,z+) at point pt of
+    the brick [lo, lo+h]: unit flux through its own face, zero elsewhere."""
+    a = face // 2
+    area = np.prod([h[b] for b in range(3) if b != a])
+    v = np.zeros(3)
+    if face % 2 == 1:
+        v[a] = (pt[a] - lo[a]) / (h[a] * area)
+    else:
+        v[a] = -(lo[a] + h[a] - pt[a]) / (h[a] * area)
+    return v
+
+
+def test_rt0_field_properties():
+    # Eq. (MFE_property_1): unit outward flux through its own face only;
+    # Eq. (MFE_property_2): integral of the divergence is 1.
+    lo, h = np.array([0.3, -0.2, 1.0]), np.array([0.5, 0.25, 2.0])
+    for i in range(6):
+        for j in range(6):
+            a = j // 2
+            pt = lo + h / 2
+            pt[a] = lo[a] + (h[a] if j % 2 else 0.0)
+            n = np.zeros(3)
+            n[a] = 1.0 if j % 2 else -1.0
+            area = np.prod([h[b] for b in range(3) if b != a])
+            flux = rt0_field(i, pt, lo, h) @ n * area  # field normal component is constant on a face
+            assert flux == pytest.approx(1.0 if i == j else 0.0, abs=1e-14)
+        a = i // 2
+        div = 1.0 / np.prod(h)  # d/dx_a of the only nonzero component
+        assert div * np.prod(h) == pytest.approx(1.0)
+
+
+def test_elemental_matrix_quadrature_and_inverse():
+    rng = np.random.default_rng(0)
+    h = np.array([0.7, 0.4, 1.3])
+    Q = np.linalg.qr(rng.normal(size=(3, 3)))[0]
+    Kf = Q @ np.diag([2.0, 0.5, 0.05]) @ Q.T
+    K6 = np.array([Kf[0, 0], Kf[1, 1], Kf[2, 2], Kf[0, 1], Kf[0, 2], Kf[1, 2]])
+    Minv = np.linalg.inv(Kf)
+    # 2-point Gauss-Legendre per direction is exact for the quadratic integrands
+    g = np.array([-1, 1]) / np.sqrt(3.0)
+    lo = np.zeros(3)
+    Bq = np.zeros((6, 6))
+    for gx in g:
+        for gy in g:
+            for gz in g:
+                pt = lo + h * (1 + np.array([gx, gy, gz])) / 2
+                E = np.array([rt0_field(i, pt, lo, h) for i in range(6)])
+                Bq += E @ Minv @ E.T * np.prod(h) / 8
+    Bg = W.elem_B(K6, h)
+    np.testing.assert_allclose(Bg, Bq, rtol=1e-13, atol=1e-15 * np.abs(Bq).max())
+    Wg = W.elem_W(K6, h)
+    np.testing.assert_allclose(Wg @ Bq, np.eye(6), atol=1e-12)
+    assert np.array_equal(Wg, Wg.T)
+    assert np.all(np.linalg.eigvalsh(Bq) > 0)
+
+
+def test_elemental_inverse_closed_form_diagonal_K():
+    # diagonal K on a brick: per axis (k_a A_a / h_a) [[4, 2], [2, 4]], no cross-axis coupling
+    h = np.array([0.5, 0.25, 0.125])
+    k = np.array([3.0, 0.2, 7.5])
+    Wg = W.elem_W(np.array([k[0], k[1], k[2], 0, 0, 0.0]), h)
+    ref = np.zeros((6, 6))
+    for a in range(3):
+        area = np.prod([h[b] for b in range(3) if b != a])
+        ref[2 * a:2 * a + 2, 2 * a:2 * a + 2] = k[a] * area / h[a] * np.array([[4, 2], [2, 4]])
+    np.testing.assert_allclose(Wg, ref, rtol=1e-13)
+    off = ref == 0
+    assert np.all(Wg[off] == 0.0)  # exact zeros: the numerical pattern stays block-diagonal
+
+
+def _full_tensor_brick(n=(3, 3, 2), seed=11, dirichlet=True, **kw):
+    s = W.Stream(seed)
+    Ne = int(np.prod(n))
+    m = np.exp(s.normal(Ne))
+    q = s.normal(4 * Ne).reshape(Ne, 4)
+    K = W.rotated_K(m, 0.1, q)
+    return W.assemble(*n, K, dirichlet=dirichlet, **kw)
+
+
+def test_face_block_symmetric_negative_definite():
+    # Sec. 2.3: A_pipi symmetric negative definite; A_pp symmetric pattern, non-symmetric values
+    s = _full_tensor_brick()
+    A = s.A.dense()
+    assert np.array_equal(A, A.T)
+    np.linalg.cholesky(-A)
+    D = s.D.dense()
+    assert np.array_equal(D != 0, (D != 0).T)
+    assert not np.allclose(D, D.T)
+    Bd, Cd = s.B.dense(), s.C.dense()
+    assert not np.allclose(Cd, Bd.T) and not np.allclose(Cd, -Bd.T)
+
+
+@pytest.mark.parametrize("kind", ["paper", "upwind"])
+def test_constant_pressure_balance(kind):
+    # a uniform pressure produces no flux: face rows balance, cell rows keep
+    # only the accumulation term Omega c / dt (Eq. discr_bal_FV_2 with p_n = 0)
+    s = W.Stream(3)
+    n = (3, 2, 4)
+    Ne = int(np.prod(n))
+    K = W.iso_K(np.exp(s.normal(Ne)))
+    kw = {}
+    if kind == "upwind":
+        tmp = W.assemble(*n, K)
+        kw = dict(fv_kind=1, lam_face=np.exp(s.normal(tmp.Nf)))
+    sysd = W.assemble(*n, K, p_left=1.0, p_right=1.0, dt=0.1, stor=0.01, **kw)
+    M = sysd.full_scipy()
+    res = M @ np.ones(sysd.n) - sysd.f_phys
+    acc = np.prod(sysd.h) * 0.01 / 0.1
+    np.testing.assert_allclose(res[: sysd.Nf], 0.0, atol=1e-12)
+    np.testing.assert_allclose(res[sysd.Nf:], acc, rtol=1e-10)
+
+
+def _centres(sysd):
+    nx, ny, nz = sysd.nx, sysd.ny, sysd.nz
+    hx = sysd.h[0]
+    ix = np.arange(sysd.Ne) % nx
+    xc = (ix + 0.5) * hx
+    xf = np.zeros(sysd.Nf)
+    nfx = (nx + 1) * ny * nz
+    fx = np.arange(nfx) % (nx + 1)
+    xf[:nfx] = fx * hx
+    # y- and z-faces sit at the x-centre of their cell
+    cells = np.where(sysd.face_cells[:, 0] >= 0, sysd.face_cells[:, 0], sysd.face_cells[:, 1])
+    xf[nfx:] = xc[cells[nfx:]]
+    return xf, xc
+
+
+def test_linear_pressure_patch():
+    # RT0 reproduces linear pressure exactly: homogeneous anisotropic diagonal K,
+    # p = 1 at x = 0, p = 0 at x = 1, no-flow elsewhere, steady state
+    n = (5, 3, 4)
+    K = np.tile([2.5, 0.3, 0.07, 0, 0, 0], (int(np.prod(n)), 1))
+    sysd = W.assemble(*n, K, stor=0.0)
+    import scipy.sparse.linalg as spl
+    u = spl.spsolve(sysd.full_scipy().tocsc(), sysd.f_phys)
+    xf, xc = _centres(sysd)
+    np.testing.assert_allclose(u[: sysd.Nf], 1 - xf, atol=1e-12)
+    np.testing.assert_allclose(u[sysd.Nf:], 1 - xc, atol=1e-12)
+
+
+def test_layered_1d_series_solution():
+    # conductivity varying along x only: the exact solution is the 1-D series
+    # (harmonic) profile, which the MHFE-FV scheme reproduces at faces and cell centres
+    n = (7, 2, 3)
+    kx = np.exp(W.Stream(9).normal(n[0]) * 1.5)
+    Ne = int(np.prod(n))
+    k = np.tile(kx, Ne // n[0])
+    sysd = W.assemble(*n, W.iso_K(k), stor=0.0)
+    import scipy.sparse.linalg as spl
+    u = spl.spsolve(sysd.full_scipy().tocsc(), sysd.f_phys)
+    h = sysd.h[0]
+    R = np.concatenate([[0.0], np.cumsum(h / kx)])
+    pface = 1.0 - R / R[-1]
+    pcell = 1.0 - (R[:-1] + 0.5 * h / kx) / R[-1]
+    xf, _ = _centres(sysd)
+    nfx = (n[0] + 1) * n[1] * n[2]
+    fx = np.arange(nfx) % (n[0] + 1)
+    np.testing.assert_allclose(u[:nfx], pface[fx], atol=1e-12)
+    ix = np.arange(Ne) % n[0]
+    np.testing.assert_allclose(u[sysd.Nf:], pcell[ix], atol=1e-12)
+    cells = np.where(sysd.face_cells[:, 0] >= 0, sysd.face_cells[:, 0], sysd.face_cells[:, 1])
+    np.testing.assert_allclose(u[nfx:sysd.Nf], pcell[ix[cells[nfx:]]], atol=1e-12)
+
+
+def _interior_faces(sysd):
+    return int(np.sum((sysd.face_cells[:, 0] >= 0) & (sysd.face_cells[:, 1] >= 0)))
+
+
+def test_nnz_row_rules_match_table1():
+    # Table 1: nnz(A_pip) = 6 N_e; with conn = (nnz(A_pp) - N_e)/2 inter-element
+    # faces, nnz(A_ppi) = 6 N_e + 2 conn (+61) on the structured grid and
+    # 6 N_e + 10 conn (+305 = 5 x 61) on the unstructured one.
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "table1_nnz.txt")):
+        if line.strip() and not line.startswith("#"):
+            p = line.split()
+            rows[p[0]] = [int(v) for v in p[1:]]
+    Ne = 51741
+    for name, (tot, a, b, c, d) in rows.items():
+        assert a + b + c + d == tot
+        assert b == 6 * Ne
+        conn = (d - Ne) // 2
+        assert (d - Ne) % 2 == 0
+        mult = 2 if name == "structured" else 10
+        resid = c - (6 * Ne + mult * conn)
+        assert resid == (61 if name == "structured" else 305)
+    # the generator follows the same per-row rules (no prescribed faces):
+    # structured (diagonal K, block-diagonal W^E) and full-tensor (dense W^E).
+    # Globally nnz(B) = 6 N_e and nnz(D) = N_e + 2 conn; per interior row a face
+    # couples to the faces of its two cells and a cell to its own faces plus the
+    # (1 or 5) far faces of each neighbour across the shared face.
+    n = (4, 3, 5)
+    Ne = int(np.prod(n))
+    diag = W.assemble(*n, W.iso_K(np.exp(W.Stream(4).normal(Ne))), dirichlet=False)
+    full = _full_tensor_brick(n, dirichlet=False)
+    for sysd, crow, arow in ((diag, 6 + 6 * 1, 3), (full, 6 + 6 * 5, 11)):
+        conn = _interior_faces(sysd)
+        assert sysd.B.nnz == 6 * Ne
+        assert sysd.D.nnz == Ne + 2 * conn
+        interior_cells = [e for e in range(Ne)
+                          if np.all(sysd.face_cells[sysd.cell_faces[e]].min(axis=1) >= 0)]
+        assert interior_cells
+        for e in interior_cells:
+            assert sysd.C.rowptr[e + 1] - sysd.C.rowptr[e] == crow
+            assert sysd.D.rowptr[e + 1] - sysd.D.rowptr[e] == 7
+        for f in np.nonzero(sysd.face_cells.min(axis=1) >= 0)[0]:
+            assert sysd.A.rowptr[f + 1] - sysd.A.rowptr[f] == arow
+            assert sysd.B.rowptr[f + 1] - sysd.B.rowptr[f] == 2
+    assert full.A.nnz == full.Nf + 30 * Ne and diag.A.nnz == diag.Nf + 6 * Ne
+
+
+def test_grid_counts():
+    s = W.config1()
+    assert (s.Nf, s.Ne) == (3300, 1000)
+    # C2 face count formula (x-, y-, z-faces)
+    n = 64
+    assert (n + 1) * n * n * 3 == 798720
+
+
+def test_rng_moments_and_determinism():
+    a = W.Stream(123).normal(200000)
+    b = W.Stream(123).normal(200000)
+    assert np.array_equal(a, b)
+    assert abs(a.mean()) < 0.01 and abs(a.std() - 1) < 0.01
+    u = W.Stream(5).uniform(100000)
+    assert u.min() >= 0 and u.max() < 1 and abs(u.mean() - 0.5) < 0.01

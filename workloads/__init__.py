@@ -1,0 +1,433 @@
+"""Seeded synthetic workloads for the EDFA hot path.
+
+The five workloads stand in for the paper's SPE10 test cases (Sec. 4,
+Table 1), whose data is not available: brick grids of cubic cells with the
+MHFE(RT0)-FV block system [A B; C D] of Sec. 2.3 (A = A_pipi faces x faces,
+B = A_pip, C = A_ppi, D = A_pp).  All random numbers come from one SplitMix64
+stream per workload (Box-Muller normals), so a workload is a pure function of
+its index.
+
+This module produces inputs only; it holds none of the preconditioner's
+arithmetic.  The assembly itself lives in ``gen.c`` (built on first use).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import tempfile
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gen.c")
+_SO = os.path.join(_HERE, "_build", "libwl.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile gen.c into workloads/_build/libwl.so (plain gcc, -O2)."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    fd, tmp = tempfile.mkstemp(suffix=".so", dir=os.path.dirname(_SO))
+    os.close(fd)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fvisibility=hidden",
+                           "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _CSR(C.Structure):
+    _fields_ = [("nrows", C.c_int32), ("ncols", C.c_int32), ("nnz", C.c_int64),
+                ("rowptr", C.POINTER(C.c_int64)), ("col", C.POINTER(C.c_int32)),
+                ("val", C.POINTER(C.c_double))]
+
+
+class _Problem(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double),
+                ("dt", C.c_double), ("stor", C.c_double),
+                ("fv_kind", C.c_int32), ("dirichlet", C.c_int32),
+                ("p_left", C.c_double), ("p_right", C.c_double),
+                ("K", C.POINTER(C.c_double)), ("lam_face", C.POINTER(C.c_double))]
+
+
+class _System(C.Structure):
+    _fields_ = [("Nf", C.c_int32), ("Ne", C.c_int32),
+                ("A", _CSR), ("B", _CSR), ("C", _CSR), ("D", _CSR),
+                ("f", C.POINTER(C.c_double)), ("W", C.POINTER(C.c_double)),
+                ("cell_faces", C.POINTER(C.c_int32)), ("face_cells", C.POINTER(C.c_int32)),
+                ("face_dir", C.POINTER(C.c_int8)), ("face_pbar", C.POINTER(C.c_double))]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        L.wl_splitmix64.restype = C.c_uint64
+        L.wl_splitmix64.argtypes = [C.POINTER(C.c_uint64)]
+        L.wl_uniform.restype = C.c_double
+        L.wl_uniform.argtypes = [C.POINTER(C.c_uint64)]
+        L.wl_normal.restype = C.c_double
+        L.wl_normal.argtypes = [C.POINTER(C.c_uint64)]
+        for fn in (L.wl_fill_uniform, L.wl_fill_normal):
+            fn.restype = None
+            fn.argtypes = [C.POINTER(C.c_uint64), C.c_int64, C.POINTER(C.c_double)]
+        L.wl_assemble.restype = C.c_int
+        L.wl_assemble.argtypes = [C.POINTER(_Problem), C.POINTER(_System)]
+        L.wl_free_system.restype = None
+        L.wl_free_system.argtypes = [C.POINTER(_System)]
+        L.wl_elem_W.restype = C.c_int
+        L.wl_elem_W.argtypes = [C.POINTER(C.c_double), C.c_double, C.c_double, C.c_double,
+                                C.POINTER(C.c_double)]
+        L.wl_elem_B.restype = None
+        L.wl_elem_B.argtypes = [C.POINTER(C.c_double), C.c_double, C.c_double, C.c_double,
+                                C.POINTER(C.c_double)]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Stream:
+    """SplitMix64 stream with Box-Muller normals (the generator in gen.c)."""
+
+    def __init__(self, seed: int):
+        self.state = C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF)
+
+    def uniform(self, n: int) -> np.ndarray:
+        out = np.empty(int(n), dtype=np.float64)
+        lib().wl_fill_uniform(C.byref(self.state), int(n), _dp(out))
+        return out
+
+    def normal(self, n: int) -> np.ndarray:
+        out = np.empty(int(n), dtype=np.float64)
+        lib().wl_fill_normal(C.byref(self.state), int(n), _dp(out))
+        return out
+
+
+@dataclass
+class CSR:
+    nrows: int
+    ncols: int
+    rowptr: np.ndarray  # int64 [nrows+1]
+    col: np.ndarray     # int32 [nnz], ascending within a row
+    val: np.ndarray     # float64 [nnz]
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+        return sp.csr_matrix((self.val, self.col, self.rowptr), shape=(self.nrows, self.ncols))
+
+    def dense(self) -> np.ndarray:
+        return self.to_scipy().toarray()
+
+
+@dataclass
+class System:
+    """One block system [A B; C D] u = b with its grid description."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    h: tuple
+    Nf: int
+    Ne: int
+    A: CSR
+    B: CSR
+    C: CSR
+    D: CSR
+    b: np.ndarray            # [Nf+Ne] right-hand side used by the workload
+    f_phys: np.ndarray       # [Nf+Ne] right-hand side from the prescribed pressures
+    K: np.ndarray            # [Ne,6]
+    W: np.ndarray            # [Ne,6,6] elemental B^{E,-1}
+    cell_faces: np.ndarray   # [Ne,6]
+    face_cells: np.ndarray   # [Nf,2]
+    face_dir: np.ndarray     # [Nf] bool
+    face_pbar: np.ndarray    # [Nf]
+    dt: float
+    stor: float
+    fv_kind: int
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return self.Nf + self.Ne
+
+    def full_scipy(self):
+        import scipy.sparse as sp
+        return sp.bmat([[self.A.to_scipy(), self.B.to_scipy()],
+                        [self.C.to_scipy(), self.D.to_scipy()]], format="csr")
+
+
+def _csr_from(c: _CSR) -> CSR:
+    n, nnz = c.nrows, c.nnz
+    rp = np.ctypeslib.as_array(c.rowptr, shape=(n + 1,)).copy()
+    if nnz:
+        col = np.ctypeslib.as_array(c.col, shape=(nnz,)).copy()
+        val = np.ctypeslib.as_array(c.val, shape=(nnz,)).copy()
+    else:
+        col = np.zeros(0, np.int32)
+        val = np.zeros(0, np.float64)
+    return CSR(c.nrows, c.ncols, rp, col, val)
+
+
+def assemble(nx, ny, nz, K, *, h=None, dt=0.1, stor=1e-2, fv_kind=0, lam_face=None,
+             dirichlet=True, p_left=1.0, p_right=0.0, name="custom", b=None) -> System:
+    """Assemble the MHFE-FV block system for a brick grid with per-cell K[Ne,6]."""
+    if h is None:
+        h = (1.0 / nx, 1.0 / nx, 1.0 / nx)
+    Ne = nx * ny * nz
+    K = np.ascontiguousarray(K, dtype=np.float64).reshape(Ne, 6)
+    P = _Problem(nx, ny, nz, h[0], h[1], h[2], dt, stor, fv_kind, 1 if dirichlet else 0,
+                 p_left, p_right, _dp(K), None)
+    if fv_kind == 1:
+        lam_face = np.ascontiguousarray(lam_face, dtype=np.float64)
+        P.lam_face = _dp(lam_face)
+    S = _System()
+    rc = lib().wl_assemble(C.byref(P), C.byref(S))
+    if rc != 0:
+        raise RuntimeError(f"wl_assemble failed ({rc})")
+    try:
+        Nf, Ne = S.Nf, S.Ne
+        sysd = System(
+            name=name, nx=nx, ny=ny, nz=nz, h=tuple(h), Nf=Nf, Ne=Ne,
+            A=_csr_from(S.A), B=_csr_from(S.B), C=_csr_from(S.C), D=_csr_from(S.D),
+            b=None, f_phys=np.ctypeslib.as_array(S.f, shape=(Nf + Ne,)).copy(), K=K.copy(),
+            W=np.ctypeslib.as_array(S.W, shape=(Ne * 36,)).copy().reshape(Ne, 6, 6),
+            cell_faces=np.ctypeslib.as_array(S.cell_faces, shape=(Ne * 6,)).copy().reshape(Ne, 6),
+            face_cells=np.ctypeslib.as_array(S.face_cells, shape=(Nf * 2,)).copy().reshape(Nf, 2),
+            face_dir=np.ctypeslib.as_array(S.face_dir, shape=(Nf,)).copy().astype(bool),
+            face_pbar=np.ctypeslib.as_array(S.face_pbar, shape=(Nf,)).copy(),
+            dt=dt, stor=stor, fv_kind=fv_kind)
+    finally:
+        lib().wl_free_system(C.byref(S))
+    sysd.b = sysd.f_phys.copy() if b is None else np.ascontiguousarray(b, dtype=np.float64)
+    return sysd
+
+
+def elem_W(K6, h):
+    K6 = np.ascontiguousarray(K6, dtype=np.float64)
+    out = np.empty(36)
+    if lib().wl_elem_W(_dp(K6), h[0], h[1], h[2], _dp(out)) != 0:
+        raise ValueError("elemental matrix not SPD")
+    return out.reshape(6, 6)
+
+
+def elem_B(K6, h):
+    K6 = np.ascontiguousarray(K6, dtype=np.float64)
+    out = np.empty(36)
+    lib().wl_elem_B(_dp(K6), h[0], h[1], h[2], _dp(out))
+    return out.reshape(6, 6)
+
+
+def iso_K(k: np.ndarray) -> np.ndarray:
+    K = np.zeros((k.size, 6))
+    K[:, 0] = K[:, 1] = K[:, 2] = k
+    return K
+
+
+def _quat_rot(q: np.ndarray) -> np.ndarray:
+    """Rotation matrices [n,3,3] from (unnormalised) quaternions [n,4]."""
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    R = np.empty((q.shape[0], 3, 3))
+    R[:, 0, 0] = 1 - 2 * (y * y + z * z)
+    R[:, 0, 1] = 2 * (x * y - w * z)
+    R[:, 0, 2] = 2 * (x * z + w * y)
+    R[:, 1, 0] = 2 * (x * y + w * z)
+    R[:, 1, 1] = 1 - 2 * (x * x + z * z)
+    R[:, 1, 2] = 2 * (y * z - w * x)
+    R[:, 2, 0] = 2 * (x * z - w * y)
+    R[:, 2, 1] = 2 * (y * z + w * x)
+    R[:, 2, 2] = 1 - 2 * (x * x + y * y)
+    return R
+
+
+def rotated_K(m: np.ndarray, aniso: float, q: np.ndarray) -> np.ndarray:
+    """K = R diag(m, m, m*aniso) R^T per cell, stored as xx yy zz xy xz yz."""
+    R = _quat_rot(q)
+    d = np.stack([m, m, m * aniso], axis=1)
+    Kf = np.einsum("nij,nj,nkj->nik", R, d, R)
+    Kf = 0.5 * (Kf + np.transpose(Kf, (0, 2, 1)))
+    return np.stack([Kf[:, 0, 0], Kf[:, 1, 1], Kf[:, 2, 2], Kf[:, 0, 1], Kf[:, 0, 2], Kf[:, 1, 2]], axis=1)
+
+
+def _face_upwind_mobility(nx, ny, nz, lam_cell, signs_u, face_cells):
+    """Face mobility lam_f = lam of the upwind cell; the upwind side of an
+    interior face is chosen by a seeded random flux sign, a boundary face
+    takes its only cell."""
+    m, p = face_cells[:, 0], face_cells[:, 1]
+    pick_plus = signs_u >= 0.5
+    up = np.where(m < 0, p, np.where(p < 0, m, np.where(pick_plus, p, m)))
+    return lam_cell[up]
+
+
+# ---------------------------------------------------------------- workloads
+def brick(nx, ny=None, nz=None, *, seed=1, sigma=1.0, kind="paper", rhs="phys", name=None,
+          dt=0.1, stor=1e-2) -> System:
+    """Small seeded isotropic-K brick system (tiny-grid pins and parity cases).
+
+    kind="paper": strong inter-element flux cell rows (Appendix A);
+    kind="upwind": C = -B^T diag(lam_upwind), D = diag(sum lam B) + Omega c/dt.
+    rhs="phys": prescribed-pressure right-hand side; "random": N(0,1) entries.
+    """
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    s = Stream(seed)
+    Ne = nx * ny * nz
+    k = np.exp(sigma * s.normal(Ne))
+    K = iso_K(k)
+    kw = {}
+    if kind == "upwind":
+        lam = np.exp(0.5 * s.normal(Ne))
+        tmp = assemble(nx, ny, nz, K, dt=dt, stor=stor)  # for the face-cell map only
+        signs = s.uniform(tmp.Nf)
+        kw = dict(fv_kind=1, lam_face=_face_upwind_mobility(nx, ny, nz, lam, signs, tmp.face_cells))
+    sysd = assemble(nx, ny, nz, K, dt=dt, stor=stor, name=name or f"brick{nx}x{ny}x{nz}", **kw)
+    if rhs == "random":
+        sysd.b = s.normal(sysd.n)
+    return sysd
+
+
+def config1() -> System:
+    """10^3 unit-brick grid, isotropic K = exp(N(0,1)), upwind-mobility C,
+    dt = 0.1, c = 1e-2, prescribed p = 1 / 0 on x = 0 / 1, random RHS, Q = own faces."""
+    s = Stream(1)
+    nx = 10
+    Ne = nx ** 3
+    K = iso_K(np.exp(s.normal(Ne)))
+    lam = np.exp(0.5 * s.normal(Ne))
+    tmp = assemble(nx, nx, nx, K)
+    signs = s.uniform(tmp.Nf)
+    lam_f = _face_upwind_mobility(nx, nx, nx, lam, signs, tmp.face_cells)
+    sysd = assemble(nx, nx, nx, K, fv_kind=1, lam_face=lam_f, name="C1 10^3 upwind-mobility")
+    sysd.b = s.normal(sysd.n)
+    sysd.extra.update(qmode="own", lam_cell=lam)
+    return sysd
+
+
+def config2(n: int = 64) -> System:
+    """n^3 grid (64^3 by default), full-tensor K = R diag(m,m,m/10) R^T with
+    m = exp(2 N(0,1)) and R a random rotation per cell; strong-flux FV;
+    prescribed-pressure RHS; Q = own faces + faces of face-neighbours."""
+    s = Stream(2)
+    Ne = n ** 3
+    m = np.exp(2.0 * s.normal(Ne))
+    q = s.normal(4 * Ne).reshape(Ne, 4)
+    K = rotated_K(m, 0.1, q)
+    sysd = assemble(n, n, n, K, name=f"C2 {n}^3 full-tensor")
+    sysd.extra.update(qmode="nbr")
+    return sysd
+
+
+def channel_K(nx, ny, nz, h, s: Stream) -> np.ndarray:
+    """Layered channelised diagonal K: background log10 Kh ~ U(-6,-3) per cell,
+    three sinusoidal channels per layer with log10 Kh ~ U(-1,0) inside,
+    Kv = 0.1 Kh."""
+    Ne = nx * ny * nz
+    lg = -6.0 + 3.0 * s.uniform(Ne)
+    lg_ch = -1.0 + s.uniform(Ne)
+    ix = np.arange(nx)
+    iy = np.arange(ny)
+    xc = (ix + 0.5) * h[0]
+    yc = (iy + 0.5) * h[1]
+    X, Y = np.meshgrid(xc, yc, indexing="xy")  # [ny, nx]
+    lg = lg.reshape(nz, ny, nx)
+    lg_ch = lg_ch.reshape(nz, ny, nx)
+    for iz in range(nz):
+        p = s.uniform(15).reshape(3, 5)
+        inside = np.zeros((ny, nx), bool)
+        for c in range(3):
+            y0 = 0.1 + 0.8 * p[c, 0]
+            a = 0.05 + 0.15 * p[c, 1]
+            fr = 0.5 + 1.5 * p[c, 2]
+            ph = 2 * np.pi * p[c, 3]
+            hw = 0.02 + 0.03 * p[c, 4]
+            inside |= np.abs(Y - (y0 + a * np.sin(2 * np.pi * fr * X + ph))) < hw
+        lg[iz][inside] = lg_ch[iz][inside]
+    kh = 10.0 ** lg.reshape(Ne)
+    K = np.zeros((Ne, 6))
+    K[:, 0] = kh
+    K[:, 1] = kh
+    K[:, 2] = 0.1 * kh
+    return K
+
+
+def config3(nx: int = 128, ny: int = 128, nz: int = 64) -> System:
+    """128x128x64 layered channelised grid (cells 1/128), diagonal K with
+    6 orders of magnitude and Kv = 0.1 Kh; strong-flux FV; prescribed-pressure
+    RHS; Q = own faces + strong A-connections |a_ij| >= 0.05 |a_ii|."""
+    s = Stream(3)
+    h = (1.0 / nx,) * 3
+    K = channel_K(nx, ny, nz, h, s)
+    sysd = assemble(nx, ny, nz, K, h=h, name=f"C3 {nx}x{ny}x{nz} channelised")
+    sysd.extra.update(qmode="thresh", thresh=0.05)
+    return sysd
+
+
+def config4_sizes(nsys: int = 256) -> np.ndarray:
+    s = Stream((4 << 32))
+    return (16 + np.floor(33 * s.uniform(nsys))).astype(np.int64)
+
+
+def config4_system(i: int, n: int) -> System:
+    """System i of the batched workload: n^3 grid, isotropic K = exp(1.5 N(0,1)),
+    strong-flux FV, random N(0,1) RHS, Q = own + neighbour faces."""
+    s = Stream((4 << 32) + 1 + i)
+    Ne = n ** 3
+    K = iso_K(np.exp(1.5 * s.normal(Ne)))
+    sysd = assemble(n, n, n, K, name=f"C4[{i}] {n}^3")
+    sysd.b = s.normal(sysd.n)
+    sysd.extra.update(qmode="nbr")
+    return sysd
+
+
+def config4(nsys: int = 256, limit=None):
+    sizes = config4_sizes(nsys)
+    idx = range(nsys) if limit is None else range(min(limit, nsys))
+    return [config4_system(i, int(sizes[i])) for i in idx]
+
+
+def config5(n: int = 48, nobs: int = 64, nfd: int = 20) -> System:
+    """n^3 grid (48^3), isotropic K = exp(N(0,1)), strong-flux FV,
+    prescribed-pressure RHS, Q = pattern of row m of C; loss = sum of squared
+    cell pressures at 64 seeded observation cells; 20 seeded cells for
+    finite-difference checks."""
+    s = Stream(5)
+    Ne = n ** 3
+    k = np.exp(s.normal(Ne))
+    K = iso_K(k)
+    sysd = assemble(n, n, n, K, name=f"C5 {n}^3 adjoint")
+    perm = np.arange(Ne)
+    u = s.uniform(nobs)
+    for j in range(nobs):  # partial Fisher-Yates: observation cells without replacement
+        r = j + int(u[j] * (Ne - j))
+        perm[j], perm[r] = perm[r], perm[j]
+    obs = np.sort(perm[:nobs]).astype(np.int64)
+    u = s.uniform(nfd)
+    perm = np.arange(Ne)
+    for j in range(nfd):
+        r = j + int(u[j] * (Ne - j))
+        perm[j], perm[r] = perm[r], perm[j]
+    fd = np.sort(perm[:nfd]).astype(np.int64)
+    sysd.extra.update(qmode="crow", obs=obs, fd_cells=fd, logk=np.log(k))
+    return sysd
+
+
+def config5_reassemble(sysd: System, logk: np.ndarray) -> System:
+    """Re-assemble workload 5 with a modified per-cell log-conductivity."""
+    out = assemble(sysd.nx, sysd.ny, sysd.nz, iso_K(np.exp(logk)), h=sysd.h, dt=sysd.dt,
+                   stor=sysd.stor, name=sysd.name + " (perturbed)")
+    out.extra.update(sysd.extra)
+    out.extra["logk"] = logk.copy()
+    return out

@@ -1,0 +1,493 @@
+/*
+ * Seeded synthetic workloads for the EDFA hot path: brick grids, conductivity
+ * fields and the MHFE(RT0)-FV block system [A B; C D] of the model problem
+ * (Sec. 2.2-2.3, Eq. (B_ij), Eq. (fluxes_MHFEM_3), Eq. (discr_bal_FV_2),
+ * Eq. (fluxes_MHFEM_STRONG), Eq. (cont_fluxes), Appendix A).
+ *
+ * This module only PRODUCES inputs.  It holds none of the preconditioner's
+ * arithmetic (no restriction sets, local solves, Schur complement,
+ * incomplete factorisation or Krylov iteration); both the CPU oracle and the
+ * CUDA library consume what it writes.
+ *
+ * Notation: A = A_pipi (faces x faces), B = A_pip (faces x cells),
+ * C = A_ppi (cells x faces), D = A_pp (cells x cells).  W^E = (B^E)^{-1} is
+ * the inverse elemental matrix of cell E, L_i^E = sum_j W^E_ij.
+ *
+ * Grid numbering: cells lexicographic (ix fastest).  Faces: all x-faces,
+ * then all y-faces, then all z-faces, each lexicographic with the face
+ * coordinate fastest.  Local face order in a cell: x-, x+, y-, y+, z-, z+.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define WL_EXPORT __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------ RNG */
+/* SplitMix64 (G. Steele, D. Lea, C. Flood, "Fast splittable pseudorandom
+ * number generators", OOPSLA 2014): state += golden gamma, then a
+ * two-multiply xor-shift finaliser. */
+WL_EXPORT uint64_t wl_splitmix64(uint64_t* s)
+{
+    uint64_t z = (*s += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* uniform on [0,1) with 53 random bits */
+WL_EXPORT double wl_uniform(uint64_t* s)
+{
+    return (double)(wl_splitmix64(s) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* standard normal by the Box-Muller transform (cosine branch only) */
+WL_EXPORT double wl_normal(uint64_t* s)
+{
+    double u1 = 1.0 - wl_uniform(s); /* (0,1] */
+    double u2 = wl_uniform(s);
+    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+WL_EXPORT void wl_fill_uniform(uint64_t* s, int64_t n, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = wl_uniform(s);
+}
+
+WL_EXPORT void wl_fill_normal(uint64_t* s, int64_t n, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = wl_normal(s);
+}
+
+/* --------------------------------------------------------------- types */
+typedef struct {
+    int32_t nx, ny, nz;
+    double hx, hy, hz;
+    double dt, stor;     /* backward-Euler step and storage coefficient c */
+    int32_t fv_kind;     /* 0: strong inter-element flux (Appendix A)
+                            1: upwind-mobility cell rows C = -B^T diag(lam) */
+    int32_t dirichlet;   /* 1: prescribed pressure on the x=0 and x=1 faces */
+    double p_left, p_right;
+    const double* K;     /* [Ne*6] Kxx Kyy Kzz Kxy Kxz Kyz per cell */
+    const double* lam_face; /* [Nf] face mobility (fv_kind 1 only) */
+} wl_problem;
+
+typedef struct {
+    int32_t nrows, ncols;
+    int64_t nnz;
+    int64_t* rowptr;
+    int32_t* col;
+    double* val;
+} wl_csr;
+
+typedef struct {
+    int32_t Nf, Ne;
+    wl_csr A, B, C, D;
+    double* f;          /* [Nf+Ne] right-hand side from the prescribed pressures */
+    double* W;          /* [Ne*36] W^E row-major, local face order */
+    int32_t* cell_faces;/* [Ne*6] */
+    int32_t* face_cells;/* [Nf*2] minus-side, plus-side cell (-1 = none) */
+    int8_t* face_dir;   /* [Nf] 1 = prescribed pressure face */
+    double* face_pbar;  /* [Nf] prescribed pressure (0 elsewhere) */
+} wl_system;
+
+/* ------------------------------------------------------------ topology */
+static inline int64_t nfx(const wl_problem* P) { return (int64_t)(P->nx + 1) * P->ny * P->nz; }
+static inline int64_t nfy(const wl_problem* P) { return (int64_t)P->nx * (P->ny + 1) * P->nz; }
+static inline int64_t nfz(const wl_problem* P) { return (int64_t)P->nx * P->ny * (P->nz + 1); }
+
+static inline int32_t xface(const wl_problem* P, int fx, int iy, int iz)
+{ return (int32_t)(fx + (int64_t)(P->nx + 1) * (iy + (int64_t)P->ny * iz)); }
+static inline int32_t yface(const wl_problem* P, int ix, int fy, int iz)
+{ return (int32_t)(nfx(P) + ix + (int64_t)P->nx * (fy + (int64_t)(P->ny + 1) * iz)); }
+static inline int32_t zface(const wl_problem* P, int ix, int iy, int fz)
+{ return (int32_t)(nfx(P) + nfy(P) + ix + (int64_t)P->nx * (iy + (int64_t)P->ny * fz)); }
+
+/* ------------------------------------------------- elemental matrices */
+/* B^E_ij = gamma * int eta_i^T K^{-1} eta_j over a brick (Eq. B_ij), gamma = 1,
+ * with the RT0 fields eta = s*phi/(h_a*A_a) e_a, phi = distance to the
+ * opposite face, s = +1 on the + face and -1 on the - face. */
+static void elem_B(const double K6[6], double hx, double hy, double hz, double Bm[36])
+{
+    double kxx = K6[0], kyy = K6[1], kzz = K6[2], kxy = K6[3], kxz = K6[4], kyz = K6[5];
+    /* M = K^{-1} by cofactors */
+    double c00 = kyy * kzz - kyz * kyz;
+    double c01 = -(kxy * kzz - kyz * kxz);
+    double c02 = kxy * kyz - kyy * kxz;
+    double c11 = kxx * kzz - kxz * kxz;
+    double c12 = -(kxx * kyz - kxy * kxz);
+    double c22 = kxx * kyy - kxy * kxy;
+    double det = kxx * c00 + kxy * c01 + kxz * c02;
+    double M[3][3] = {{c00 / det, c01 / det, c02 / det},
+                      {c01 / det, c11 / det, c12 / det},
+                      {c02 / det, c12 / det, c22 / det}};
+    double h[3] = {hx, hy, hz};
+    double Ar[3] = {hy * hz, hx * hz, hx * hy};
+    double V = hx * hy * hz;
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            int a = i / 2, b = j / 2;
+            double si = (i & 1) ? 1.0 : -1.0, sj = (j & 1) ? 1.0 : -1.0;
+            double v;
+            if (a == b) {
+                if (i == j) v = M[a][a] * h[a] / (3.0 * Ar[a]);
+                else v = -M[a][a] * h[a] / (6.0 * Ar[a]);
+            } else {
+                v = si * sj * M[a][b] * V / (4.0 * Ar[a] * Ar[b]);
+            }
+            Bm[i * 6 + j] = v;
+        }
+}
+
+/* W = B^{-1} through a 6x6 Cholesky factorisation, then symmetrised so that
+ * the assembled face block is exactly symmetric. Returns 0 on success. */
+static int spd_inverse6(const double Bm[36], double Wm[36])
+{
+    double L[36];
+    memset(L, 0, sizeof L);
+    for (int j = 0; j < 6; ++j) {
+        double d = Bm[j * 6 + j];
+        for (int k = 0; k < j; ++k) d -= L[j * 6 + k] * L[j * 6 + k];
+        if (!(d > 0.0)) return -1;
+        L[j * 6 + j] = sqrt(d);
+        for (int i = j + 1; i < 6; ++i) {
+            double v = Bm[i * 6 + j];
+            for (int k = 0; k < j; ++k) v -= L[i * 6 + k] * L[j * 6 + k];
+            L[i * 6 + j] = v / L[j * 6 + j];
+        }
+    }
+    for (int c = 0; c < 6; ++c) {
+        double y[6], x[6];
+        for (int i = 0; i < 6; ++i) {
+            double v = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) v -= L[i * 6 + k] * y[k];
+            y[i] = v / L[i * 6 + i];
+        }
+        for (int i = 5; i >= 0; --i) {
+            double v = y[i];
+            for (int k = i + 1; k < 6; ++k) v -= L[k * 6 + i] * x[k];
+            x[i] = v / L[i * 6 + i];
+        }
+        for (int i = 0; i < 6; ++i) Wm[i * 6 + c] = x[i];
+    }
+    for (int i = 0; i < 6; ++i)
+        for (int j = i + 1; j < 6; ++j) {
+            double s = 0.5 * (Wm[i * 6 + j] + Wm[j * 6 + i]);
+            Wm[i * 6 + j] = s;
+            Wm[j * 6 + i] = s;
+        }
+    return 0;
+}
+
+WL_EXPORT int wl_elem_W(const double K6[6], double hx, double hy, double hz, double Wm[36])
+{
+    double Bm[36];
+    elem_B(K6, hx, hy, hz, Bm);
+    return spd_inverse6(Bm, Wm);
+}
+
+WL_EXPORT void wl_elem_B(const double K6[6], double hx, double hy, double hz, double Bm[36])
+{
+    elem_B(K6, hx, hy, hz, Bm);
+}
+
+/* ------------------------------------------------------------ triplets */
+typedef struct {
+    int64_t n, cap;
+    int32_t* r;
+    int32_t* c;
+    double* v;
+} trip;
+
+static int trip_push(trip* t, int32_t r, int32_t c, double v)
+{
+    if (t->n == t->cap) {
+        int64_t nc = t->cap ? 2 * t->cap : 1024;
+        int32_t* nr = (int32_t*)realloc(t->r, nc * sizeof(int32_t));
+        if (!nr) return -1;
+        t->r = nr;
+        int32_t* ncc = (int32_t*)realloc(t->c, nc * sizeof(int32_t));
+        if (!ncc) return -1;
+        t->c = ncc;
+        double* nv = (double*)realloc(t->v, nc * sizeof(double));
+        if (!nv) return -1;
+        t->v = nv;
+        t->cap = nc;
+    }
+    t->r[t->n] = r;
+    t->c[t->n] = c;
+    t->v[t->n] = v;
+    t->n++;
+    return 0;
+}
+
+static void trip_free(trip* t) { free(t->r); free(t->c); free(t->v); memset(t, 0, sizeof *t); }
+
+/* Triplets -> CSR with ascending columns and duplicates summed in push order
+ * (stable counting sort by row, then insertion sort by column within a row). */
+static int trip_to_csr(const trip* t, int32_t nrows, int32_t ncols, wl_csr* M)
+{
+    M->nrows = nrows;
+    M->ncols = ncols;
+    int64_t* cnt = (int64_t*)calloc((size_t)nrows + 1, sizeof(int64_t));
+    int32_t* cc = (int32_t*)malloc((size_t)(t->n ? t->n : 1) * sizeof(int32_t));
+    double* vv = (double*)malloc((size_t)(t->n ? t->n : 1) * sizeof(double));
+    if (!cnt || !cc || !vv) { free(cnt); free(cc); free(vv); return -1; }
+    for (int64_t k = 0; k < t->n; ++k) cnt[t->r[k] + 1]++;
+    for (int32_t i = 0; i < nrows; ++i) cnt[i + 1] += cnt[i];
+    int64_t* pos = (int64_t*)malloc((size_t)(nrows ? nrows : 1) * sizeof(int64_t));
+    if (!pos) { free(cnt); free(cc); free(vv); return -1; }
+    memcpy(pos, cnt, (size_t)nrows * sizeof(int64_t));
+    for (int64_t k = 0; k < t->n; ++k) {
+        int64_t p = pos[t->r[k]]++;
+        cc[p] = t->c[k];
+        vv[p] = t->v[k];
+    }
+    free(pos);
+    /* sort within rows (stable insertion sort), merge duplicates */
+    int64_t* rp = (int64_t*)malloc(((size_t)nrows + 1) * sizeof(int64_t));
+    if (!rp) { free(cnt); free(cc); free(vv); return -1; }
+    int64_t out = 0;
+    rp[0] = 0;
+    for (int32_t i = 0; i < nrows; ++i) {
+        int64_t b = cnt[i], e = cnt[i + 1];
+        for (int64_t p = b + 1; p < e; ++p) {
+            int32_t kc = cc[p];
+            double kv = vv[p];
+            int64_t q = p - 1;
+            while (q >= b && cc[q] > kc) { cc[q + 1] = cc[q]; vv[q + 1] = vv[q]; --q; }
+            cc[q + 1] = kc;
+            vv[q + 1] = kv;
+        }
+        for (int64_t p = b; p < e; ++p) {
+            if (out > rp[i] && cc[out - 1] == cc[p]) vv[out - 1] += vv[p];
+            else { cc[out] = cc[p]; vv[out] = vv[p]; out++; }
+        }
+        rp[i + 1] = out;
+    }
+    free(cnt);
+    M->rowptr = rp;
+    M->col = cc;
+    M->val = vv;
+    M->nnz = out;
+    return 0;
+}
+
+/* keep entries for which keep(row, col, val) is true; compacts in place */
+typedef int (*keep_fn)(const void* ctx, int32_t r, int32_t c, double v);
+
+static void csr_filter(wl_csr* M, keep_fn keep, const void* ctx)
+{
+    int64_t out = 0, b = 0;
+    for (int32_t i = 0; i < M->nrows; ++i) {
+        int64_t e = M->rowptr[i + 1];
+        for (int64_t p = b; p < e; ++p)
+            if (keep(ctx, i, M->col[p], M->val[p])) {
+                M->col[out] = M->col[p];
+                M->val[out] = M->val[p];
+                out++;
+            }
+        b = e;
+        M->rowptr[i + 1] = out;
+    }
+    M->nnz = out;
+}
+
+typedef struct { const int8_t* dir; int mode; } keep_ctx;
+
+/* mode 0: face block A: drop couplings of prescribed faces (keep their
+ *         diagonal), drop exact zeros off the diagonal
+ * mode 1: B: drop rows of prescribed faces and exact zeros
+ * mode 2: C: drop columns of prescribed faces and exact zeros
+ * mode 3: D: drop exact zeros off the diagonal */
+static int keep_entry(const void* vctx, int32_t r, int32_t c, double v)
+{
+    const keep_ctx* k = (const keep_ctx*)vctx;
+    switch (k->mode) {
+    case 0:
+        if (r == c) return 1;
+        if (k->dir[r] || k->dir[c]) return 0;
+        return v != 0.0;
+    case 1:
+        if (k->dir[r]) return 0;
+        return v != 0.0;
+    case 2:
+        if (k->dir[c]) return 0;
+        return v != 0.0;
+    default:
+        if (r == c) return 1;
+        return v != 0.0;
+    }
+}
+
+WL_EXPORT void wl_free_system(wl_system* S)
+{
+    wl_csr* m[4] = {&S->A, &S->B, &S->C, &S->D};
+    for (int k = 0; k < 4; ++k) {
+        free(m[k]->rowptr);
+        free(m[k]->col);
+        free(m[k]->val);
+    }
+    free(S->f);
+    free(S->W);
+    free(S->cell_faces);
+    free(S->face_cells);
+    free(S->face_dir);
+    free(S->face_pbar);
+    memset(S, 0, sizeof *S);
+}
+
+/* ------------------------------------------------------------ assembly */
+WL_EXPORT int wl_assemble(const wl_problem* P, wl_system* S)
+{
+    memset(S, 0, sizeof *S);
+    const int nx = P->nx, ny = P->ny, nz = P->nz;
+    const int64_t Ne64 = (int64_t)nx * ny * nz;
+    const int64_t Nf64 = nfx(P) + nfy(P) + nfz(P);
+    if (nx < 1 || ny < 1 || nz < 1 || Nf64 >= INT32_MAX) return -1;
+    const int32_t Ne = (int32_t)Ne64, Nf = (int32_t)Nf64;
+    S->Ne = Ne;
+    S->Nf = Nf;
+    S->W = (double*)malloc((size_t)Ne * 36 * sizeof(double));
+    S->cell_faces = (int32_t*)malloc((size_t)Ne * 6 * sizeof(int32_t));
+    S->face_cells = (int32_t*)malloc((size_t)Nf * 2 * sizeof(int32_t));
+    S->face_dir = (int8_t*)calloc((size_t)Nf, 1);
+    S->face_pbar = (double*)calloc((size_t)Nf, sizeof(double));
+    S->f = (double*)calloc((size_t)Nf + Ne, sizeof(double));
+    if (!S->W || !S->cell_faces || !S->face_cells || !S->face_dir || !S->face_pbar || !S->f) {
+        wl_free_system(S);
+        return -2;
+    }
+    for (int64_t i = 0; i < 2 * (int64_t)Nf; ++i) S->face_cells[i] = -1;
+
+    for (int iz = 0; iz < nz; ++iz)
+        for (int iy = 0; iy < ny; ++iy)
+            for (int ix = 0; ix < nx; ++ix) {
+                int32_t e = ix + nx * (iy + ny * iz);
+                int32_t* cf = S->cell_faces + (int64_t)e * 6;
+                cf[0] = xface(P, ix, iy, iz);
+                cf[1] = xface(P, ix + 1, iy, iz);
+                cf[2] = yface(P, ix, iy, iz);
+                cf[3] = yface(P, ix, iy + 1, iz);
+                cf[4] = zface(P, ix, iy, iz);
+                cf[5] = zface(P, ix, iy, iz + 1);
+                for (int l = 0; l < 6; ++l) {
+                    /* a cell is the plus-side cell of its minus faces */
+                    int side = (l & 1) ? 0 : 1;
+                    S->face_cells[2 * (int64_t)cf[l] + side] = e;
+                }
+                if (wl_elem_W(P->K + 6 * (int64_t)e, P->hx, P->hy, P->hz, S->W + 36 * (int64_t)e)) {
+                    wl_free_system(S);
+                    return -3;
+                }
+            }
+    if (P->dirichlet)
+        for (int iz = 0; iz < nz; ++iz)
+            for (int iy = 0; iy < ny; ++iy) {
+                int32_t f0 = xface(P, 0, iy, iz), f1 = xface(P, nx, iy, iz);
+                S->face_dir[f0] = 1;
+                S->face_pbar[f0] = P->p_left;
+                S->face_dir[f1] = 1;
+                S->face_pbar[f1] = P->p_right;
+            }
+
+    trip tA = {0}, tB = {0}, tC = {0}, tD = {0};
+    int err = 0;
+    /* face rows: q_i^E + q_i^E' = 0 with q^E = W^E (p^E 1 - pi^E)
+       (Eq. fluxes_MHFEM_3, Eq. cont_fluxes); no-flow faces keep only q_i^E */
+    for (int32_t i = 0; i < Nf && !err; ++i)
+        for (int side = 0; side < 2; ++side) {
+            int32_t e = S->face_cells[2 * (int64_t)i + side];
+            if (e < 0) continue;
+            const int32_t* cf = S->cell_faces + (int64_t)e * 6;
+            const double* W = S->W + 36 * (int64_t)e;
+            int li = 0;
+            while (cf[li] != i) ++li;
+            double L = 0.0;
+            for (int j = 0; j < 6; ++j) {
+                err |= trip_push(&tA, i, cf[j], -W[li * 6 + j]);
+                L += W[li * 6 + j];
+            }
+            err |= trip_push(&tB, i, e, L);
+        }
+    /* cell rows */
+    const double acc = P->hx * P->hy * P->hz * P->stor / P->dt;
+    for (int32_t e = 0; e < Ne && !err; ++e) {
+        const int32_t* cf = S->cell_faces + (int64_t)e * 6;
+        const double* W = S->W + 36 * (int64_t)e;
+        double Lrow[6];
+        for (int l = 0; l < 6; ++l) {
+            double s = 0.0;
+            for (int j = 0; j < 6; ++j) s += W[l * 6 + j];
+            Lrow[l] = s;
+        }
+        err |= trip_push(&tD, e, e, acc);
+        if (P->fv_kind == 1) {
+            /* C = -B^T diag(lam_face), D = diag(sum_f lam_f B_fE) + acc */
+            for (int l = 0; l < 6; ++l) {
+                double lam = P->lam_face[cf[l]];
+                err |= trip_push(&tC, e, cf[l], -lam * Lrow[l]);
+                err |= trip_push(&tD, e, e, lam * Lrow[l]);
+            }
+            continue;
+        }
+        for (int l = 0; l < 6; ++l) {
+            int32_t i = cf[l];
+            int side = (l & 1) ? 0 : 1; /* this cell's slot on face i */
+            int32_t e2 = S->face_cells[2 * (int64_t)i + (1 - side)];
+            if (e2 >= 0) {
+                /* strong inter-element flux (Eq. fluxes_MHFEM_STRONG):
+                   q = w Lambda^E - (1-w) Lambda^E', w = W'_ii / (W_ii + W'_ii) */
+                const int32_t* cf2 = S->cell_faces + (int64_t)e2 * 6;
+                const double* W2 = S->W + 36 * (int64_t)e2;
+                int l2 = 0;
+                while (cf2[l2] != i) ++l2;
+                double L2 = 0.0;
+                for (int j = 0; j < 6; ++j) L2 += W2[l2 * 6 + j];
+                double w = W2[l2 * 6 + l2] / (W[l * 6 + l] + W2[l2 * 6 + l2]);
+                double wc = W[l * 6 + l] / (W[l * 6 + l] + W2[l2 * 6 + l2]);
+                err |= trip_push(&tD, e, e, w * Lrow[l]);
+                for (int j = 0; j < 6; ++j)
+                    if (j != l) err |= trip_push(&tC, e, cf[j], -w * W[l * 6 + j]);
+                err |= trip_push(&tD, e, e2, -wc * L2);
+                for (int j = 0; j < 6; ++j)
+                    if (j != l2) err |= trip_push(&tC, e, cf2[j], wc * W2[l2 * 6 + j]);
+            } else if (S->face_dir[i]) {
+                /* prescribed-pressure face: q_i = sum_j W_ij (p^E - pi_j), pi_i = pbar */
+                err |= trip_push(&tD, e, e, Lrow[l]);
+                for (int j = 0; j < 6; ++j) err |= trip_push(&tC, e, cf[j], -W[l * 6 + j]);
+            }
+            /* no-flow face: q_i = 0 */
+        }
+    }
+    if (err) { trip_free(&tA); trip_free(&tB); trip_free(&tC); trip_free(&tD); wl_free_system(S); return -2; }
+    err |= trip_to_csr(&tA, Nf, Nf, &S->A);
+    err |= trip_to_csr(&tB, Nf, Ne, &S->B);
+    err |= trip_to_csr(&tC, Ne, Nf, &S->C);
+    err |= trip_to_csr(&tD, Ne, Ne, &S->D);
+    trip_free(&tA); trip_free(&tB); trip_free(&tC); trip_free(&tD);
+    if (err) { wl_free_system(S); return -2; }
+
+    /* move the prescribed face pressures to the right-hand side (symmetric
+       elimination: the face keeps its unknown, row i reads A_ii pi_i = A_ii pbar) */
+    double* fpi = S->f;
+    double* fp = S->f + Nf;
+    for (int32_t r = 0; r < Nf; ++r)
+        for (int64_t p = S->A.rowptr[r]; p < S->A.rowptr[r + 1]; ++p) {
+            int32_t c = S->A.col[p];
+            if (c == r) { if (S->face_dir[r]) fpi[r] = S->A.val[p] * S->face_pbar[r]; }
+            else if (S->face_dir[c] && !S->face_dir[r]) fpi[r] -= S->A.val[p] * S->face_pbar[c];
+        }
+    for (int32_t r = 0; r < Ne; ++r)
+        for (int64_t p = S->C.rowptr[r]; p < S->C.rowptr[r + 1]; ++p) {
+            int32_t c = S->C.col[p];
+            if (S->face_dir[c]) fp[r] -= S->C.val[p] * S->face_pbar[c];
+        }
+    keep_ctx k0 = {S->face_dir, 0}, k1 = {S->face_dir, 1}, k2 = {S->face_dir, 2}, k3 = {S->face_dir, 3};
+    csr_filter(&S->A, keep_entry, &k0);
+    csr_filter(&S->B, keep_entry, &k1);
+    csr_filter(&S->C, keep_entry, &k2);
+    csr_filter(&S->D, keep_entry, &k3);
+    return 0;
+}
