@@ -1,0 +1,180 @@
+/*
+ * edfa.h - C ABI of the GB300 (sm_103a) EDFA library.
+ *
+ * EDFA (Explicit Decoupling Factor Approximation) is the block preconditioner
+ * of Nardean, Ferronato & Abushaikha, arXiv 2009.13916, for the block system
+ * of the MHFE-FV flow model (Sec. 2.3, Eq. system):
+ *
+ *        [ A  B ] [ pi ]   [ f_pi ]      A = A_pipi  (N_f x N_f, faces)
+ *        [ C  D ] [ p  ] = [ f_p  ]      B = A_pip   (N_f x N_e)
+ *                                        C = A_ppi   (N_e x N_f)
+ *                                        D = A_pp    (N_e x N_e, cells)
+ *
+ * Stage 1 (edfa_build, Algorithm 1): restriction sets Q^(m), one restricted
+ * dense solve per cell (Eq. syst_MRHS_res, Eq. syst_MRHS_res-F) giving the
+ * decoupling-factor approximations X~ = -F~ (and G~), the product H~ and the
+ * ILU(0) factors standing for A~^{-1}.
+ * Stage 2 (edfa_setup, Algorithm 2): S~ = D - H~ (Eq. sparse_S) and its ILU(0).
+ * Application (edfa_apply): z = P^{-1} r with P^{-1} of Eq. (EDFA_prec).
+ * Solve (edfa_solve): right-preconditioned flexible GMRES(m), x0 = 0, stopping
+ * at ||b - A x||_2 / ||b||_2 <= rtol (the stopping rule of Sec. 4).
+ *
+ * Conventions shared by every entry point
+ *  - Every pointer inside edfa_csr and every vector argument is DEVICE memory
+ *    on the current CUDA device, owned by the caller.  The handle keeps
+ *    non-owning references to A, B, C, D until edfa_free: keep them alive and
+ *    unchanged (D may be replaced through edfa_setup).
+ *  - The handle owns everything it computes (restriction sets, X~, G~, H~,
+ *    S~, factors, Krylov workspace) and releases it in edfa_free.
+ *  - CSR: int64 row pointers (nrows+1 entries, rowptr[0] = 0, non-decreasing),
+ *    int32 column indices ascending and unique within a row, FP64 values.
+ *    Sizes must fit int32 (N_f + N_e < 2^31).
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  The calls synchronise `stream` where stated (sizing of ragged
+ *    outputs in edfa_build, the convergence test of edfa_solve); edfa_apply
+ *    never synchronises.
+ *  - Every call returns EDFA_OK (0) or an error code; no C++ exception
+ *    crosses the ABI.  edfa_strerror gives a static message;
+ *    edfa_last_error_detail gives the offending row/cell of the last failure
+ *    on the calling thread (or -1).
+ */
+#ifndef EDFA_H
+#define EDFA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define EDFA_API __attribute__((visibility("default")))
+#else
+#define EDFA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* edfa_stream;
+
+enum {
+    EDFA_OK = 0,
+    EDFA_ERR_INVALID = 1,       /* bad sizes, pattern, option or non-finite value */
+    EDFA_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    EDFA_ERR_OOM = 3,           /* device allocation failed */
+    EDFA_ERR_BREAKDOWN = 4,     /* zero/negative local pivot or zero ILU(0) pivot */
+    EDFA_ERR_NOT_CONVERGED = 5, /* FGMRES reached maxit */
+    EDFA_ERR_TIMEOUT = 6,       /* a bounded device wait ran out */
+    EDFA_ERR_BOUNDS = 7,        /* a ragged set exceeded a fixed device capacity */
+    EDFA_ERR_UNSUPPORTED = 8    /* combination of options not implemented */
+};
+
+typedef struct {
+    int32_t nrows, ncols;
+    int64_t nnz;
+    const int64_t* rowptr; /* device [nrows+1] */
+    const int32_t* col;    /* device [nnz] */
+    const double* val;     /* device [nnz] */
+} edfa_csr;
+
+/* Restriction-set builders (Sec. 3, static and dynamic techniques). */
+enum {
+    EDFA_Q_OWN = 0,     /* F_m: the faces of cell m (stored rows of column m of B) */
+    EDFA_Q_NBR = 1,     /* F_m plus the faces of every cell sharing a face with m */
+    EDFA_Q_CROW = 2,    /* stored columns of row m of C (the base pattern Q_{A_ppi}) */
+    EDFA_Q_THRESH = 3,  /* F_m plus j with |A_ij| >= thresh |A_ii| for some i in F_m */
+    EDFA_Q_DYNAMIC = 4, /* Algorithm 1 dynamic branch from Q_{A_ppi}: n_add, n_ent, it_max */
+    EDFA_Q_GIVEN = 5    /* caller-supplied qptr/qidx (device, ascending per cell) */
+};
+
+typedef struct {
+    int32_t qmode;
+    double thresh;          /* EDFA_Q_THRESH */
+    int32_t n_add, n_ent, it_max; /* EDFA_Q_DYNAMIC */
+    const int64_t* qptr;    /* EDFA_Q_GIVEN: device [N_e+1] */
+    const int32_t* qidx;    /* EDFA_Q_GIVEN: device [qptr[N_e]] */
+    int32_t schur_form;     /* 0: S~ = D - C X~ ; 1: S~ = D - G~ A F~ (Eq. sparse_S) */
+    int32_t variant;        /* 0: full block LDU of Eq. (EDFA_prec); 1: upper block triangular */
+    int32_t precision;      /* 0: FP64 throughout; 1: FP32 local solves, S~, factors and
+                               application, FP64 Krylov vectors, Arnoldi and true residual */
+    int32_t warps_per_block;/* local-solve launch shape; 0 = default */
+    int32_t sweep_warps_per_sm; /* resident warps per SM of the sync-free ILU(0) sweeps; 0 = default (16) */
+} edfa_options;
+
+typedef struct edfa_handle_s* edfa_handle;
+
+typedef struct {
+    int32_t iterations;   /* total inner FGMRES iterations */
+    int32_t converged;    /* 1 if the true residual met rtol */
+    int32_t restarts;
+    double est_rel;       /* last Arnoldi estimate |g_{j+1}| / ||b|| */
+    double true_rel;      /* ||b - A x|| / ||b|| at exit */
+} edfa_solve_info;
+
+/* Per-phase device times of the last build/setup/solve (CUDA events on the stream). */
+typedef struct {
+    float ms_qsets, ms_local, ms_schur, ms_ilu_a;  /* Stage 1 */
+    float ms_stage2;                               /* S~ = D - H~ and ILU(0) of S~ */
+    float ms_solve;                                /* last edfa_solve */
+    int64_t n_local;                               /* number of local systems solved */
+    int64_t q_total;                               /* sum of |Q^(m)| */
+    int32_t q_max;                                 /* max |Q^(m)| */
+    int64_t s_nnz;                                 /* nnz of S~ */
+    int32_t levels_a, levels_s;                    /* dependency depth of the ILU(0) sweeps */
+} edfa_stats;
+
+/* Read-only views of what the handle computed (device pointers, valid until
+ * edfa_free; values FP64 unless precision = 1, where the *_f32 fields are set). */
+typedef struct {
+    int32_t Nf, Ne;
+    const int64_t* qptr;  /* [Ne+1] */
+    const int32_t* qidx;  /* [qptr[Ne]] ascending per cell */
+    const double* xval;   /* X~ column m on Q^(m) (FP64 path) */
+    const double* gval;   /* G~ row m on Q^(m) (two-sided form only) */
+    const float* xval_f32;
+    int64_t s_nnz;
+    const int64_t* s_rowptr;
+    const int32_t* s_col;
+    const double* s_val;  /* S~ values (FP64 path) */
+    const float* s_val_f32;
+} edfa_view;
+
+EDFA_API void edfa_default_options(edfa_options* opt);
+
+/* Stage 1 (+ Stage 2 with the given D).  On success *h receives a new handle.
+ * Synchronises `stream` to size the restriction sets and S~. */
+EDFA_API int edfa_build(edfa_handle* h, const edfa_csr* A, const edfa_csr* B, const edfa_csr* C,
+               const edfa_csr* D, const edfa_options* opt, edfa_stream stream);
+
+/* Stage 2 only: new values of D with the SAME pattern as at build time.
+ * Recomputes S~ = D - H~ and its ILU(0).  D must stay alive until the next
+ * edfa_setup or edfa_free. */
+EDFA_API int edfa_setup(edfa_handle h, const edfa_csr* D, edfa_stream stream);
+
+/* z = P^{-1} r, both device vectors of length N_f + N_e (faces first). */
+EDFA_API int edfa_apply(edfa_handle h, const double* r, double* z, edfa_stream stream);
+
+/* y = [A B; C D] x (device vectors of length N_f + N_e). */
+EDFA_API int edfa_matvec(edfa_handle h, const double* x, double* y, edfa_stream stream);
+
+/* FGMRES(restart), x0 = 0; x receives the solution (device, N_f + N_e).
+ * Returns EDFA_ERR_NOT_CONVERGED if maxit inner iterations do not reach rtol
+ * (x then holds the last iterate).  info may be NULL. */
+EDFA_API int edfa_solve(edfa_handle h, const double* b, double* x, int32_t restart, double rtol,
+               int32_t maxit, edfa_solve_info* info, edfa_stream stream);
+
+/* Residual-estimate history of the last edfa_solve (host array of
+ * iterations+1 entries, hist[0] = 1); returns the number written. */
+EDFA_API int32_t edfa_history(edfa_handle h, double* hist, int32_t cap);
+
+EDFA_API int edfa_get_view(edfa_handle h, edfa_view* v);
+EDFA_API int edfa_get_stats(edfa_handle h, edfa_stats* s);
+
+EDFA_API int edfa_free(edfa_handle h);
+
+EDFA_API const char* edfa_strerror(int code);
+EDFA_API int64_t edfa_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EDFA_H */

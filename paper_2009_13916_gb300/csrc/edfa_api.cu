@@ -1,0 +1,423 @@
+// C ABI of libedfa.so: handle lifecycle, Stage 1 / Stage 2 orchestration
+// (Algorithms 1 and 2), the preconditioner application and the outer flexible
+// GMRES driver.  See include/edfa.h for argument meaning, layout, ownership and
+// error behaviour.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+using namespace edfa;
+
+static thread_local long long g_detail = -1;
+
+namespace edfa {
+
+void set_detail(long long d) { g_detail = d; }
+
+int dalloc(edfa_handle_s* h, void** p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void* q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return EDFA_ERR_OOM;
+    }
+    h->owned.push_back(DBuf{q, bytes});
+    *p = q;
+    return EDFA_OK;
+}
+
+int check_err(edfa_handle_s* h, cudaStream_t s)
+{
+    cudaMemcpyAsync(h->err_host, h->err, sizeof(DevErr), cudaMemcpyDeviceToHost, s);
+    cudaError_t ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) {
+        fprintf(stderr, "edfa: CUDA error %s\n", cudaGetErrorString(ce));
+        return EDFA_ERR_CUDA;
+    }
+    if (h->err_host->code != 0) {
+        int code = h->err_host->code;
+        set_detail(h->err_host->detail);
+        cudaMemsetAsync(h->err, 0, sizeof(DevErr), s);
+        cudaStreamSynchronize(s);
+        h->err_host->code = 0;
+        return code;
+    }
+    return EDFA_OK;
+}
+
+}  // namespace edfa
+
+static void free_all(edfa_handle_s* h)
+{
+    if (!h) return;
+    for (auto& b : h->owned) cudaFree(b.p);
+    h->owned.clear();
+    if (h->err_host) cudaFreeHost(h->err_host);
+    if (h->hbuf_host) cudaFreeHost(h->hbuf_host);
+    for (auto& e : h->ev)
+        if (e) cudaEventDestroy(e);
+    delete h;
+}
+
+static bool csr_shape_ok(const edfa_csr* M, int32_t r, int32_t c)
+{
+    return M && M->nrows == r && M->ncols == c && M->nnz >= 0;
+}
+
+extern "C" {
+
+void edfa_default_options(edfa_options* o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->qmode = EDFA_Q_OWN;
+    o->thresh = 0.05;
+    o->n_add = 1;
+    o->n_ent = 4;
+    o->it_max = 100;
+    o->schur_form = 0;
+    o->variant = 0;
+    o->precision = 0;
+    o->warps_per_block = 0;
+}
+
+const char* edfa_strerror(int code)
+{
+    switch (code) {
+    case EDFA_OK: return "ok";
+    case EDFA_ERR_INVALID: return "invalid argument (sizes, pattern, option or non-finite value)";
+    case EDFA_ERR_CUDA: return "CUDA runtime error";
+    case EDFA_ERR_OOM: return "device allocation failed";
+    case EDFA_ERR_BREAKDOWN: return "zero or wrong-signed pivot (local solve or ILU(0))";
+    case EDFA_ERR_NOT_CONVERGED: return "FGMRES did not converge within maxit";
+    case EDFA_ERR_TIMEOUT: return "bounded device wait timed out";
+    case EDFA_ERR_BOUNDS: return "ragged set exceeds a fixed device capacity";
+    case EDFA_ERR_UNSUPPORTED: return "option combination not supported";
+    default: return "unknown error";
+    }
+}
+
+int64_t edfa_last_error_detail(void) { return g_detail; }
+
+#define TRY(x)                                   \
+    do {                                         \
+        int _rc = (x);                           \
+        if (_rc != EDFA_OK) { free_all(h); return _rc; } \
+    } while (0)
+
+int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edfa_csr* C, const edfa_csr* D,
+               const edfa_options* opt, edfa_stream stream)
+{
+    g_detail = -1;
+    if (!out || !A || !B || !C || !D) return EDFA_ERR_INVALID;
+    *out = nullptr;
+    const int32_t Nf = A->nrows, Ne = D->nrows;
+    if (Nf < 0 || Ne < 0 || (int64_t)Nf + Ne >= INT32_MAX) return EDFA_ERR_INVALID;
+    if (!csr_shape_ok(A, Nf, Nf) || !csr_shape_ok(B, Nf, Ne) || !csr_shape_ok(C, Ne, Nf) || !csr_shape_ok(D, Ne, Ne))
+        return EDFA_ERR_INVALID;
+    edfa_options o;
+    if (opt) o = *opt; else edfa_default_options(&o);
+    if (o.qmode < EDFA_Q_OWN || o.qmode > EDFA_Q_GIVEN) return EDFA_ERR_INVALID;
+    if (o.qmode == EDFA_Q_GIVEN && (!o.qptr || !o.qidx)) return EDFA_ERR_INVALID;
+    if (o.qmode == EDFA_Q_THRESH && !(o.thresh >= 0.0)) return EDFA_ERR_INVALID;
+    if (o.qmode == EDFA_Q_DYNAMIC && (o.n_add < 0 || o.n_ent < 0 || o.it_max < 0)) return EDFA_ERR_INVALID;
+    if (o.schur_form < 0 || o.schur_form > 1 || o.variant < 0 || o.variant > 1 || o.precision < 0 ||
+        o.precision > 1)
+        return EDFA_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    edfa_handle_s* h = new (std::nothrow) edfa_handle_s();
+    if (!h) return EDFA_ERR_OOM;
+    h->opt = o;
+    h->Nf = Nf;
+    h->Ne = Ne;
+    h->A = *A;
+    h->B = *B;
+    h->C = *C;
+    h->D = *D;
+    if (cudaGetDevice(&h->device) != cudaSuccess) { free_all(h); return EDFA_ERR_CUDA; }
+    cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device);
+    if (h->nsm < 1) h->nsm = 1;
+    TRY(dalloc_t(h, &h->err, 1));
+    if (cudaMallocHost((void**)&h->err_host, sizeof(DevErr)) != cudaSuccess) { free_all(h); return EDFA_ERR_OOM; }
+    memset(h->err_host, 0, sizeof(DevErr));
+    cudaMemsetAsync(h->err, 0, sizeof(DevErr), s);
+    TRY(dalloc_t(h, &h->ticket, 1));
+    const int32_t nmax = Nf > Ne ? Nf : Ne;
+    TRY(dalloc_t(h, &h->flags, (size_t)(nmax > 0 ? nmax : 1)));
+    cudaMemsetAsync(h->flags, 0, (size_t)(nmax > 0 ? nmax : 1) * sizeof(int), s);
+    for (auto& e : h->ev) cudaEventCreate(&e);
+
+    // inputs
+    TRY(launch_validate(h, *A, 1, s));
+    TRY(launch_validate(h, *B, 0, s));
+    TRY(launch_validate(h, *C, 0, s));
+    TRY(launch_validate(h, *D, 0, s));
+    TRY(check_err(h, s));
+    if (o.precision == 1) {
+        TRY(dalloc_t(h, &h->a32, (size_t)(A->nnz > 0 ? A->nnz : 1)));
+        TRY(dalloc_t(h, &h->b32, (size_t)(B->nnz > 0 ? B->nnz : 1)));
+        TRY(dalloc_t(h, &h->c32, (size_t)(C->nnz > 0 ? C->nnz : 1)));
+        TRY(to_f32(A->val, h->a32, A->nnz, s));
+        TRY(to_f32(B->val, h->b32, B->nnz, s));
+        TRY(to_f32(C->val, h->c32, C->nnz, s));
+    }
+
+    // Stage 1 (Algorithm 1)
+    cudaEventRecord(h->ev[0], s);
+    TRY(build_bt(h, s));
+    if (o.qmode == EDFA_Q_DYNAMIC) TRY(build_qsets_dynamic(h, s));
+    else TRY(build_qsets(h, s));
+    cudaEventRecord(h->ev[1], s);
+    TRY(run_local_solves(h, s));
+    cudaEventRecord(h->ev[2], s);
+    TRY(check_err(h, s));
+    cudaEventRecord(h->ev[3], s);
+    TRY(build_schur(h, s));
+    cudaEventRecord(h->ev[4], s);
+    TRY(factor_plan(h, h->fa, Nf, A->nnz, A->rowptr, A->col, s));
+    TRY(factor_numeric(h, h->fa, A->val, h->a32, s));
+    cudaEventRecord(h->ev[5], s);
+    TRY(check_err(h, s));
+
+    // Stage 2 (Algorithm 2) with the given D
+    cudaEventRecord(h->ev[6], s);
+    TRY(stage2_values(h, s));
+    TRY(factor_plan(h, h->fs, Ne, h->s_nnz, h->s_ptr, h->s_col, s));
+    TRY(factor_numeric(h, h->fs, h->s_val, h->s_val32, s));
+    cudaEventRecord(h->ev[7], s);
+
+    // application temporaries
+    const size_t esz = o.precision == 1 ? sizeof(float) : sizeof(double);
+    TRY(dalloc(h, &h->tmp1, (size_t)(nmax > 0 ? nmax : 1) * esz));
+    TRY(dalloc(h, &h->tmp2, (size_t)(nmax > 0 ? nmax : 1) * esz));
+    TRY(dalloc(h, &h->tmp3, (size_t)(nmax > 0 ? nmax : 1) * esz));
+    TRY(check_err(h, s));
+
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]); h->stats.ms_qsets = ms;
+    cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]); h->stats.ms_local = ms;
+    cudaEventElapsedTime(&ms, h->ev[3], h->ev[4]); h->stats.ms_schur = ms;
+    cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]); h->stats.ms_ilu_a = ms;
+    cudaEventElapsedTime(&ms, h->ev[6], h->ev[7]); h->stats.ms_stage2 = ms;
+    h->stats.n_local = Ne;
+    h->stats.q_total = h->qtot;
+    h->stats.q_max = h->qmax;
+    h->stats.s_nnz = h->s_nnz;
+    h->stats.levels_a = h->fa.fwd.nlevels;
+    h->stats.levels_s = h->fs.fwd.nlevels;
+    *out = h;
+    return EDFA_OK;
+}
+
+#undef TRY
+
+int edfa_setup(edfa_handle h, const edfa_csr* D, edfa_stream stream)
+{
+    g_detail = -1;
+    if (!h || !D) return EDFA_ERR_INVALID;
+    if (D->nrows != h->Ne || D->ncols != h->Ne || D->nnz != h->D.nnz) return EDFA_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = launch_validate(h, *D, 0, s);
+    if (!rc) rc = check_err(h, s);
+    if (rc) return rc;
+    h->D = *D;
+    cudaEventRecord(h->ev[6], s);
+    rc = stage2_values(h, s);
+    if (!rc) rc = factor_numeric(h, h->fs, h->s_val, h->s_val32, s);
+    cudaEventRecord(h->ev[7], s);
+    if (!rc) rc = check_err(h, s);
+    if (rc) return rc;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[6], h->ev[7]);
+    h->stats.ms_stage2 = ms;
+    return EDFA_OK;
+}
+
+int edfa_apply(edfa_handle h, const double* r, double* z, edfa_stream stream)
+{
+    if (!h || (!r && h->Nf + h->Ne > 0) || (!z && h->Nf + h->Ne > 0)) return EDFA_ERR_INVALID;
+    return apply_prec(h, r, z, (cudaStream_t)stream);
+}
+
+int edfa_matvec(edfa_handle h, const double* x, double* y, edfa_stream stream)
+{
+    if (!h || (!x && h->Nf + h->Ne > 0) || (!y && h->Nf + h->Ne > 0)) return EDFA_ERR_INVALID;
+    return matvec(h, x, y, (cudaStream_t)stream);
+}
+
+// Right-preconditioned flexible GMRES(m) (Saad, Alg. 9.6): Arnoldi with
+// classical Gram-Schmidt applied twice (CGS2) in FP64 on the device, the
+// (m+1) x m Hessenberg least-squares problem by Givens rotations on the host
+// (one (j+2)-value device->host read per inner iteration), x0 = 0, and the
+// true residual ||b - A x|| checked at the end of every cycle; the outer loop
+// restarts while it exceeds rtol ||b||.
+int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol, int32_t maxit,
+               edfa_solve_info* info, edfa_stream stream)
+{
+    g_detail = -1;
+    if (!h || m < 1 || m > 126 || !(rtol >= 0.0) || maxit < 0) return EDFA_ERR_INVALID;
+    const int64_t n = (int64_t)h->Nf + h->Ne;
+    if (n > 0 && (!b || !x)) return EDFA_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->kry_m < m) {
+        // (re)allocate workspace; previous buffers stay owned until edfa_free
+        if (dalloc_t(h, &h->V, (size_t)(m + 1) * n) || dalloc_t(h, &h->Z, (size_t)m * n) ||
+            dalloc_t(h, &h->w, (size_t)(n > 0 ? n : 1)) || dalloc_t(h, &h->part, (size_t)kry_part_size(n, m + 1)) ||
+            dalloc_t(h, &h->hbuf, (size_t)4 * (m + 2)))
+            return EDFA_ERR_OOM;
+        if (h->hbuf_host) cudaFreeHost(h->hbuf_host);
+        if (cudaMallocHost((void**)&h->hbuf_host, sizeof(double) * 4 * (m + 2)) != cudaSuccess) return EDFA_ERR_OOM;
+        h->kry_m = m;
+    }
+    double* h1 = h->hbuf;
+    double* h2 = h->hbuf + (m + 2);
+    double* hf = h->hbuf + 2 * (m + 2);
+    double* misc = h->hbuf + 3 * (m + 2);  // [0] = squared norm, [1] = norm
+    double* hh = h->hbuf_host;
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
+    h->hist.assign(1, 1.0);
+    edfa_solve_info loc{};
+    cudaEventRecord(h->ev[0], s);
+
+    int rc = EDFA_OK;
+    // ||b||
+    rc = kry_multidot(h->V, n, 0, b, n, h->part, misc, nullptr, nullptr, 1, s);
+    if (rc) return rc;
+    cudaMemcpyAsync(hh, misc, sizeof(double), cudaMemcpyDeviceToHost, s);
+    rc = check_err(h, s);
+    if (rc) return rc;
+    const double bnorm = std::sqrt(hh[0]);
+    cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), s);
+    if (bnorm == 0.0 || n == 0) {
+        loc.converged = 1;
+        if (info) *info = loc;
+        return check_err(h, s);
+    }
+    cudaMemcpyAsync(h->w, b, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    double beta = bnorm;
+    int it = 0, status = EDFA_ERR_NOT_CONVERGED;
+    while (it < maxit) {
+        rc = kry_scale_const(h->w, h->V, n, 1.0 / beta, s);
+        if (rc) return rc;
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int jlast = -1;
+        for (int j = 0; j < m && it < maxit; ++j) {
+            double* vj = h->V + (int64_t)j * n;
+            double* zj = h->Z + (int64_t)j * n;
+            if ((rc = apply_prec(h, vj, zj, s))) return rc;
+            if ((rc = matvec(h, zj, h->w, s))) return rc;
+            const int nv = j + 1;
+            if ((rc = kry_multidot(h->V, n, nv, h->w, n, h->part, h1, nullptr, nullptr, 0, s))) return rc;
+            if ((rc = kry_update(h->V, n, nv, h1, h->w, n, h->part, nullptr, s))) return rc;
+            if ((rc = kry_multidot(h->V, n, nv, h->w, n, h->part, h2, h1, hf, 0, s))) return rc;
+            if ((rc = kry_update(h->V, n, nv, h2, h->w, n, h->part, misc, s))) return rc;
+            if ((rc = kry_scale_from(h->w, h->V + (int64_t)(j + 1) * n, n, misc, hf + nv, s))) return rc;
+            cudaMemcpyAsync(hh, hf, sizeof(double) * (nv + 1), cudaMemcpyDeviceToHost, s);
+            if ((rc = check_err(h, s))) return rc;
+            for (int i = 0; i <= j + 1; ++i) H[(size_t)i * m + j] = hh[i];
+            for (int i = 0; i < j; ++i) {
+                double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+            }
+            double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+            double den = std::sqrt(a * a + c * c);
+            cs[j] = den > 0 ? a / den : 1.0;
+            sn[j] = den > 0 ? c / den : 0.0;
+            H[(size_t)j * m + j] = den;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++it;
+            jlast = j;
+            const double est = std::fabs(g[j + 1]) / bnorm;
+            h->hist.push_back(est);
+            loc.est_rel = est;
+            if (est <= rtol || hh[j + 1] == 0.0) break;
+        }
+        const int k = jlast + 1;
+        for (int i = k - 1; i >= 0; --i) {
+            double v = g[i];
+            for (int l = i + 1; l < k; ++l) v -= H[(size_t)i * m + l] * y[l];
+            y[i] = H[(size_t)i * m + i] != 0.0 ? v / H[(size_t)i * m + i] : 0.0;
+        }
+        memcpy(hh, y.data(), sizeof(double) * k);
+        cudaMemcpyAsync(h1, hh, sizeof(double) * k, cudaMemcpyHostToDevice, s);
+        if ((rc = kry_combine(h->Z, n, k, h1, x, n, s))) return rc;
+        if ((rc = matvec(h, x, h->w, s))) return rc;
+        if ((rc = kry_residual(b, h->w, n, h->part, misc, s))) return rc;
+        cudaMemcpyAsync(hh, misc, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if ((rc = check_err(h, s))) return rc;
+        beta = std::sqrt(hh[0]);
+        loc.true_rel = beta / bnorm;
+        if (loc.true_rel <= rtol) { status = EDFA_OK; break; }
+        if (beta == 0.0) { status = EDFA_OK; break; }
+        loc.restarts++;
+    }
+    cudaEventRecord(h->ev[1], s);
+    cudaEventSynchronize(h->ev[1]);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+    h->stats.ms_solve = ms;
+    loc.iterations = it;
+    loc.converged = status == EDFA_OK;
+    if (info) *info = loc;
+    return status;
+}
+
+int32_t edfa_history(edfa_handle h, double* hist, int32_t cap)
+{
+    if (!h || !hist || cap <= 0) return 0;
+    int32_t n = (int32_t)h->hist.size();
+    if (n > cap) n = cap;
+    memcpy(hist, h->hist.data(), sizeof(double) * n);
+    return n;
+}
+
+int edfa_get_view(edfa_handle h, edfa_view* v)
+{
+    if (!h || !v) return EDFA_ERR_INVALID;
+    v->Nf = h->Nf;
+    v->Ne = h->Ne;
+    v->qptr = h->qptr;
+    v->qidx = h->qidx;
+    v->xval = h->xval;
+    v->gval = h->gval;
+    v->xval_f32 = h->xval32;
+    v->s_nnz = h->s_nnz;
+    v->s_rowptr = h->s_ptr;
+    v->s_col = h->s_col;
+    v->s_val = h->s_val;
+    v->s_val_f32 = h->s_val32;
+    return EDFA_OK;
+}
+
+int edfa_get_stats(edfa_handle h, edfa_stats* st)
+{
+    if (!h || !st) return EDFA_ERR_INVALID;
+    *st = h->stats;
+    return EDFA_OK;
+}
+
+int edfa_free(edfa_handle h)
+{
+    if (!h) return EDFA_ERR_INVALID;
+    cudaDeviceSynchronize();
+    free_all(h);
+    return EDFA_OK;
+}
+
+}  // extern "C"
+
+// dynamic restriction sets are provided by k_dynamic.cu when built; until then
+// the option is rejected.
+namespace edfa {
+__attribute__((weak)) int build_qsets_dynamic(edfa_handle_s*, cudaStream_t) { return EDFA_ERR_UNSUPPORTED; }
+}  // namespace edfa

@@ -1,0 +1,217 @@
+// Internal declarations shared by the translation units of libedfa.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "edfa.h"
+
+namespace edfa {
+
+// ------------------------------------------------------------------ errors
+// Device-side error record: the first failing thread wins the code; the detail
+// (row/cell index) is written by the same thread.  Read by the host after a
+// synchronisation point.
+struct DevErr {
+    int code;
+    int pad;
+    long long detail;
+};
+
+__device__ __forceinline__ void raise_err(DevErr* e, int code, long long detail)
+{
+    if (atomicCAS(&e->code, 0, code) == 0) e->detail = detail;
+}
+
+// Bounded spin budget for cross-warp waits (polling with nanosleep): about
+// 2^20 polls of >= 20 ns, i.e. the wait gives up after some tens of ms,
+// records EDFA_ERR_TIMEOUT and lets the kernel finish.  Every wait also gives
+// up as soon as any thread has recorded an error, so a failure ends the whole
+// kernel within one wait period.
+constexpr unsigned kSpinLimit = 1u << 20;
+
+__device__ __forceinline__ bool err_set(const DevErr* e)
+{
+    return *(volatile const int*)&e->code != 0;
+}
+
+// acquire load of a completion flag written by another SM
+__device__ __forceinline__ int ld_acquire(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Polling back-off: the sleep between polls doubles from 32 ns up to 256 ns,
+// which keeps thousands of waiting warps from flooding L2 with polls.
+constexpr unsigned kBackoffMin = 32, kBackoffMax = 256;
+
+// wait until *flag == epoch; returns false (and raises) on timeout
+__device__ __forceinline__ bool wait_flag(const int* flag, int epoch, DevErr* err, long long who)
+{
+    if (ld_acquire(flag) == epoch) return true;
+    unsigned ns = kBackoffMin;
+    for (unsigned it = 0; it < kSpinLimit; ++it) {
+        __nanosleep(ns);
+        if (ns < kBackoffMax) ns <<= 1;
+        if (ld_acquire(flag) == epoch) return true;
+        if ((it & 255u) == 255u && err_set(err)) return false;
+    }
+    raise_err(err, EDFA_ERR_TIMEOUT, who);
+    return false;
+}
+
+template <class T>
+__device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
+
+// ------------------------------------------------------------------ CSR
+template <class T>
+struct Csr {
+    int32_t nrows, ncols;
+    int64_t nnz;
+    const int64_t* rowptr;
+    const int32_t* col;
+    const T* val;
+};
+
+inline Csr<double> csr_of(const edfa_csr& m)
+{
+    return Csr<double>{m.nrows, m.ncols, m.nnz, m.rowptr, m.col, m.val};
+}
+
+// --------------------------------------------------------- device buffers
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// ------------------------------------------------------------- sweeps
+// A level-ordered triangular-sweep plan over a CSR pattern: rows grouped by
+// dependency level (forward: on smaller columns, backward: on larger ones),
+// each level padded with -1 to a multiple of 32 so that a warp never holds two
+// rows of different levels.
+struct SweepPlan {
+    int32_t* perm = nullptr;  // [nslots]
+    int64_t nslots = 0;
+    int32_t nlevels = 0;
+};
+
+struct Factor {
+    // pattern (not owned unless owned_pattern)
+    int32_t n = 0;
+    int64_t nnz = 0;
+    const int64_t* rowptr = nullptr;
+    const int32_t* col = nullptr;
+    int64_t* diag = nullptr;   // [n] position of the diagonal
+    double* lu64 = nullptr;    // factor values (FP64 path)
+    float* lu32 = nullptr;     // factor values (FP32 path)
+    double* dinv64 = nullptr;  // 1 / U_ii
+    float* dinv32 = nullptr;
+    SweepPlan fwd, bwd;
+};
+
+}  // namespace edfa
+
+struct edfa_handle_s {
+    int device = 0;
+    int nsm = 0;
+    edfa_options opt{};
+    int32_t Nf = 0, Ne = 0;
+    edfa_csr A{}, B{}, C{}, D{};
+    // FP32 copies of the block values (precision 1)
+    float *a32 = nullptr, *b32 = nullptr, *c32 = nullptr, *d32 = nullptr;
+    // B^T pattern: faces of each cell
+    int64_t* bt_ptr = nullptr;
+    int32_t* bt_col = nullptr;
+    // restriction sets
+    int64_t* qptr = nullptr;
+    int32_t* qidx = nullptr;
+    int64_t qtot = 0;
+    int32_t qmax = 0;
+    double *xval = nullptr, *gval = nullptr;
+    float *xval32 = nullptr, *gval32 = nullptr;
+    // X~ rows: cells whose set holds each face
+    int64_t* xr_ptr = nullptr;
+    int32_t* xr_cell = nullptr;
+    // S~ = D - H~
+    int64_t s_nnz = 0;
+    int64_t* s_ptr = nullptr;
+    int32_t* s_col = nullptr;
+    double *h_val = nullptr, *s_val = nullptr;
+    float *h_val32 = nullptr, *s_val32 = nullptr;
+    int64_t* d_map = nullptr;  // position of each D entry in S~
+    // ILU(0) factors
+    edfa::Factor fa, fs;
+    // sweep synchronisation
+    int* flags = nullptr;          // [max(Nf, Ne)] completion epochs
+    unsigned long long* ticket = nullptr;  // work counter, zeroed before every sync-free launch
+    int epoch = 0;
+    // apply temporaries (length Nf + Ne) in the working precision
+    void* tmp1 = nullptr;
+    void* tmp2 = nullptr;
+    void* tmp3 = nullptr;
+    // Krylov workspace
+    int32_t kry_m = 0;
+    double *V = nullptr, *Z = nullptr, *w = nullptr, *part = nullptr, *hbuf = nullptr;
+    double* hbuf_host = nullptr;  // pinned
+    // device error record and its pinned host mirror
+    edfa::DevErr* err = nullptr;
+    edfa::DevErr* err_host = nullptr;
+    cudaEvent_t ev[8] = {};
+    edfa_stats stats{};
+    std::vector<double> hist;
+    std::vector<edfa::DBuf> owned;  // every device allocation, released by edfa_free
+};
+
+namespace edfa {
+
+// allocation helpers (record into h->owned)
+int dalloc(edfa_handle_s* h, void** p, size_t bytes);
+template <class T>
+int dalloc_t(edfa_handle_s* h, T** p, size_t count)
+{
+    return dalloc(h, (void**)p, count * sizeof(T));
+}
+int check_err(edfa_handle_s* h, cudaStream_t s);  // sync + read device error record
+void set_detail(long long d);
+
+// exclusive scan of int64 counts in place: out[i] = sum_{j<i} in[j]; out[n] = total.
+int scan_i64(edfa_handle_s* h, int64_t* data, int64_t n, cudaStream_t s);
+
+// launchers (return EDFA_* codes, enqueue only)
+int launch_validate(edfa_handle_s* h, const edfa_csr& M, int need_diag, cudaStream_t s);
+int build_bt(edfa_handle_s* h, cudaStream_t s);
+int build_qsets(edfa_handle_s* h, cudaStream_t s);
+int build_qsets_dynamic(edfa_handle_s* h, cudaStream_t s);
+int run_local_solves(edfa_handle_s* h, cudaStream_t s);
+int build_schur(edfa_handle_s* h, cudaStream_t s);
+int stage2_values(edfa_handle_s* h, cudaStream_t s);
+int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64_t* rowptr,
+                const int32_t* col, cudaStream_t s);
+int factor_numeric(edfa_handle_s* h, Factor& f, const double* vals64, const float* vals32,
+                   cudaStream_t s);
+int apply_prec(edfa_handle_s* h, const double* r, double* z, cudaStream_t s);
+int matvec(edfa_handle_s* h, const double* x, double* y, cudaStream_t s);
+int to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
+int to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t s);
+
+// Krylov building blocks (k_krylov.cu)
+int kry_multidot(const double* V, int64_t ld, int nv, const double* w, int64_t n, double* part, double* out,
+                 const double* add, double* out_sum, int with_self, cudaStream_t s);
+int kry_update(const double* V, int64_t ld, int nv, const double* hcoef, double* w, int64_t n, double* part,
+               double* nrm2_out, cudaStream_t s);
+int kry_scale_from(const double* w, double* v, int64_t n, const double* nrm2, double* out_norm, cudaStream_t s);
+int kry_scale_const(const double* w, double* v, int64_t n, double alpha, cudaStream_t s);
+int kry_combine(const double* Z, int64_t ld, int k, const double* y, double* x, int64_t n, cudaStream_t s);
+int kry_residual(const double* b, double* r, int64_t n, double* part, double* nrm2_out, cudaStream_t s);
+int64_t kry_part_size(int64_t n, int nvmax);
+
+}  // namespace edfa

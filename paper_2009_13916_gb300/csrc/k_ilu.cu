@@ -1,0 +1,625 @@
+// ILU(0) in the natural ordering (the inner preconditioners standing for
+// A~^{-1} and S~^{-1} in Eq. (EDFA_prec)) and its triangular sweeps.
+//
+// Design (GB300): the dependency depth of a natural-order sweep is fixed by
+// the pattern (193 levels for the 64^3 face block, ~700 for S~), so the
+// sweeps are latency-bound.  Every kernel here is sync-free: rows are handed
+// out in dependency-level order through a global ticket, and a row waits only
+// for the rows it reads.  The sweeps poll the result values themselves (the
+// output vector is pre-filled with an all-ones NaN that no arithmetic
+// produces), so one L2 round trip resolves a dependency.  Rows of one level are
+// padded to whole warps so that no warp ever waits on itself.
+//
+// Every wait is bounded (kSpinLimit polls); on timeout the kernel records
+// EDFA_ERR_TIMEOUT and finishes.
+#include <climits>
+
+#include "internal.cuh"
+
+namespace edfa {
+
+constexpr int kFacWarps = 4;
+constexpr unsigned kSweepBackoffMax = 64;
+constexpr int kSweepThreads = 64;
+
+// next c work items for this warp (the counter is zeroed before each launch)
+__device__ __forceinline__ long long claim(unsigned long long* ticket, int c)
+{
+    unsigned long long v = 0;
+    if ((threadIdx.x & 31) == 0) v = atomicAdd(ticket, (unsigned long long)c);
+    v = __shfl_sync(0xffffffffu, v, 0);
+    return (long long)v;
+}
+
+// ------------------------------------------------------------ levels
+// level(i) = 1 + max level(j) over the stored j < i (fwd) or j > i (bwd); the
+// level array starts at -1 (all-ones bytes) and doubles as the ready flag.
+template <int FWD>
+__global__ void k_levels(int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                         int* level, int* maxlev, unsigned long long* ticket, DevErr* err)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        long long t = claim(ticket, 1);
+        if (t >= n) break;
+        int i = FWD ? (int)t : (int)(n - 1 - t);
+        int64_t b = rowptr[i], e = rowptr[i + 1];
+        int lv = -1;
+        for (int64_t p = b + lane; p < e; p += 32) {
+            int j = col[p];
+            if (FWD ? (j < i) : (j > i)) {
+                int v = ld_acquire(level + j);
+                unsigned it = 0, ns = kBackoffMin;
+                while (v < 0 && it < kSpinLimit) {
+                    __nanosleep(ns);
+                    if (ns < kBackoffMax) ns <<= 1;
+                    v = ld_acquire(level + j);
+                    ++it;
+                    if ((it & 255u) == 0u && err_set(err)) break;
+                }
+                if (v < 0) { raise_err(err, EDFA_ERR_TIMEOUT, i); v = 0; }
+                lv = max(lv, v);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lv = max(lv, __shfl_xor_sync(0xffffffffu, lv, o));
+        if (lane == 0) {
+            st_release(level + i, lv + 1);
+            atomicMax(maxlev, lv + 1);
+        }
+    }
+}
+
+__global__ void k_level_hist(int32_t n, const int* level, unsigned long long* hist)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&hist[level[i]], 1ull);
+}
+
+__global__ void k_level_pad(int32_t nlev, int64_t* hist, int g)
+{
+    int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (l < nlev) hist[l] = (hist[l] + g - 1) / g * g;
+}
+
+__global__ void k_level_scatter(int32_t n, const int* level, const int64_t* off, unsigned long long* cursor,
+                                int32_t* perm)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int l = level[i];
+    unsigned long long k = atomicAdd(&cursor[l], 1ull);
+    perm[off[l] + (int64_t)k] = (int32_t)i;
+}
+
+// grid of a sync-free kernel: at most `warps_per_sm` resident warps per SM
+// (0 = default), never more than the occupancy limit
+static int resident_grid(edfa_handle_s* h, const void* fn, int threads, size_t smem, int warps_per_sm = 0)
+{
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
+    if (per < 1) per = 1;
+    int want = warps_per_sm > 0 ? warps_per_sm : 16;
+    int bl = want * 32 / threads;
+    if (bl < 1) bl = 1;
+    if (bl < per) per = bl;
+    return per * h->nsm;
+}
+
+static int make_plan(edfa_handle_s* h, SweepPlan& plan, int32_t n, const int64_t* rowptr, const int32_t* col,
+                     int fwd, int pad, cudaStream_t s)
+{
+    int* level = nullptr;
+    int* maxlev = nullptr;
+    if (cudaMallocAsync((void**)&level, (size_t)(n > 0 ? n : 1) * sizeof(int), s) != cudaSuccess) return EDFA_ERR_OOM;
+    if (cudaMallocAsync((void**)&maxlev, sizeof(int), s) != cudaSuccess) return EDFA_ERR_OOM;
+    cudaMemsetAsync(level, 0xFF, (size_t)(n > 0 ? n : 1) * sizeof(int), s);
+    cudaMemsetAsync(maxlev, 0, sizeof(int), s);
+    const void* fn = fwd ? (const void*)k_levels<1> : (const void*)k_levels<0>;
+    int grid = resident_grid(h, fn, 256, 0);
+    cudaMemsetAsync(h->ticket, 0, sizeof(unsigned long long), s);
+    if (fwd) k_levels<1><<<grid, 256, 0, s>>>(n, rowptr, col, level, maxlev, h->ticket, h->err);
+    else k_levels<0><<<grid, 256, 0, s>>>(n, rowptr, col, level, maxlev, h->ticket, h->err);
+    int nlev = 0;
+    cudaMemcpyAsync(&nlev, maxlev, sizeof(int), cudaMemcpyDeviceToHost, s);
+    int rc = check_err(h, s);
+    if (rc) return rc;
+    nlev += 1;
+    if (n == 0) nlev = 0;
+    int64_t* off = nullptr;
+    unsigned long long* cursor = nullptr;
+    if (cudaMallocAsync((void**)&off, ((size_t)nlev + 1) * sizeof(int64_t), s) != cudaSuccess) return EDFA_ERR_OOM;
+    if (cudaMallocAsync((void**)&cursor, ((size_t)nlev + 1) * sizeof(int64_t), s) != cudaSuccess) return EDFA_ERR_OOM;
+    cudaMemsetAsync(off, 0, ((size_t)nlev + 1) * sizeof(int64_t), s);
+    cudaMemsetAsync(cursor, 0, ((size_t)nlev + 1) * sizeof(int64_t), s);
+    if (n > 0) k_level_hist<<<(n + 255) / 256, 256, 0, s>>>(n, level, (unsigned long long*)off);
+    if (nlev > 0) k_level_pad<<<(nlev + 255) / 256, 256, 0, s>>>(nlev, off, pad);
+    rc = scan_i64(h, off, nlev, s);
+    if (rc) return rc;
+    int64_t nslots = 0;
+    cudaMemcpyAsync(&nslots, off + nlev, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    rc = dalloc_t(h, &plan.perm, (size_t)(nslots > 0 ? nslots : 1));
+    if (rc) return rc;
+    cudaMemsetAsync(plan.perm, 0xFF, (size_t)(nslots > 0 ? nslots : 1) * sizeof(int32_t), s);
+    if (n > 0) k_level_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, level, off, cursor, plan.perm);
+    plan.nslots = nslots;
+    plan.nlevels = nlev;
+    cudaFreeAsync(off, s);
+    cudaFreeAsync(cursor, s);
+    cudaFreeAsync(level, s);
+    cudaFreeAsync(maxlev, s);
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
+__global__ void k_find_diag(int32_t n, const int64_t* rowptr, const int32_t* col, int64_t* diag, DevErr* err)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t d = -1;
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+        if (col[p] == i) d = p;
+    if (d < 0) raise_err(err, EDFA_ERR_BREAKDOWN, i);
+    diag[i] = d;
+}
+
+int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                cudaStream_t s)
+{
+    f.n = n;
+    f.nnz = nnz;
+    f.rowptr = rowptr;
+    f.col = col;
+    int rc = dalloc_t(h, &f.diag, (size_t)(n > 0 ? n : 1));
+    if (rc) return rc;
+    if (n > 0) k_find_diag<<<(n + 255) / 256, 256, 0, s>>>(n, rowptr, col, f.diag, h->err);
+    rc = make_plan(h, f.fwd, n, rowptr, col, 1, 32, s);
+    if (rc) return rc;
+    rc = make_plan(h, f.bwd, n, rowptr, col, 0, 32, s);
+    if (rc) return rc;
+    const bool f32 = h->opt.precision == 1;
+    if (f32) {
+        rc = dalloc_t(h, &f.lu32, (size_t)(nnz > 0 ? nnz : 1));
+        if (!rc) rc = dalloc_t(h, &f.dinv32, (size_t)(n > 0 ? n : 1));
+    } else {
+        rc = dalloc_t(h, &f.lu64, (size_t)(nnz > 0 ? nnz : 1));
+        if (!rc) rc = dalloc_t(h, &f.dinv64, (size_t)(n > 0 ? n : 1));
+    }
+    return rc;
+}
+
+// ------------------------------------------------------------ factorisation
+// ILU(0), IKJ order (Saad, Alg. 10.4): row i, for each stored k < i in
+// ascending order: l_ik = a_ik / u_kk, then a_ij -= l_ik u_kj for stored
+// j > k present in row k.  One warp per row, rows taken in level order.
+// The warp first waits for all rows it depends on (lanes in parallel), then
+// copies their U parts into shared memory with batched loads, and eliminates
+// from shared memory.  Rows whose data exceed the shared buffers fall back to
+// searching the U parts in global memory.
+constexpr int kFRow = 256;    // row entries held in shared memory
+constexpr int kFU = 1536;     // U-part entries of all dependencies held in shared memory
+
+template <class T>
+struct FacSmem {
+    T rv[kFRow];
+    T dk[kFRow];
+    T uv[kFU];
+    int rc[kFRow];
+    int uo[kFRow + 1];
+    int uc[kFU];
+};
+
+template <class T>
+__global__ void __launch_bounds__(kFacWarps * 32)
+k_ilu0(int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+       const int64_t* __restrict__ diag, const T* __restrict__ vals, T* lu, T* dinv, const int32_t* perm,
+       int64_t nslots, int* flags, int epoch, unsigned long long* ticket, DevErr* err)
+{
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    FacSmem<T>& S = reinterpret_cast<FacSmem<T>*>(fsm_raw)[wid];
+    for (;;) {
+        long long t = claim(ticket, 1);
+        if (t >= nslots) break;
+        int i = perm[t];
+        if (i < 0) continue;
+        const int64_t b = rowptr[i], e = rowptr[i + 1];
+        const int len = (int)(e - b);
+        const int dpos = (int)(diag[i] - b);
+        if (len > kFRow) {
+            if (lane == 0) { raise_err(err, EDFA_ERR_BOUNDS, i); st_release(flags + i, epoch); }
+            continue;
+        }
+        for (int u = lane; u < len; u += 32) { S.rv[u] = vals[b + u]; S.rc[u] = col[b + u]; }
+        __syncwarp();
+        // wait for every dependency (one lane per dependency)
+        for (int u = lane; u < dpos; u += 32) wait_flag(flags + S.rc[u], epoch, err, i);
+        __syncwarp();
+        // sizes of the dependencies' U parts and their dinv
+        int tot = 0;
+        for (int base0 = 0; base0 < dpos; base0 += 32) {
+            int u = base0 + lane;
+            int ul = 0;
+            if (u < dpos) {
+                int k = S.rc[u];
+                int64_t ub = ld_cg(diag + k) + 1;
+                ul = (int)(rowptr[k + 1] - ub);
+                S.dk[u] = ld_cg(dinv + k);
+            }
+            int x = ul;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (u < dpos) S.uo[u] = tot + x - ul;
+            tot += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) S.uo[dpos] = tot;
+        __syncwarp();
+        const bool in_smem = tot <= kFU;
+        if (in_smem) {
+            // flattened copy of all U parts: entry q belongs to dependency u with uo[u] <= q < uo[u+1]
+            for (int q0 = 0; q0 < tot; q0 += 4 * 32) {
+                int cc[4];
+                T vv[4];
+                int qq[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    int q = q0 + r * 32 + lane;
+                    qq[r] = q;
+                    cc[r] = -1;
+                    if (q < tot) {
+                        int lo = 0, hi = dpos - 1;
+                        while (lo < hi) {
+                            int mid = (lo + hi + 1) >> 1;
+                            if (S.uo[mid] <= q) lo = mid; else hi = mid - 1;
+                        }
+                        int k = S.rc[lo];
+                        int64_t src = ld_cg(diag + k) + 1 + (q - S.uo[lo]);
+                        cc[r] = col[src];
+                        vv[r] = ld_cg(lu + src);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (qq[r] < tot) { S.uc[qq[r]] = cc[r]; S.uv[qq[r]] = vv[r]; }
+            }
+            __syncwarp();
+        }
+        for (int tt = 0; tt < dpos; ++tt) {
+            const T lik = S.rv[tt] * S.dk[tt];
+            __syncwarp();
+            if (lane == 0) S.rv[tt] = lik;
+            if (in_smem) {
+                const int ub = S.uo[tt], ue = S.uo[tt + 1];
+                for (int u = tt + 1 + lane; u < len; u += 32) {
+                    int j = S.rc[u];
+                    int lo = ub, hi = ue - 1;
+                    while (lo <= hi) {
+                        int mid = (lo + hi) >> 1;
+                        int cm = S.uc[mid];
+                        if (cm == j) { S.rv[u] -= lik * S.uv[mid]; break; }
+                        if (cm < j) lo = mid + 1; else hi = mid - 1;
+                    }
+                }
+            } else {
+                const int k = S.rc[tt];
+                const int64_t ub = ld_cg(diag + k) + 1, ue = rowptr[k + 1];
+                for (int u = tt + 1 + lane; u < len; u += 32) {
+                    int j = S.rc[u];
+                    int64_t lo = ub, hi = ue - 1;
+                    while (lo <= hi) {
+                        int64_t mid = (lo + hi) >> 1;
+                        int cm = col[mid];
+                        if (cm == j) { S.rv[u] -= lik * ld_cg(lu + mid); break; }
+                        if (cm < j) lo = mid + 1; else hi = mid - 1;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        const T piv = S.rv[dpos];
+        for (int u = lane; u < len; u += 32) lu[b + u] = S.rv[u];
+        if (lane == 0) {
+            if (!(piv != T(0)) || !isfinite((double)piv)) raise_err(err, EDFA_ERR_BREAKDOWN, i);
+            dinv[i] = T(1) / piv;
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release(flags + i, epoch);
+        __syncwarp();
+    }
+}
+
+int factor_numeric(edfa_handle_s* h, Factor& f, const double* vals64, const float* vals32, cudaStream_t s)
+{
+    if (f.n == 0) return EDFA_OK;
+    h->epoch += 1;
+    if (h->epoch == INT_MAX) {
+        h->epoch = 1;
+        int32_t nmax = h->Nf > h->Ne ? h->Nf : h->Ne;
+        cudaMemsetAsync(h->flags, 0, (size_t)nmax * sizeof(int), s);
+    }
+    cudaMemsetAsync(h->ticket, 0, sizeof(unsigned long long), s);
+    if (h->opt.precision == 1) {
+        size_t smem = sizeof(FacSmem<float>) * kFacWarps;
+        cudaFuncSetAttribute(k_ilu0<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int grid = resident_grid(h, (const void*)k_ilu0<float>, kFacWarps * 32, smem, 32);
+        k_ilu0<float><<<grid, kFacWarps * 32, smem, s>>>(f.n, f.rowptr, f.col, f.diag, vals32, f.lu32, f.dinv32,
+                                                          f.fwd.perm, f.fwd.nslots, h->flags, h->epoch, h->ticket,
+                                                          h->err);
+    } else {
+        size_t smem = sizeof(FacSmem<double>) * kFacWarps;
+        cudaFuncSetAttribute(k_ilu0<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int grid = resident_grid(h, (const void*)k_ilu0<double>, kFacWarps * 32, smem, 32);
+        k_ilu0<double><<<grid, kFacWarps * 32, smem, s>>>(f.n, f.rowptr, f.col, f.diag, vals64, f.lu64,
+                                                           f.dinv64, f.fwd.perm, f.fwd.nslots, h->flags, h->epoch,
+                                                           h->ticket, h->err);
+    }
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
+// ------------------------------------------------------------ sweeps
+// Sentinel: all-ones bit pattern (a NaN no arithmetic produces).
+__device__ __forceinline__ bool is_sentinel(double v) { return __double_as_longlong(v) == -1ll; }
+__device__ __forceinline__ bool is_sentinel(float v) { return __float_as_int(v) == -1; }
+
+__device__ __forceinline__ double ld_poll(const double* p)
+{
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_poll(const float* p)
+{
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(double* p, double v)
+{
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(float* p, float v)
+{
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+template <class T>
+__device__ __forceinline__ T wait_value(const T* p, DevErr* err, long long who)
+{
+    T v = ld_poll(p);
+    unsigned it = 0, ns = kBackoffMin;
+    while (is_sentinel(v) && it < kSpinLimit) {
+        __nanosleep(ns);
+        if (ns < kBackoffMax) ns <<= 1;
+        v = ld_poll(p);
+        ++it;
+        if ((it & 255u) == 0u && err_set(err)) break;
+    }
+    if (is_sentinel(v)) { raise_err(err, EDFA_ERR_TIMEOUT, who); v = T(0); }
+    return v;
+}
+
+template <class TI>
+__device__ __forceinline__ double to_d(TI v) { return (double)v; }
+
+// One sweep over a level-ordered plan; LPR lanes per row.
+//   FWD=1: out_i = rhs_i - sum_{j<i} L_ij out_j          (unit lower L)
+//   FWD=0: out_i = dinv_i (rhs_i - sum_{j>i} U_ij out_j)
+// rhs_i = base_i - sum_p M_ip v_p  when a coupling matrix M is given (fused
+// SpMV of the block apply), else base_i.
+// Latency: everything that does not depend on this sweep's results (column
+// indices, factor values, the coupling term, base_i) is loaded first; then the
+// polls of up to KMAX dependencies per lane are issued back to back, so a row
+// whose dependencies are ready costs one L2 round trip.
+template <class T, class TB, class TO, int FWD, int LPR, int KMAX>
+__global__ void __launch_bounds__(kSweepThreads)
+k_sweep(const int32_t* __restrict__ perm, int64_t nslots, const int64_t* __restrict__ rowptr,
+        const int32_t* __restrict__ col, const T* __restrict__ lu, const int64_t* __restrict__ diag,
+        const T* __restrict__ dinv, const TB* __restrict__ base, const int64_t* __restrict__ mptr,
+        const int32_t* __restrict__ mcol, const T* __restrict__ mval, const TO* __restrict__ mv, TO* out,
+        unsigned long long* ticket, DevErr* err)
+{
+    constexpr int RPW = 32 / LPR;  // rows per warp
+    const int lane = threadIdx.x & 31;
+    const int g = lane / LPR, gl = lane % LPR;
+    for (;;) {
+        long long t0 = claim(ticket, RPW);
+        if (t0 >= nslots) break;
+        long long t = t0 + g;
+        int i = (t < nslots) ? perm[t] : -1;
+        T acc = T(0);
+        T bi = T(0), di = T(1);
+        if (i >= 0) {
+            bi = (T)to_d(base[i]);
+            if (!FWD) di = dinv[i];
+            const int64_t b = rowptr[i], e = rowptr[i + 1];
+            const int64_t d = diag[i];
+            const int64_t lo = FWD ? b : d + 1, hi = FWD ? d : e;
+            if (mptr) {
+                const int64_t mb = mptr[i], me = mptr[i + 1];
+                for (int64_t p = mb + gl; p < me; p += 4 * LPR) {
+                    int c[4];
+                    T w[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        int64_t q = p + u * LPR;
+                        c[u] = q < me ? mcol[q] : -1;
+                        w[u] = q < me ? mval[q] : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (c[u] >= 0) acc = fma(w[u], (T)mv[c[u]], acc);
+                }
+            }
+            T lacc = T(0);
+            for (int64_t c0 = lo; c0 < hi; c0 += KMAX * LPR) {
+                int cj[KMAX];
+                T lv[KMAX];
+#pragma unroll
+                for (int k = 0; k < KMAX; ++k) {
+                    int64_t p = c0 + gl + k * LPR;
+                    cj[k] = p < hi ? col[p] : -1;
+                    lv[k] = p < hi ? lu[p] : T(0);
+                }
+                T xv[KMAX];
+                unsigned pending = 0;
+#pragma unroll
+                for (int k = 0; k < KMAX; ++k) xv[k] = cj[k] >= 0 ? ld_poll(out + cj[k]) : T(0);
+#pragma unroll
+                for (int k = 0; k < KMAX; ++k)
+                    if (cj[k] >= 0 && is_sentinel(xv[k])) pending |= 1u << k;
+                // poll every still-pending dependency in the same round; the
+                // polls are issued before the back-off sleep so the two overlap
+                unsigned ns = kBackoffMin, it = 0;
+                while (pending && it < kSpinLimit) {
+#pragma unroll
+                    for (int k = 0; k < KMAX; ++k)
+                        if ((pending >> k) & 1u) xv[k] = ld_poll(out + cj[k]);
+                    __nanosleep(ns);
+                    if (ns < kSweepBackoffMax) ns <<= 1;
+#pragma unroll
+                    for (int k = 0; k < KMAX; ++k)
+                        if (((pending >> k) & 1u) && !is_sentinel(xv[k])) pending &= ~(1u << k);
+                    ++it;
+                    if ((it & 255u) == 0u && err_set(err)) break;
+                }
+                if (pending) {
+                    raise_err(err, EDFA_ERR_TIMEOUT, i);
+#pragma unroll
+                    for (int k = 0; k < KMAX; ++k)
+                        if ((pending >> k) & 1u) xv[k] = T(0);
+                }
+                // products summed as a tree: short dependent FP64 chain once
+                // the last dependency has arrived
+                T pr[KMAX];
+#pragma unroll
+                for (int k = 0; k < KMAX; ++k) pr[k] = lv[k] * xv[k];
+#pragma unroll
+                for (int w = 1; w < KMAX; w <<= 1)
+#pragma unroll
+                    for (int k = 0; k + w < KMAX; k += 2 * w) pr[k] += pr[k + w];
+                lacc += pr[0];
+            }
+            acc += lacc;
+        }
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (i >= 0 && gl == 0) {
+            T r = bi - acc;
+            if (!FWD) r *= di;
+            st_relaxed(out + i, (TO)r);
+        }
+    }
+}
+
+template <class T, class TB, class TO, int FWD, int LPR>
+static int launch_sweep(edfa_handle_s* h, const Factor& f, const TB* base, const int64_t* mptr, const int32_t* mcol,
+                        const T* mval, const TO* mv, TO* out, cudaStream_t s)
+{
+    const SweepPlan& p = FWD ? f.fwd : f.bwd;
+    if (f.n == 0) return EDFA_OK;
+    cudaMemsetAsync(out, 0xFF, (size_t)f.n * sizeof(TO), s);
+    cudaMemsetAsync(h->ticket, 0, sizeof(unsigned long long), s);
+    const T* lu = nullptr;
+    const T* dinv = nullptr;
+    if constexpr (sizeof(T) == 8) { lu = (const T*)f.lu64; dinv = (const T*)f.dinv64; }
+    else { lu = (const T*)f.lu32; dinv = (const T*)f.dinv32; }
+    auto fn = k_sweep<T, TB, TO, FWD, LPR, (LPR >= 32 ? 1 : (LPR >= 16 ? 2 : 4))>;
+    // resident warps: enough to hold ~3 dependency levels of rows in flight
+    // (fewer warps means fewer pollers competing for L2), 2..16 per SM
+    int wps = h->opt.sweep_warps_per_sm;
+    if (wps <= 0) wps = 8;
+    int grid = resident_grid(h, (const void*)fn, kSweepThreads, 0, wps);
+    fn<<<grid, kSweepThreads, 0, s>>>(p.perm, p.nslots, f.rowptr, f.col, lu, f.diag, dinv, base, mptr, mcol, mval, mv, out,
+                            h->ticket, h->err);
+    return EDFA_OK;
+}
+
+// ------------------------------------------------------------ block apply
+// z = P^{-1} r, Eq. (EDFA_prec):
+//   y    = A~^{-1} r_pi                  (L sweep, U sweep of ILU(0)(A))
+//   z_p  = S~^{-1} (r_p - C y)           (C y fused into the L sweep of S~)
+//   z_pi = A~^{-1} (r_pi - B z_p)        (B z_p fused into the L sweep of A)
+// variant 1 (upper block triangular): z_p = S~^{-1} r_p, then z_pi as above.
+#ifndef EDFA_LPR_A
+#define EDFA_LPR_A 4
+#endif
+#ifndef EDFA_LPR_S
+#define EDFA_LPR_S 8
+#endif
+template <class T>
+static int apply_impl(edfa_handle_s* h, const double* r, double* z, cudaStream_t s)
+{
+    const int32_t Nf = h->Nf, Ne = h->Ne;
+    const double* rpi = r;
+    const double* rp = r + Nf;
+    double* zpi = z;
+    double* zp = z + Nf;
+    T* u1 = (T*)h->tmp1;  // length Nf
+    T* u2 = (T*)h->tmp2;  // length max(Nf, Ne)
+    const T* bval;
+    const T* cval;
+    if constexpr (sizeof(T) == 8) { bval = (const T*)h->B.val; cval = (const T*)h->C.val; }
+    else { bval = (const T*)h->b32; cval = (const T*)h->c32; }
+    int rc;
+    if (h->opt.variant == 0) {
+        // y = A~^{-1} r_pi
+        rc = launch_sweep<T, double, T, 1, EDFA_LPR_A>(h, h->fa, rpi, nullptr, nullptr, (const T*)nullptr, (const T*)nullptr, u2, s);
+        if (rc) return rc;
+        rc = launch_sweep<T, T, T, 0, EDFA_LPR_A>(h, h->fa, u2, nullptr, nullptr, (const T*)nullptr, (const T*)nullptr, u1, s);
+        if (rc) return rc;
+        // w = L_S^{-1} (r_p - C y)
+        rc = launch_sweep<T, double, T, 1, EDFA_LPR_S>(h, h->fs, rp, h->C.rowptr, h->C.col, cval, u1, u2, s);
+        if (rc) return rc;
+    } else {
+        rc = launch_sweep<T, double, T, 1, EDFA_LPR_S>(h, h->fs, rp, nullptr, nullptr, (const T*)nullptr, (const T*)nullptr, u2, s);
+        if (rc) return rc;
+    }
+    // z_p = U_S^{-1} w  (written in the output precision)
+    if constexpr (sizeof(T) == 8) {
+        rc = launch_sweep<T, T, double, 0, EDFA_LPR_S>(h, h->fs, u2, nullptr, nullptr, (const T*)nullptr, (const double*)nullptr, zp, s);
+        if (rc) return rc;
+        // v = L_A^{-1} (r_pi - B z_p)
+        rc = launch_sweep<T, double, T, 1, EDFA_LPR_A>(h, h->fa, rpi, h->B.rowptr, h->B.col, bval, zp, u2, s);
+        if (rc) return rc;
+        rc = launch_sweep<T, T, double, 0, EDFA_LPR_A>(h, h->fa, u2, nullptr, nullptr, (const T*)nullptr, (const double*)nullptr, zpi, s);
+    } else {
+        T* zp32 = (T*)h->tmp3;
+        rc = launch_sweep<T, T, T, 0, EDFA_LPR_S>(h, h->fs, u2, nullptr, nullptr, (const T*)nullptr, (const T*)nullptr, zp32, s);
+        if (rc) return rc;
+        rc = launch_sweep<T, double, T, 1, EDFA_LPR_A>(h, h->fa, rpi, h->B.rowptr, h->B.col, bval, zp32, u2, s);
+        if (rc) return rc;
+        rc = launch_sweep<T, T, double, 0, EDFA_LPR_A>(h, h->fa, u2, nullptr, nullptr, (const T*)nullptr, (const double*)nullptr, zpi, s);
+        if (rc) return rc;
+        rc = to_f64_launch(zp32, zp, Ne, s);
+    }
+    if (rc) return rc;
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
+__global__ void k_f32_to_f64(const float* in, double* out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+int to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return EDFA_OK;
+    int64_t g = (n + 255) / 256;
+    if (g > 65535) g = 65535;
+    k_f32_to_f64<<<(unsigned)g, 256, 0, s>>>(in, out, n);
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
+int apply_prec(edfa_handle_s* h, const double* r, double* z, cudaStream_t s)
+{
+    if (h->opt.precision == 1) return apply_impl<float>(h, r, z, s);
+    return apply_impl<double>(h, r, z, s);
+}
+
+}  // namespace edfa

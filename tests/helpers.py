@@ -1,0 +1,73 @@
+"""Shared helpers for the parity tests: run the CUDA path through the C ABI
+and the oracle on the same seeded inputs, and compare."""
+import numpy as np
+
+import oracle as O
+
+QCODE = {"own": 0, "nbr": 1, "crow": 2, "thresh": 3, "dynamic": 4}
+
+# Tolerances (derived in the design doc):
+#  FP64 local solves and S~: |gpu - oracle| <= TOL_FP64 * max |oracle| over the
+#  column of X~ / row of S~ (the bar of 1e-10 relative, applied normwise).
+TOL_FP64 = 1e-10
+#  FP32 local solves: normwise 1e-4 against the FP64 oracle (single precision,
+#  condition numbers of the restricted blocks up to ~1e3 on the workloads).
+TOL_FP32 = 2e-3
+
+
+def gpu_handle(sysd, mode=None, form=0, variant=0, precision=0, thresh=None, dyn=None, qsets=None):
+    import torch
+
+    import paper_2009_13916_gb300 as P
+    A, B, C, D = P.system_to_device(sysd)
+    mode = mode or sysd.extra.get("qmode", "own")
+    kw = {}
+    if dyn is not None:
+        kw = dict(n_add=dyn[0], n_ent=dyn[1], it_max=dyn[2])
+    if qsets is not None:
+        kw["qsets"] = (torch.as_tensor(qsets[0], dtype=torch.int64, device="cuda"),
+                       torch.as_tensor(qsets[1], dtype=torch.int32, device="cuda"))
+    h = P.Edfa(A, B, C, D, sysd.Nf, sysd.Ne, qmode=mode,
+               thresh=thresh if thresh is not None else sysd.extra.get("thresh", 0.05),
+               schur_form=form, variant=variant, precision=precision, **kw)
+    return h
+
+
+def gpu_results(h):
+    t = h.tensors()
+    return {k: (v.cpu().numpy() if v is not None else None) for k, v in t.items()}
+
+
+def normwise_cols(x_gpu, x_orc, qptr):
+    """max over cells m of max|gpu - oracle| / max|oracle| on Q^(m)."""
+    worst = 0.0
+    d = np.abs(x_gpu - x_orc)
+    for m in range(len(qptr) - 1):
+        a, b = qptr[m], qptr[m + 1]
+        if b == a:
+            continue
+        scale = np.abs(x_orc[a:b]).max()
+        if scale == 0:
+            err = d[a:b].max()
+        else:
+            err = d[a:b].max() / scale
+        worst = max(worst, err)
+    return worst
+
+
+def normwise_cols_fast(x_gpu, x_orc, qptr):
+    d = np.abs(x_gpu - x_orc)
+    seg = np.repeat(np.arange(len(qptr) - 1), np.diff(qptr))
+    nseg = len(qptr) - 1
+    dmax = np.zeros(nseg)
+    smax = np.zeros(nseg)
+    np.maximum.at(dmax, seg, d)
+    np.maximum.at(smax, seg, np.abs(x_orc))
+    smax[smax == 0] = 1.0
+    return float((dmax / smax).max()) if nseg else 0.0
+
+
+def oracle_pipeline(sysd, mode=None, form=0, variant=0, dyn=None, solve=True, restart=50, rtol=1e-8,
+                    maxit=2000, b=None):
+    return O.edfa_pipeline(sysd, mode=mode, form=form, variant=variant, dyn=dyn, solve=solve,
+                           restart=restart, rtol=rtol, maxit=maxit, b=b)

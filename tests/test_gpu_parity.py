@@ -1,0 +1,182 @@
+"""CUDA path vs the FP64 oracle on the same seeded inputs (through the C ABI).
+
+Bar: restriction sets and S~ patterns bit-exact; X~, G~ and S~ values within
+1e-10 normwise (per column of X~ / row of S~); FGMRES(50) reaching 1e-8 with
+an iteration count within 1 of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from helpers import TOL_FP64, gpu_handle, gpu_results, normwise_cols_fast
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def full_tensor(n, seed=11):
+    s = W.Stream(seed)
+    Ne = int(np.prod(n))
+    m = np.exp(2.0 * s.normal(Ne))
+    q = s.normal(4 * Ne).reshape(Ne, 4)
+    sysd = W.assemble(*n, W.rotated_K(m, 0.1, q))
+    sysd.extra["qmode"] = "nbr"
+    return sysd
+
+
+CASES = {
+    "c1": lambda: W.config1(),
+    "brick6_paper": lambda: W.brick(6, seed=3, sigma=1.0),
+    "ragged_full_7x5x3": lambda: full_tensor((7, 5, 3)),
+    "c3_small": lambda: W.config3(24, 20, 6),
+    "c5_small": lambda: W.config5(10),
+}
+
+
+def compare_setup(sysd, mode, form=0):
+    torch = _torch()
+    ref = O.edfa_pipeline(sysd, mode=mode, form=form, solve=False)
+    h = gpu_handle(sysd, mode=mode, form=form)
+    g = gpu_results(h)
+    # restriction sets: bit-exact
+    assert np.array_equal(g["qptr"], ref["qptr"])
+    assert np.array_equal(g["qidx"], ref["qidx"])
+    # X~ (and G~) normwise per cell
+    ex = normwise_cols_fast(g["xval"], ref["xval"], ref["qptr"])
+    assert ex <= TOL_FP64, f"X~ error {ex:.3e}"
+    if form == 1:
+        eg = normwise_cols_fast(g["gval"], ref["gval"], ref["qptr"])
+        assert eg <= TOL_FP64, f"G~ error {eg:.3e}"
+    # S~ pattern bit-exact, values normwise per row
+    S = ref["S"]
+    assert np.array_equal(g["s_rowptr"], S.rowptr)
+    assert np.array_equal(g["s_col"], S.col)
+    es = normwise_cols_fast(g["s_val"], S.val, S.rowptr)
+    assert es <= TOL_FP64, f"S~ error {es:.3e}"
+    torch.cuda.synchronize()
+    return h, ref
+
+
+@pytest.mark.parametrize("case,mode", [("c1", "own"), ("brick6_paper", "own"), ("brick6_paper", "nbr"),
+                                       ("brick6_paper", "crow"), ("ragged_full_7x5x3", "nbr"),
+                                       ("c3_small", "thresh"), ("c5_small", "crow")])
+def test_setup_parity(case, mode):
+    sysd = CASES[case]()
+    h, _ = compare_setup(sysd, mode)
+    h.close()
+
+
+@pytest.mark.parametrize("case,mode", [("brick6_paper", "nbr"), ("ragged_full_7x5x3", "crow")])
+def test_two_sided_schur_parity(case, mode):
+    sysd = CASES[case]()
+    h, _ = compare_setup(sysd, mode, form=1)
+    h.close()
+
+
+@pytest.mark.parametrize("case,mode,variant", [("brick6_paper", "nbr", 0), ("ragged_full_7x5x3", "nbr", 0),
+                                               ("c3_small", "thresh", 0), ("brick6_paper", "own", 1)])
+def test_apply_and_fgmres_parity(case, mode, variant):
+    torch = _torch()
+    sysd = CASES[case]()
+    ref = O.edfa_pipeline(sysd, mode=mode, variant=variant, solve=True)
+    h = gpu_handle(sysd, mode=mode, variant=variant)
+    # one application on a seeded vector
+    r = W.Stream(77).normal(sysd.n)
+    z_ref = ref["prec"].apply(r)
+    z = h.apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    err = np.abs(z - z_ref).max() / np.abs(z_ref).max()
+    assert err <= 1e-9, f"apply error {err:.3e}"
+    # matvec
+    y = h.matvec(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    yref = sysd.full_scipy() @ r
+    assert np.abs(y - yref).max() <= 1e-12 * np.abs(yref).max()
+    # FGMRES
+    b = torch.as_tensor(sysd.b, device="cuda")
+    x, info = h.solve(b, restart=50, rtol=1e-8, maxit=2000)
+    assert info.converged and info.true_rel <= 1e-8
+    assert abs(info.iterations - ref["iters"]) <= 1, (info.iterations, ref["iters"])
+    xr = x.cpu().numpy()
+    res = np.linalg.norm(sysd.full_scipy() @ xr - sysd.b) / np.linalg.norm(sysd.b)
+    assert res <= 1.05e-8
+    h.close()
+
+
+def test_config1_stagnation_matches_oracle():
+    # the weak-form config-1 coupling stagnates with own-face sets; both sides
+    # must trace the same residual history over a fixed budget
+    torch = _torch()
+    sysd = W.config1()
+    ref = O.edfa_pipeline(sysd, mode="own", maxit=100)
+    h = gpu_handle(sysd, mode="own")
+    x, info = h.solve(torch.as_tensor(sysd.b, device="cuda"), restart=50, rtol=1e-8, maxit=100)
+    hist = h.history()
+    assert info.iterations == 100 and not info.converged
+    np.testing.assert_allclose(hist[:len(ref["hist"])], ref["hist"], rtol=1e-6)
+    h.close()
+
+
+def test_stage2_setup_new_D():
+    torch = _torch()
+    sysd = CASES["brick6_paper"]()
+    h = gpu_handle(sysd, mode="nbr")
+    # new storage term: D changes on the diagonal only (same pattern)
+    D2 = sysd.D.to_scipy().tocsr().copy()
+    D2.setdiag(D2.diagonal() * 3.0)
+    D2.sort_indices()
+    import paper_2009_13916_gb300 as P
+    Dt = (torch.as_tensor(D2.indptr, dtype=torch.int64, device="cuda"),
+          torch.as_tensor(D2.indices, dtype=torch.int32, device="cuda"),
+          torch.as_tensor(D2.data, dtype=torch.float64, device="cuda"))
+    h.setup(Dt)
+    q = O.qsets("nbr", sysd.A, sysd.B, sysd.C)
+    x, _ = O.local_solves(sysd.A, sysd.B, sysd.C, *q)
+    S = O.schur(0, sysd.A, sysd.C, D2, *q, x)
+    g = gpu_results(h)
+    assert np.array_equal(g["s_col"], S.col)
+    assert normwise_cols_fast(g["s_val"], S.val, S.rowptr) <= TOL_FP64
+    h.close()
+
+
+def test_invalid_inputs_rejected():
+    torch = _torch()
+    import paper_2009_13916_gb300 as P
+    sysd = CASES["brick6_paper"]()
+    A, B, C, D = P.system_to_device(sysd)
+    bad = A[2].clone()
+    bad[5] = float("nan")
+    with pytest.raises(P.EdfaError) as e:
+        P.Edfa((A[0], A[1], bad), B, C, D, sysd.Nf, sysd.Ne)
+    assert e.value.code == 1
+    # unsorted columns in one row of C
+    col = C[1].clone()
+    b0 = int(sysd.C.rowptr[3])
+    col[b0], col[b0 + 1] = col[b0 + 1].clone(), col[b0].clone()
+    with pytest.raises(P.EdfaError) as e:
+        P.Edfa(A, B, (C[0], col, C[2]), D, sysd.Nf, sysd.Ne)
+    assert e.value.code == 1 and e.value.detail == 3
+
+
+def test_local_breakdown_reports_cell():
+    torch = _torch()
+    import paper_2009_13916_gb300 as P
+    sysd = CASES["brick6_paper"]()
+    # make one face diagonal of A positive: its local systems are no longer
+    # negative definite, the first cell whose set holds the face breaks down
+    Av = sysd.A.val.copy()
+    f = int(sysd.cell_faces[40, 1])
+    p = [k for k in range(sysd.A.rowptr[f], sysd.A.rowptr[f + 1]) if sysd.A.col[k] == f][0]
+    Av[p] = abs(Av[p])
+    A, B, C, D = P.system_to_device(sysd)
+    At = (A[0], A[1], torch.as_tensor(Av, device="cuda"))
+    with pytest.raises(P.EdfaError) as e:
+        P.Edfa(At, B, C, D, sysd.Nf, sysd.Ne, qmode="own")
+    assert e.value.code == 4
+    owners = set(int(c) for c in sysd.face_cells[f] if c >= 0)
+    assert e.value.detail in owners
