@@ -119,6 +119,11 @@ typedef struct {
     int32_t q_max;                                 /* max |Q^(m)| */
     int64_t s_nnz;                                 /* nnz of S~ */
     int32_t levels_a, levels_s;                    /* dependency depth of the ILU(0) sweeps */
+    /* with profiling on (edfa_set_profiling): accumulated device time and
+       launch count of the triangular sweeps, kind 0..3 = A~ forward, A~
+       backward, S~ forward, S~ backward */
+    double sweep_ms[4];
+    int64_t sweep_n[4];
 } edfa_stats;
 
 /* Read-only views of what the handle computed (device pointers, valid until
@@ -167,6 +172,13 @@ EDFA_API int32_t edfa_history(edfa_handle h, double* hist, int32_t cap);
 
 EDFA_API int edfa_get_view(edfa_handle h, edfa_view* v);
 EDFA_API int edfa_get_stats(edfa_handle h, edfa_stats* s);
+
+/* Turn per-sweep device timing on (1) or off (0); turning it on clears the
+ * accumulated sweep times.  Timing adds one event pair per sweep launch. */
+EDFA_API int edfa_set_profiling(edfa_handle h, int32_t on);
+
+/* Number of CUDA kernels this library has launched in this process. */
+EDFA_API int64_t edfa_launch_count(void);
 
 EDFA_API int edfa_free(edfa_handle h);
 

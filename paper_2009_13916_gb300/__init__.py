@@ -55,7 +55,8 @@ class Stats(C.Structure):
     _fields_ = [("ms_qsets", C.c_float), ("ms_local", C.c_float), ("ms_schur", C.c_float),
                 ("ms_ilu_a", C.c_float), ("ms_stage2", C.c_float), ("ms_solve", C.c_float),
                 ("n_local", C.c_int64), ("q_total", C.c_int64), ("q_max", C.c_int32),
-                ("s_nnz", C.c_int64), ("levels_a", C.c_int32), ("levels_s", C.c_int32)]
+                ("s_nnz", C.c_int64), ("levels_a", C.c_int32), ("levels_s", C.c_int32),
+                ("sweep_ms", C.c_double * 4), ("sweep_n", C.c_int64 * 4)]
 
 
 class View(C.Structure):
@@ -67,8 +68,8 @@ class View(C.Structure):
 
 _lib = None
 EXPORTS = ("edfa_default_options", "edfa_build", "edfa_setup", "edfa_apply", "edfa_matvec",
-           "edfa_solve", "edfa_history", "edfa_get_view", "edfa_get_stats", "edfa_free",
-           "edfa_strerror", "edfa_last_error_detail")
+           "edfa_solve", "edfa_history", "edfa_get_view", "edfa_get_stats", "edfa_set_profiling",
+           "edfa_launch_count", "edfa_free", "edfa_strerror", "edfa_last_error_detail")
 
 
 def lib_path() -> str:
@@ -99,6 +100,10 @@ def lib(build_if_missing: bool = True):
         L.edfa_get_view.argtypes = [vp, P(View)]
         L.edfa_get_stats.argtypes = [vp, P(Stats)]
         L.edfa_free.argtypes = [vp]
+        L.edfa_set_profiling.argtypes = [vp, C.c_int32]
+        L.edfa_set_profiling.restype = C.c_int
+        L.edfa_launch_count.argtypes = []
+        L.edfa_launch_count.restype = C.c_int64
         L.edfa_strerror.argtypes = [C.c_int]
         L.edfa_strerror.restype = C.c_char_p
         L.edfa_last_error_detail.restype = C.c_int64
@@ -145,6 +150,10 @@ def edfa_solve(h, b_ptr: int, x_ptr: int, restart: int, rtol: float, maxit: int,
     if rc != EDFA_OK and not (rc == EDFA_ERR_NOT_CONVERGED and not raise_on_nonconv):
         raise EdfaError(rc, "edfa_solve", lib().edfa_last_error_detail())
     return info
+
+
+def launch_count() -> int:
+    return int(lib().edfa_launch_count())
 
 
 def edfa_free(h):
@@ -236,6 +245,9 @@ class Edfa:
         buf = (C.c_double * 100000)()
         n = lib().edfa_history(self.h, buf, 100000)
         return np.array(buf[:n])
+
+    def set_profiling(self, on: bool):
+        lib().edfa_set_profiling(self.h, 1 if on else 0)
 
     def stats(self) -> Stats:
         st = Stats()

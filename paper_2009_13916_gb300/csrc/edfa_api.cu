@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "internal.cuh"
@@ -12,10 +13,25 @@
 using namespace edfa;
 
 static thread_local long long g_detail = -1;
+static std::atomic<long long> g_launches{0};
 
 namespace edfa {
 
 void set_detail(long long d) { g_detail = d; }
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// fold the recorded sweep event pairs into the stats (stream already synchronised)
+static void prof_collect(edfa_handle_s* h)
+{
+    for (size_t k = 0; k < h->prof_used; ++k) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, h->prof_ev[2 * k], h->prof_ev[2 * k + 1]) == cudaSuccess) {
+            h->stats.sweep_ms[h->prof_kind[k]] += ms;
+            h->stats.sweep_n[h->prof_kind[k]] += 1;
+        }
+    }
+    h->prof_used = 0;
+}
 
 int dalloc(edfa_handle_s* h, void** p, size_t bytes)
 {
@@ -61,6 +77,7 @@ static void free_all(edfa_handle_s* h)
     if (h->hbuf_host) cudaFreeHost(h->hbuf_host);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : h->prof_ev) cudaEventDestroy(e);
     delete h;
 }
 
@@ -366,6 +383,7 @@ int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
     h->stats.ms_solve = ms;
+    prof_collect(h);
     loc.iterations = it;
     loc.converged = status == EDFA_OK;
     if (info) *info = loc;
@@ -402,9 +420,24 @@ int edfa_get_view(edfa_handle h, edfa_view* v)
 int edfa_get_stats(edfa_handle h, edfa_stats* st)
 {
     if (!h || !st) return EDFA_ERR_INVALID;
+    if (h->prof_used) {
+        cudaDeviceSynchronize();
+        prof_collect(h);
+    }
     *st = h->stats;
     return EDFA_OK;
 }
+
+int edfa_set_profiling(edfa_handle h, int32_t on)
+{
+    if (!h) return EDFA_ERR_INVALID;
+    h->profiling = on ? 1 : 0;
+    h->prof_used = 0;
+    for (int k = 0; k < 4; ++k) { h->stats.sweep_ms[k] = 0; h->stats.sweep_n[k] = 0; }
+    return EDFA_OK;
+}
+
+int64_t edfa_launch_count(void) { return g_launches.load(); }
 
 int edfa_free(edfa_handle h)
 {

@@ -166,12 +166,21 @@ struct edfa_handle_s {
     edfa::DevErr* err = nullptr;
     edfa::DevErr* err_host = nullptr;
     cudaEvent_t ev[8] = {};
+    // opt-in per-sweep device timing: event pairs recorded around every sweep
+    // launch (kind 0..3 = A forward, A backward, S~ forward, S~ backward)
+    int profiling = 0;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_kind;
+    size_t prof_used = 0;
     edfa_stats stats{};
     std::vector<double> hist;
     std::vector<edfa::DBuf> owned;  // every device allocation, released by edfa_free
 };
 
 namespace edfa {
+
+// process-wide count of kernel launches issued by the library
+void count_launch();
 
 // allocation helpers (record into h->owned)
 int dalloc(edfa_handle_s* h, void** p, size_t bytes);

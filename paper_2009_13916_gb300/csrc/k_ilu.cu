@@ -118,8 +118,8 @@ static int make_plan(edfa_handle_s* h, SweepPlan& plan, int32_t n, const int64_t
     const void* fn = fwd ? (const void*)k_levels<1> : (const void*)k_levels<0>;
     int grid = resident_grid(h, fn, 256, 0);
     cudaMemsetAsync(h->ticket, 0, sizeof(unsigned long long), s);
-    if (fwd) k_levels<1><<<grid, 256, 0, s>>>(n, rowptr, col, level, maxlev, h->ticket, h->err);
-    else k_levels<0><<<grid, 256, 0, s>>>(n, rowptr, col, level, maxlev, h->ticket, h->err);
+    if (fwd) (edfa::count_launch(), k_levels<1><<<grid, 256, 0, s>>>(n, rowptr, col, level, maxlev, h->ticket, h->err));
+    else (edfa::count_launch(), k_levels<0><<<grid, 256, 0, s>>>(n, rowptr, col, level, maxlev, h->ticket, h->err));
     int nlev = 0;
     cudaMemcpyAsync(&nlev, maxlev, sizeof(int), cudaMemcpyDeviceToHost, s);
     int rc = check_err(h, s);
@@ -132,8 +132,8 @@ static int make_plan(edfa_handle_s* h, SweepPlan& plan, int32_t n, const int64_t
     if (cudaMallocAsync((void**)&cursor, ((size_t)nlev + 1) * sizeof(int64_t), s) != cudaSuccess) return EDFA_ERR_OOM;
     cudaMemsetAsync(off, 0, ((size_t)nlev + 1) * sizeof(int64_t), s);
     cudaMemsetAsync(cursor, 0, ((size_t)nlev + 1) * sizeof(int64_t), s);
-    if (n > 0) k_level_hist<<<(n + 255) / 256, 256, 0, s>>>(n, level, (unsigned long long*)off);
-    if (nlev > 0) k_level_pad<<<(nlev + 255) / 256, 256, 0, s>>>(nlev, off, pad);
+    if (n > 0) (edfa::count_launch(), k_level_hist<<<(n + 255) / 256, 256, 0, s>>>(n, level, (unsigned long long*)off));
+    if (nlev > 0) (edfa::count_launch(), k_level_pad<<<(nlev + 255) / 256, 256, 0, s>>>(nlev, off, pad));
     rc = scan_i64(h, off, nlev, s);
     if (rc) return rc;
     int64_t nslots = 0;
@@ -142,7 +142,7 @@ static int make_plan(edfa_handle_s* h, SweepPlan& plan, int32_t n, const int64_t
     rc = dalloc_t(h, &plan.perm, (size_t)(nslots > 0 ? nslots : 1));
     if (rc) return rc;
     cudaMemsetAsync(plan.perm, 0xFF, (size_t)(nslots > 0 ? nslots : 1) * sizeof(int32_t), s);
-    if (n > 0) k_level_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, level, off, cursor, plan.perm);
+    if (n > 0) (edfa::count_launch(), k_level_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, level, off, cursor, plan.perm));
     plan.nslots = nslots;
     plan.nlevels = nlev;
     cudaFreeAsync(off, s);
@@ -172,7 +172,7 @@ int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64
     f.col = col;
     int rc = dalloc_t(h, &f.diag, (size_t)(n > 0 ? n : 1));
     if (rc) return rc;
-    if (n > 0) k_find_diag<<<(n + 255) / 256, 256, 0, s>>>(n, rowptr, col, f.diag, h->err);
+    if (n > 0) (edfa::count_launch(), k_find_diag<<<(n + 255) / 256, 256, 0, s>>>(n, rowptr, col, f.diag, h->err));
     rc = make_plan(h, f.fwd, n, rowptr, col, 1, 32, s);
     if (rc) return rc;
     rc = make_plan(h, f.bwd, n, rowptr, col, 0, 32, s);
@@ -346,16 +346,16 @@ int factor_numeric(edfa_handle_s* h, Factor& f, const double* vals64, const floa
         size_t smem = sizeof(FacSmem<float>) * kFacWarps;
         cudaFuncSetAttribute(k_ilu0<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int grid = resident_grid(h, (const void*)k_ilu0<float>, kFacWarps * 32, smem, 32);
-        k_ilu0<float><<<grid, kFacWarps * 32, smem, s>>>(f.n, f.rowptr, f.col, f.diag, vals32, f.lu32, f.dinv32,
+        (edfa::count_launch(), k_ilu0<float><<<grid, kFacWarps * 32, smem, s>>>(f.n, f.rowptr, f.col, f.diag, vals32, f.lu32, f.dinv32,
                                                           f.fwd.perm, f.fwd.nslots, h->flags, h->epoch, h->ticket,
-                                                          h->err);
+                                                          h->err));
     } else {
         size_t smem = sizeof(FacSmem<double>) * kFacWarps;
         cudaFuncSetAttribute(k_ilu0<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int grid = resident_grid(h, (const void*)k_ilu0<double>, kFacWarps * 32, smem, 32);
-        k_ilu0<double><<<grid, kFacWarps * 32, smem, s>>>(f.n, f.rowptr, f.col, f.diag, vals64, f.lu64,
+        (edfa::count_launch(), k_ilu0<double><<<grid, kFacWarps * 32, smem, s>>>(f.n, f.rowptr, f.col, f.diag, vals64, f.lu64,
                                                            f.dinv64, f.fwd.perm, f.fwd.nslots, h->flags, h->epoch,
-                                                           h->ticket, h->err);
+                                                           h->ticket, h->err));
     }
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
@@ -534,8 +534,24 @@ static int launch_sweep(edfa_handle_s* h, const Factor& f, const TB* base, const
     int wps = h->opt.sweep_warps_per_sm;
     if (wps <= 0) wps = 8;
     int grid = resident_grid(h, (const void*)fn, kSweepThreads, 0, wps);
-    fn<<<grid, kSweepThreads, 0, s>>>(p.perm, p.nslots, f.rowptr, f.col, lu, f.diag, dinv, base, mptr, mcol, mval, mv, out,
-                            h->ticket, h->err);
+    cudaEvent_t* pe = nullptr;
+    if (h->profiling) {
+        if (h->prof_used * 2 + 2 > h->prof_ev.size()) {
+            for (int k = 0; k < 64; ++k) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                h->prof_ev.push_back(e);
+            }
+            h->prof_kind.resize(h->prof_ev.size() / 2);
+        }
+        pe = &h->prof_ev[2 * h->prof_used];
+        h->prof_kind[h->prof_used] = (&f == &h->fs ? 2 : 0) + (FWD ? 0 : 1);
+        h->prof_used++;
+        cudaEventRecord(pe[0], s);
+    }
+    (edfa::count_launch(), fn<<<grid, kSweepThreads, 0, s>>>(p.perm, p.nslots, f.rowptr, f.col, lu, f.diag, dinv, base, mptr, mcol, mval, mv, out,
+                            h->ticket, h->err));
+    if (pe) cudaEventRecord(pe[1], s);
     return EDFA_OK;
 }
 
@@ -612,7 +628,7 @@ int to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t s)
     if (n <= 0) return EDFA_OK;
     int64_t g = (n + 255) / 256;
     if (g > 65535) g = 65535;
-    k_f32_to_f64<<<(unsigned)g, 256, 0, s>>>(in, out, n);
+    (edfa::count_launch(), k_f32_to_f64<<<(unsigned)g, 256, 0, s>>>(in, out, n));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 

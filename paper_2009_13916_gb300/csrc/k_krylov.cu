@@ -37,8 +37,8 @@ int matvec(edfa_handle_s* h, const double* x, double* y, cudaStream_t s)
 {
     int64_t n = (int64_t)h->Nf + h->Ne;
     if (n == 0) return EDFA_OK;
-    k_block_spmv<<<(unsigned)((n + kKT - 1) / kKT), kKT, 0, s>>>(h->Nf, h->Ne, csr_of(h->A), csr_of(h->B),
-                                                                  csr_of(h->C), csr_of(h->D), x, y);
+    (edfa::count_launch(), k_block_spmv<<<(unsigned)((n + kKT - 1) / kKT), kKT, 0, s>>>(h->Nf, h->Ne, csr_of(h->A), csr_of(h->B),
+                                                                  csr_of(h->C), csr_of(h->D), x, y));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
@@ -176,8 +176,8 @@ int kry_multidot(const double* V, int64_t ld, int nv, const double* w, int64_t n
                  const double* add, double* out_sum, int with_self, cudaStream_t s)
 {
     int nc = Kry::nchunks(n);
-    k_multidot<<<nc, kKT, 0, s>>>(V, ld, nv, w, n, part, nc, with_self);
-    k_reduce_parts<<<nv + with_self, kKT, 0, s>>>(part, nc, out, add, out_sum);
+    (edfa::count_launch(), k_multidot<<<nc, kKT, 0, s>>>(V, ld, nv, w, n, part, nc, with_self));
+    (edfa::count_launch(), k_reduce_parts<<<nv + with_self, kKT, 0, s>>>(part, nc, out, add, out_sum));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
@@ -185,8 +185,8 @@ int kry_update(const double* V, int64_t ld, int nv, const double* hcoef, double*
                double* nrm2_out, cudaStream_t s)
 {
     int nc = Kry::nchunks(n);
-    k_update<<<nc, kKT, 0, s>>>(V, ld, nv, hcoef, w, n, nrm2_out ? part : nullptr);
-    if (nrm2_out) k_reduce_parts<<<1, kKT, 0, s>>>(part, nc, nrm2_out, nullptr, nullptr);
+    (edfa::count_launch(), k_update<<<nc, kKT, 0, s>>>(V, ld, nv, hcoef, w, n, nrm2_out ? part : nullptr));
+    if (nrm2_out) (edfa::count_launch(), k_reduce_parts<<<1, kKT, 0, s>>>(part, nc, nrm2_out, nullptr, nullptr));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
@@ -195,7 +195,7 @@ int kry_scale_from(const double* w, double* v, int64_t n, const double* nrm2, do
     int64_t g = (n + kKT - 1) / kKT;
     if (g > 4096) g = 4096;
     if (g < 1) g = 1;
-    k_scale_from<<<(unsigned)g, kKT, 0, s>>>(w, v, n, nrm2, out_norm);
+    (edfa::count_launch(), k_scale_from<<<(unsigned)g, kKT, 0, s>>>(w, v, n, nrm2, out_norm));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
@@ -204,15 +204,15 @@ int kry_combine(const double* Z, int64_t ld, int k, const double* y, double* x, 
     int64_t g = (n + kKT - 1) / kKT;
     if (g > 4096) g = 4096;
     if (g < 1) g = 1;
-    k_combine<<<(unsigned)g, kKT, 0, s>>>(Z, ld, k, y, x, n);
+    (edfa::count_launch(), k_combine<<<(unsigned)g, kKT, 0, s>>>(Z, ld, k, y, x, n));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
 int kry_residual(const double* b, double* r, int64_t n, double* part, double* nrm2_out, cudaStream_t s)
 {
     int nc = Kry::nchunks(n);
-    k_residual<<<nc, kKT, 0, s>>>(b, r, n, part);
-    k_reduce_parts<<<1, kKT, 0, s>>>(part, nc, nrm2_out, nullptr, nullptr);
+    (edfa::count_launch(), k_residual<<<nc, kKT, 0, s>>>(b, r, n, part));
+    (edfa::count_launch(), k_reduce_parts<<<1, kKT, 0, s>>>(part, nc, nrm2_out, nullptr, nullptr));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
@@ -221,7 +221,7 @@ int kry_scale_const(const double* w, double* v, int64_t n, double alpha, cudaStr
     int64_t g = (n + kKT - 1) / kKT;
     if (g > 4096) g = 4096;
     if (g < 1) g = 1;
-    k_scale_const<<<(unsigned)g, kKT, 0, s>>>(w, v, n, alpha);
+    (edfa::count_launch(), k_scale_const<<<(unsigned)g, kKT, 0, s>>>(w, v, n, alpha));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 

@@ -189,7 +189,7 @@ static int launch_local_t(edfa_handle_s* h, const LocalArgs<T>& a, int warps, cu
     long long grid = (long long)per * h->nsm;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    fn<<<(unsigned)grid, warps * 32, smem, s>>>(a);
+    (edfa::count_launch(), fn<<<(unsigned)grid, warps * 32, smem, s>>>(a));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 

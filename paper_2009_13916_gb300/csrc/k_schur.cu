@@ -273,14 +273,14 @@ static int schur_t(edfa_handle_s* h, const T* xval, const T* gval, T** h_val, cu
     if (rc) return rc;
     cudaMemsetAsync(h->xr_ptr, 0, ((size_t)Nf + 1) * sizeof(int64_t), s);
     if (h->qtot > 0)
-        k_q_count<<<(unsigned)((h->qtot + 255) / 256), 256, 0, s>>>(h->qidx, h->qtot, (unsigned long long*)h->xr_ptr);
+        (edfa::count_launch(), k_q_count<<<(unsigned)((h->qtot + 255) / 256), 256, 0, s>>>(h->qidx, h->qtot, (unsigned long long*)h->xr_ptr));
     rc = scan_i64(h, h->xr_ptr, Nf, s);
     if (rc) return rc;
     unsigned long long* cursor = nullptr;
     if (cudaMallocAsync((void**)&cursor, ((size_t)Nf + 1) * sizeof(int64_t), s) != cudaSuccess) return EDFA_ERR_OOM;
     cudaMemcpyAsync(cursor, h->xr_ptr, ((size_t)Nf + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
-    if (Ne > 0) k_q_fill<<<(Ne + 255) / 256, 256, 0, s>>>(Ne, h->qptr, h->qidx, cursor, h->xr_cell);
-    if (Nf > 0) k_row_sort2<<<(Nf + 255) / 256, 256, 0, s>>>(h->xr_ptr, h->xr_cell, Nf);
+    if (Ne > 0) (edfa::count_launch(), k_q_fill<<<(Ne + 255) / 256, 256, 0, s>>>(Ne, h->qptr, h->qidx, cursor, h->xr_cell));
+    if (Nf > 0) (edfa::count_launch(), k_row_sort2<<<(Nf + 255) / 256, 256, 0, s>>>(h->xr_ptr, h->xr_cell, Nf));
     cudaFreeAsync(cursor, s);
 
     SchurArgs<T> a{};
@@ -316,7 +316,7 @@ static int schur_t(edfa_handle_s* h, const T* xval, const T* gval, T** h_val, cu
     long long need = (Ne + kSWarps - 1) / kSWarps;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k_schur<T, 0><<<(unsigned)grid, kSWarps * 32, 0, s>>>(a);
+    (edfa::count_launch(), k_schur<T, 0><<<(unsigned)grid, kSWarps * 32, 0, s>>>(a));
     rc = scan_i64(h, h->s_ptr, Ne, s);
     if (rc) return rc;
     int64_t nnz = 0;
@@ -333,7 +333,7 @@ static int schur_t(edfa_handle_s* h, const T* xval, const T* gval, T** h_val, cu
     a.s_col = h->s_col;
     a.h_val = *h_val;
     a.d_map = h->d_map;
-    k_schur<T, 1><<<(unsigned)grid, kSWarps * 32, 0, s>>>(a);
+    (edfa::count_launch(), k_schur<T, 1><<<(unsigned)grid, kSWarps * 32, 0, s>>>(a));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
@@ -358,11 +358,11 @@ int stage2_values(edfa_handle_s* h, cudaStream_t s)
     if (gd > 65535) gd = 65535;
     if (gd < 1) gd = 1;
     if (h->opt.precision == 1) {
-        k_stage2<float><<<(unsigned)g, 256, 0, s>>>(h->s_nnz, h->h_val32, h->s_val32);
-        k_stage2_d<float><<<(unsigned)gd, 256, 0, s>>>(h->D.nnz, h->D.val, h->d_map, h->s_val32);
+        (edfa::count_launch(), k_stage2<float><<<(unsigned)g, 256, 0, s>>>(h->s_nnz, h->h_val32, h->s_val32));
+        (edfa::count_launch(), k_stage2_d<float><<<(unsigned)gd, 256, 0, s>>>(h->D.nnz, h->D.val, h->d_map, h->s_val32));
     } else {
-        k_stage2<double><<<(unsigned)g, 256, 0, s>>>(h->s_nnz, h->h_val, h->s_val);
-        k_stage2_d<double><<<(unsigned)gd, 256, 0, s>>>(h->D.nnz, h->D.val, h->d_map, h->s_val);
+        (edfa::count_launch(), k_stage2<double><<<(unsigned)g, 256, 0, s>>>(h->s_nnz, h->h_val, h->s_val));
+        (edfa::count_launch(), k_stage2_d<double><<<(unsigned)gd, 256, 0, s>>>(h->D.nnz, h->D.val, h->d_map, h->s_val));
     }
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }

@@ -38,7 +38,7 @@ int launch_validate(edfa_handle_s* h, const edfa_csr& M, int need_diag, cudaStre
     if (M.nrows < 0 || M.ncols < 0 || M.nnz < 0) return EDFA_ERR_INVALID;
     if (M.nrows > 0 && (!M.rowptr || (M.nnz > 0 && (!M.col || !M.val)))) return EDFA_ERR_INVALID;
     int64_t n = (int64_t)M.nrows + 1;
-    k_validate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(csr_of(M), need_diag, h->err);
+    (edfa::count_launch(), k_validate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(csr_of(M), need_diag, h->err));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
@@ -129,9 +129,9 @@ int scan_i64(edfa_handle_s* h, int64_t* data, int64_t n, cudaStream_t s)
     if (nb == 0) nb = 1;
     int64_t* part = nullptr;
     if (cudaMallocAsync((void**)&part, (nb + 1) * sizeof(int64_t), s) != cudaSuccess) return EDFA_ERR_OOM;
-    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, part);
-    k_scan_parts<<<1, kScanThreads, 0, s>>>(part, nb);
-    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, part);
+    (edfa::count_launch(), k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, part));
+    (edfa::count_launch(), k_scan_parts<<<1, kScanThreads, 0, s>>>(part, nb));
+    (edfa::count_launch(), k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, part));
     cudaFreeAsync(part, s);
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
@@ -176,14 +176,14 @@ int build_bt(edfa_handle_s* h, cudaStream_t s)
     cudaMemsetAsync(h->bt_ptr, 0, ((size_t)Ne + 1) * sizeof(int64_t), s);
     Csr<double> B = csr_of(h->B);
     if (B.nnz > 0)
-        k_col_count<<<(unsigned)((B.nnz + 255) / 256), 256, 0, s>>>(B, (unsigned long long*)h->bt_ptr);
+        (edfa::count_launch(), k_col_count<<<(unsigned)((B.nnz + 255) / 256), 256, 0, s>>>(B, (unsigned long long*)h->bt_ptr));
     rc = scan_i64(h, h->bt_ptr, Ne, s);
     if (rc) return rc;
     unsigned long long* cursor = nullptr;
     if (cudaMallocAsync((void**)&cursor, ((size_t)Ne + 1) * sizeof(int64_t), s) != cudaSuccess) return EDFA_ERR_OOM;
     cudaMemcpyAsync(cursor, h->bt_ptr, ((size_t)Ne + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
-    if (B.nrows > 0) k_col_fill<<<(unsigned)((B.nrows + 255) / 256), 256, 0, s>>>(B, cursor, h->bt_col);
-    if (Ne > 0) k_row_sort<<<(unsigned)((Ne + 255) / 256), 256, 0, s>>>(h->bt_ptr, h->bt_col, Ne);
+    if (B.nrows > 0) (edfa::count_launch(), k_col_fill<<<(unsigned)((B.nrows + 255) / 256), 256, 0, s>>>(B, cursor, h->bt_col));
+    if (Ne > 0) (edfa::count_launch(), k_row_sort<<<(unsigned)((Ne + 255) / 256), 256, 0, s>>>(h->bt_ptr, h->bt_col, Ne));
     cudaFreeAsync(cursor, s);
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
@@ -323,7 +323,7 @@ int build_qsets(edfa_handle_s* h, cudaStream_t s)
     unsigned cap = (unsigned)h->nsm * 16;
     if (grid > cap) grid = cap;
     if (grid == 0) grid = 1;
-    k_qsets<0><<<grid, kQWarps * 32, 0, s>>>(a);
+    (edfa::count_launch(), k_qsets<0><<<grid, kQWarps * 32, 0, s>>>(a));
     rc = scan_i64(h, h->qptr, Ne, s);
     if (rc) return rc;
     int64_t tot = 0;
@@ -339,7 +339,7 @@ int build_qsets(edfa_handle_s* h, cudaStream_t s)
     if (rc) return rc;
     a.qptr = h->qptr;
     a.qidx = h->qidx;
-    k_qsets<1><<<grid, kQWarps * 32, 0, s>>>(a);
+    (edfa::count_launch(), k_qsets<1><<<grid, kQWarps * 32, 0, s>>>(a));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
@@ -355,7 +355,7 @@ int to_f32(const double* in, float* out, int64_t n, cudaStream_t s)
     if (n <= 0) return EDFA_OK;
     int64_t g = (n + 255) / 256;
     if (g > 65535) g = 65535;
-    k_to_f32<<<(unsigned)g, 256, 0, s>>>(in, out, n);
+    (edfa::count_launch(), k_to_f32<<<(unsigned)g, 256, 0, s>>>(in, out, n));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
