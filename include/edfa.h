@@ -177,6 +177,44 @@ EDFA_API int edfa_get_stats(edfa_handle h, edfa_stats* s);
  * accumulated sweep times.  Timing adds one event pair per sweep launch. */
 EDFA_API int edfa_set_profiling(edfa_handle h, int32_t on);
 
+/* Restriction sets Q^(m) without any device memory allocation.
+ *
+ * For callers that must not allocate device memory after start-up: host
+ * programs that hand all device memory to their own pool or budget up front
+ * (a simulator time loop with a fixed memory reservation, an embedding
+ * application whose allocator owns the GPU), or code that cannot afford the
+ * device-wide synchronisation and the possible failure of cudaMalloc in the
+ * middle of a run.  It computes the same sets as edfa_build for the static
+ * modes EDFA_Q_OWN, EDFA_Q_NBR, EDFA_Q_CROW and EDFA_Q_THRESH (thresh used by
+ * the last one); the paper has no counterpart of this entry point.
+ *
+ * A, B, C: the blocks as for edfa_build (device CSR, validated here).
+ * qptr:    caller-owned device array of N_e + 1 int64, receives the offsets.
+ * qidx:    caller-owned device array of qidx_capacity int32, receives the
+ *          sets, ascending per cell.
+ * qtot:    host pointer, receives the total size qptr[N_e].
+ * Working memory comes from one fixed device array of
+ * EDFA_NOALLOC_SCRATCH_BYTES inside the library (held by every GPU that
+ * loads the library until the process exits); the call needs
+ * 8 (N_e+1) x 2 + 4 nnz(B) + 8 (N_e/2048 + 2) + 512 bytes of it, rounded up to
+ * 256-byte pieces.  A problem that needs more returns EDFA_ERR_BOUNDS before
+ * touching the device, with the needed bytes in edfa_last_error_detail.  If
+ * the sets do not fit in qidx_capacity the call returns EDFA_ERR_BOUNDS with
+ * the needed capacity in *qtot and edfa_last_error_detail (qidx untouched).
+ *
+ * The first call on a device looks up the device address of the fixed array
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call reuses the same array and leaves
+ * its contents behind (the parts that must start at zero are cleared on each
+ * call), so calls whose work overlaps on the GPU (different streams or host
+ * threads at the same time) race and must not be issued.  The call
+ * synchronises `stream` once, to read the total size; the fill of qidx is
+ * then enqueued on `stream`.  Calls no allocating CUDA or library routine. */
+#define EDFA_NOALLOC_SCRATCH_BYTES (64ull << 20)
+EDFA_API int edfa_qsets_noalloc(const edfa_csr* A, const edfa_csr* B, const edfa_csr* C, int32_t qmode,
+                                double thresh, int64_t* qptr, int32_t* qidx, int64_t qidx_capacity,
+                                int64_t* qtot, edfa_stream stream);
+
 /* Number of CUDA kernels this library has launched in this process. */
 EDFA_API int64_t edfa_launch_count(void);
 

@@ -69,7 +69,8 @@ class View(C.Structure):
 _lib = None
 EXPORTS = ("edfa_default_options", "edfa_build", "edfa_setup", "edfa_apply", "edfa_matvec",
            "edfa_solve", "edfa_history", "edfa_get_view", "edfa_get_stats", "edfa_set_profiling",
-           "edfa_launch_count", "edfa_free", "edfa_strerror", "edfa_last_error_detail")
+           "edfa_launch_count", "edfa_qsets_noalloc", "edfa_free", "edfa_strerror",
+           "edfa_last_error_detail")
 
 
 def lib_path() -> str:
@@ -102,6 +103,9 @@ def lib(build_if_missing: bool = True):
         L.edfa_free.argtypes = [vp]
         L.edfa_set_profiling.argtypes = [vp, C.c_int32]
         L.edfa_set_profiling.restype = C.c_int
+        L.edfa_qsets_noalloc.argtypes = [P(Csr), P(Csr), P(Csr), C.c_int32, C.c_double, vp, vp, C.c_int64,
+                                         P(C.c_int64), vp]
+        L.edfa_qsets_noalloc.restype = C.c_int
         L.edfa_launch_count.argtypes = []
         L.edfa_launch_count.restype = C.c_int64
         L.edfa_strerror.argtypes = [C.c_int]
@@ -150,6 +154,19 @@ def edfa_solve(h, b_ptr: int, x_ptr: int, restart: int, rtol: float, maxit: int,
     if rc != EDFA_OK and not (rc == EDFA_ERR_NOT_CONVERGED and not raise_on_nonconv):
         raise EdfaError(rc, "edfa_solve", lib().edfa_last_error_detail())
     return info
+
+
+def qsets_noalloc(A, B, C_, Nf: int, Ne: int, qmode="nbr", thresh=0.05, qptr=None, qidx=None,
+                  stream=None):
+    """Restriction sets through edfa_qsets_noalloc (no device allocation inside
+    the library; the caller provides qptr [Ne+1] int64 and qidx int32).
+    Returns (rc, qtot)."""
+    tot = C.c_int64(0)
+    mode = QMODES[qmode] if isinstance(qmode, str) else int(qmode)
+    rc = lib().edfa_qsets_noalloc(C.byref(csr(*A, Nf)), C.byref(csr(*B, Ne)), C.byref(csr(*C_, Nf)), mode,
+                                  float(thresh), qptr.data_ptr(), qidx.data_ptr() if qidx is not None else None,
+                                  qidx.numel() if qidx is not None else 0, C.byref(tot), _stream(stream))
+    return rc, tot.value
 
 
 def launch_count() -> int:

@@ -2,6 +2,7 @@
 // restriction sets Q^(m) (Sec. 3, Eq. r_r^m; static technique; base pattern
 // Q_{A_ppi} = stored columns of row m of A_ppi).
 #include <climits>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -360,3 +361,152 @@ int to_f32(const double* in, float* out, int64_t n, cudaStream_t s)
 }
 
 }  // namespace edfa
+
+// ------------------------------------------------------------ no-allocation variant
+// edfa_qsets_noalloc: the static restriction sets with all working memory
+// taken from one fixed file-scope device array instead of cudaMalloc.  The
+// kernels are the ones the handle path uses.
+namespace edfa {
+
+static __device__ __align__(256) unsigned char g_qsets_scratch[EDFA_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+static void* g_scratch_addr[kMaxDevices] = {};
+static std::mutex g_scratch_mu;
+
+// device address of the fixed array on the current device (looked up once per device)
+static int scratch_address(void** out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return EDFA_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_qsets_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return EDFA_ERR_CUDA;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return EDFA_OK;
+}
+
+static size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// same three kernels as scan_i64, with the block partials in caller storage
+static int scan_i64_into(int64_t* data, int64_t n, int64_t* part, cudaStream_t s)
+{
+    int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    if (nb == 0) nb = 1;
+    (edfa::count_launch(), k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, part));
+    (edfa::count_launch(), k_scan_parts<<<1, kScanThreads, 0, s>>>(part, nb));
+    (edfa::count_launch(), k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, part));
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
+}  // namespace edfa
+
+extern "C" int edfa_qsets_noalloc(const edfa_csr* A, const edfa_csr* B, const edfa_csr* C, int32_t qmode,
+                                  double thresh, int64_t* qptr, int32_t* qidx, int64_t qidx_capacity,
+                                  int64_t* qtot, edfa_stream stream)
+{
+    using namespace edfa;
+    set_detail(-1);
+    if (!A || !B || !C || !qptr || !qtot || qidx_capacity < 0) return EDFA_ERR_INVALID;
+    if (qmode != EDFA_Q_OWN && qmode != EDFA_Q_NBR && qmode != EDFA_Q_CROW && qmode != EDFA_Q_THRESH)
+        return EDFA_ERR_INVALID;
+    if (qmode == EDFA_Q_THRESH && !(thresh >= 0.0)) return EDFA_ERR_INVALID;
+    const int32_t Nf = A->nrows, Ne = B->ncols;
+    if (Nf < 0 || Ne < 0 || A->ncols != Nf || B->nrows != Nf || C->nrows != Ne || C->ncols != Nf ||
+        A->nnz < 0 || B->nnz < 0 || C->nnz < 0)
+        return EDFA_ERR_INVALID;
+    // scratch layout, checked against the fixed size before any device work
+    const int64_t nb = ((int64_t)Ne + kScanChunk - 1) / kScanChunk + 1;
+    const size_t off_btp = 0;
+    const size_t off_btc = off_btp + round256(((size_t)Ne + 1) * sizeof(int64_t));
+    const size_t off_cur = off_btc + round256((size_t)(B->nnz > 0 ? B->nnz : 1) * sizeof(int32_t));
+    const size_t off_part = off_cur + round256(((size_t)Ne + 1) * sizeof(int64_t));
+    const size_t off_misc = off_part + round256(((size_t)nb + 1) * sizeof(int64_t));
+    const size_t need = off_misc + round256(sizeof(DevErr) + sizeof(int));
+    if (need > (size_t)EDFA_NOALLOC_SCRATCH_BYTES) {
+        set_detail((long long)need);
+        return EDFA_ERR_BOUNDS;
+    }
+    if ((Nf > 0 && (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val)))) ||
+        (Nf > 0 && (!B->rowptr || (B->nnz > 0 && (!B->col || !B->val)))) ||
+        (Ne > 0 && (!C->rowptr || (C->nnz > 0 && (!C->col || !C->val)))))
+        return EDFA_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* base = nullptr;
+    int rc = scratch_address((void**)&base);
+    if (rc) return rc;
+    int64_t* bt_ptr = (int64_t*)(base + off_btp);
+    int32_t* bt_col = (int32_t*)(base + off_btc);
+    unsigned long long* cursor = (unsigned long long*)(base + off_cur);
+    int64_t* part = (int64_t*)(base + off_part);
+    DevErr* err = (DevErr*)(base + off_misc);
+    int* qmax = (int*)(base + off_misc + sizeof(DevErr));
+    int nsm = 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm < 1) nsm = 1;
+
+    // state that must start at zero
+    cudaMemsetAsync(base + off_misc, 0, sizeof(DevErr) + sizeof(int), s);
+    cudaMemsetAsync(bt_ptr, 0, ((size_t)Ne + 1) * sizeof(int64_t), s);
+    cudaMemsetAsync(qptr, 0, ((size_t)Ne + 1) * sizeof(int64_t), s);
+    // input validation (same checks as edfa_build)
+    const edfa_csr* mats[3] = {A, B, C};
+    for (int k = 0; k < 3; ++k) {
+        int64_t n = (int64_t)mats[k]->nrows + 1;
+        (edfa::count_launch(), k_validate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(csr_of(*mats[k]), 0, err));
+    }
+    // B^T pattern: the faces of each cell
+    Csr<double> Bc = csr_of(*B);
+    if (Bc.nnz > 0)
+        (edfa::count_launch(), k_col_count<<<(unsigned)((Bc.nnz + 255) / 256), 256, 0, s>>>(Bc, (unsigned long long*)bt_ptr));
+    if ((rc = scan_i64_into(bt_ptr, Ne, part, s))) return rc;
+    cudaMemcpyAsync(cursor, bt_ptr, ((size_t)Ne + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+    if (Bc.nrows > 0) (edfa::count_launch(), k_col_fill<<<(unsigned)((Bc.nrows + 255) / 256), 256, 0, s>>>(Bc, cursor, bt_col));
+    if (Ne > 0) (edfa::count_launch(), k_row_sort<<<(unsigned)((Ne + 255) / 256), 256, 0, s>>>(bt_ptr, bt_col, Ne));
+    // counting pass, offsets, total
+    QArgs a{};
+    a.mode = qmode;
+    a.thresh = thresh;
+    a.Ne = Ne;
+    a.A = csr_of(*A);
+    a.B = Bc;
+    a.C = csr_of(*C);
+    a.bt_ptr = bt_ptr;
+    a.bt_col = bt_col;
+    a.err = err;
+    a.cnt = qptr;
+    a.qmax = qmax;
+    unsigned grid = (unsigned)((Ne + kQWarps - 1) / kQWarps);
+    unsigned cap = (unsigned)nsm * 16;
+    if (grid > cap) grid = cap;
+    if (grid == 0) grid = 1;
+    (edfa::count_launch(), k_qsets<0><<<grid, kQWarps * 32, 0, s>>>(a));
+    if ((rc = scan_i64_into(qptr, Ne, part, s))) return rc;
+    int64_t tot = 0;
+    DevErr e{};
+    cudaMemcpyAsync(&tot, qptr + Ne, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&e, err, sizeof(DevErr), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return EDFA_ERR_CUDA;
+    if (e.code != 0) {
+        set_detail(e.detail);
+        return e.code;
+    }
+    *qtot = tot;
+    if (tot > qidx_capacity) {
+        set_detail(tot);
+        return EDFA_ERR_BOUNDS;
+    }
+    if (tot > 0 && !qidx) return EDFA_ERR_INVALID;
+    a.qptr = qptr;
+    a.qidx = qidx;
+    (edfa::count_launch(), k_qsets<1><<<grid, kQWarps * 32, 0, s>>>(a));
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
