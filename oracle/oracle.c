@@ -255,9 +255,13 @@ ORC_EXPORT int orc_local_solves(const orc_csr* A, const orc_csr* B, const orc_cs
  * start from Q_(0) = the stored columns of row m of C, solve for g~, form the
  * prolonged residual r = c_m^T + A R^T g~ (Eq. prol_res), then repeatedly add
  * at most n = min(n_add, n_ent - n_prog) new indices j (j not in Q, A_jq
- * stored for some q in Q) with the largest |r_j| (ties: smaller j first),
+ * stored for some q in Q) with the largest |r_j| (values within a relative
+ * 1e-12 of the largest count as tied; ties: smaller j first),
  * re-solve and recompute r, while n_prog < n_ent and k < it_max.  The loop
  * also ends when no candidate index exists. */
+/* relative width of a tie between prolonged-residual magnitudes */
+#define DYN_TIE 1e-12
+
 static int dyn_one(const orc_csr* A, const orc_csr* C, int32_t m, int n_add, int n_ent,
                    int it_max, ilist* Q)
 {
@@ -304,12 +308,16 @@ static int dyn_one(const orc_csr* A, const orc_csr* C, int32_t m, int n_add, int
         int n = n_add < (n_ent - n_prog) ? n_add : (n_ent - n_prog);
         int added = 0;
         while (added < n) {
+            /* largest remaining |r_j|; every candidate within a relative
+               DYN_TIE of it counts as tied, and the smallest j among the tied
+               wins (candidates are ascending in j) */
+            double rmax = -1.0;
+            for (int64_t t = 0; t < nc; ++t)
+                if (rv[t] >= 0 && rv[t] > rmax) rmax = rv[t];
+            if (rmax < 0) break;
             int64_t best = -1;
-            for (int64_t t = 0; t < nc; ++t) {
-                if (rv[t] < 0) continue; /* taken */
-                if (best < 0 || rv[t] > rv[best]) best = t; /* ascending j: ties keep smaller j */
-            }
-            if (best < 0) break;
+            for (int64_t t = 0; t < nc; ++t)
+                if (rv[t] >= 0 && rv[t] >= rmax * (1.0 - DYN_TIE)) { best = t; break; }
             il_push(Q, cj.v[best]);
             rv[best] = -1.0;
             added++;

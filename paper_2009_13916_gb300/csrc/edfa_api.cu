@@ -448,9 +448,3 @@ int edfa_free(edfa_handle h)
 }
 
 }  // extern "C"
-
-// dynamic restriction sets are provided by k_dynamic.cu when built; until then
-// the option is rejected.
-namespace edfa {
-__attribute__((weak)) int build_qsets_dynamic(edfa_handle_s*, cudaStream_t) { return EDFA_ERR_UNSUPPORTED; }
-}  // namespace edfa

@@ -180,3 +180,21 @@ def test_local_breakdown_reports_cell():
     assert e.value.code == 4
     owners = set(int(c) for c in sysd.face_cells[f] if c >= 0)
     assert e.value.detail in owners
+
+
+@pytest.mark.parametrize("dyn", [(1, 4, 100), (2, 6, 10), (4, 6, 1), (3, 0, 5)])
+def test_dynamic_sets_parity(dyn):
+    # Algorithm 1 (dynamic branch): sets grown by the prolonged residual
+    torch = _torch()
+    sysd = full_tensor((7, 6, 5), seed=23)
+    ref = O.edfa_pipeline(sysd, mode="dynamic", dyn=dyn, solve=True)
+    h = gpu_handle(sysd, mode="dynamic", dyn=dyn)
+    g = gpu_results(h)
+    assert np.array_equal(g["qptr"], ref["qptr"])
+    assert np.array_equal(g["qidx"], ref["qidx"])
+    assert normwise_cols_fast(g["xval"], ref["xval"], ref["qptr"]) <= TOL_FP64
+    assert np.array_equal(g["s_col"], ref["S"].col)
+    assert normwise_cols_fast(g["s_val"], ref["S"].val, ref["S"].rowptr) <= TOL_FP64
+    x, info = h.solve(torch.as_tensor(sysd.b, device="cuda"), restart=50, rtol=1e-8, maxit=2000)
+    assert info.converged and abs(info.iterations - ref["iters"]) <= 1
+    h.close()

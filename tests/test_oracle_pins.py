@@ -281,8 +281,14 @@ def test_dynamic_first_step_adds_largest_residual_entries():
             r = Cd[m].copy()
             r += Ad[:, q0] @ g  # prolonged residual, Eq. (prol_res)
             cand = [j for j in range(sysd.Nf) if j not in q0 and np.any(Ad[j, q0] != 0)]
-            order = sorted(cand, key=lambda j: (-abs(r[j]), j))
-            ref = sorted(q0 + order[:n_add])
+            picked = []
+            for _ in range(n_add):
+                left = [j for j in cand if j not in picked]
+                if not left:
+                    break
+                rmax = max(abs(r[j]) for j in left)
+                picked.append(min(j for j in left if abs(r[j]) >= rmax * (1 - 1e-12)))
+            ref = sorted(q0 + picked)
             assert list(qidx[qptr[m]:qptr[m + 1]]) == ref
     qptr0, qidx0 = O.qsets_dynamic(sysd.A, sysd.C, 2, 0, 5)
     qptr1, qidx1 = O.qsets("crow", sysd.A, sysd.B, sysd.C)
