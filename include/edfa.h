@@ -177,6 +177,30 @@ EDFA_API int edfa_get_stats(edfa_handle h, edfa_stats* s);
  * accumulated sweep times.  Timing adds one event pair per sweep launch. */
 EDFA_API int edfa_set_profiling(edfa_handle h, int32_t on);
 
+/* Preconditioner for the transposed system [A B; C D]^T = [A C^T; B^T D^T]
+ * (adjoint solves), built from the forward handle `fwd`: the transposed blocks
+ * C^T, B^T, D^T are formed on the device and owned by the new handle; the
+ * forward restriction sets are reused, so every local system A^(m) is the
+ * same and only the right-hand sides swap roles (the F~/G~ roles of
+ * Eq. EDFA_systems_1/2 exchange).  With schur_form = 1 the new S~ is exactly
+ * the transpose of the forward S~.  `fwd` must stay alive during the call
+ * only.  Synchronises `stream` like edfa_build. */
+EDFA_API int edfa_build_adjoint(edfa_handle* adj, edfa_handle fwd, edfa_stream stream);
+
+/* Gradient of a scalar L(u) with respect to the per-cell log-conductivities
+ * theta_E = log k_E of an isotropic brick-grid MHFE-FV system with strong-flux
+ * cell rows (Eq. fluxes_MHFEM_STRONG, Appendix A) and prescribed pressures on
+ * faces:  grad_E = lambda^T (d b / d theta_E - d A / d theta_E u), where
+ * A^T lambda = dL/du (the adjoint solve) and A u = b.  All arrays are device
+ * memory:  cell_faces [Ne*6] (local order x-,x+,y-,y+,z-,z+), face_cells
+ * [Nf*2] (minus-side cell, plus-side cell, -1 = none), face_dir [Nf] (1 =
+ * prescribed pressure), face_pbar [Nf], W [Ne*36] the inverse elemental
+ * matrices (B^E)^{-1} row-major, u and lambda [Nf+Ne], grad [Ne] (output).
+ * Asynchronous on `stream`. */
+EDFA_API int edfa_grad_logk(int32_t Nf, int32_t Ne, const int32_t* cell_faces, const int32_t* face_cells,
+                            const int8_t* face_dir, const double* face_pbar, const double* W,
+                            const double* u, const double* lam, double* grad, edfa_stream stream);
+
 /* Restriction sets Q^(m) without any device memory allocation.
  *
  * For callers that must not allocate device memory after start-up: host

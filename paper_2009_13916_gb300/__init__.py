@@ -69,7 +69,8 @@ class View(C.Structure):
 _lib = None
 EXPORTS = ("edfa_default_options", "edfa_build", "edfa_setup", "edfa_apply", "edfa_matvec",
            "edfa_solve", "edfa_history", "edfa_get_view", "edfa_get_stats", "edfa_set_profiling",
-           "edfa_launch_count", "edfa_qsets_noalloc", "edfa_free", "edfa_strerror",
+           "edfa_launch_count", "edfa_qsets_noalloc", "edfa_build_adjoint", "edfa_grad_logk",
+           "edfa_free", "edfa_strerror",
            "edfa_last_error_detail")
 
 
@@ -106,6 +107,10 @@ def lib(build_if_missing: bool = True):
         L.edfa_qsets_noalloc.argtypes = [P(Csr), P(Csr), P(Csr), C.c_int32, C.c_double, vp, vp, C.c_int64,
                                          P(C.c_int64), vp]
         L.edfa_qsets_noalloc.restype = C.c_int
+        L.edfa_build_adjoint.argtypes = [P(vp), vp, vp]
+        L.edfa_build_adjoint.restype = C.c_int
+        L.edfa_grad_logk.argtypes = [C.c_int32, C.c_int32] + [vp] * 8 + [vp]
+        L.edfa_grad_logk.restype = C.c_int
         L.edfa_launch_count.argtypes = []
         L.edfa_launch_count.restype = C.c_int64
         L.edfa_strerror.argtypes = [C.c_int]
@@ -167,6 +172,19 @@ def qsets_noalloc(A, B, C_, Nf: int, Ne: int, qmode="nbr", thresh=0.05, qptr=Non
                                   float(thresh), qptr.data_ptr(), qidx.data_ptr() if qidx is not None else None,
                                   qidx.numel() if qidx is not None else 0, C.byref(tot), _stream(stream))
     return rc, tot.value
+
+
+def grad_logk(geom, u, lam, Nf: int, Ne: int, stream=None):
+    """edfa_grad_logk on device tensors; geom = dict(cell_faces int32 [Ne,6],
+    face_cells int32 [Nf,2], face_dir int8 [Nf], face_pbar f64 [Nf], W f64 [Ne,6,6])."""
+    import torch
+    g = torch.empty(Ne, dtype=torch.float64, device=u.device)
+    rc = lib().edfa_grad_logk(int(Nf), int(Ne), geom["cell_faces"].data_ptr(), geom["face_cells"].data_ptr(),
+                              geom["face_dir"].data_ptr(), geom["face_pbar"].data_ptr(), geom["W"].data_ptr(),
+                              u.data_ptr(), lam.data_ptr(), g.data_ptr(), C.c_void_p(_stream(stream)))
+    if rc != EDFA_OK:
+        raise EdfaError(rc, "edfa_grad_logk")
+    return g
 
 
 def launch_count() -> int:
@@ -262,6 +280,20 @@ class Edfa:
         buf = (C.c_double * 100000)()
         n = lib().edfa_history(self.h, buf, 100000)
         return np.array(buf[:n])
+
+    def adjoint(self, stream=None) -> "Edfa":
+        """Handle for the transposed system [A C^T; B^T D^T] (edfa_build_adjoint)."""
+        h = C.c_void_p()
+        rc = lib().edfa_build_adjoint(C.byref(h), self.h, C.c_void_p(_stream(stream)))
+        if rc != EDFA_OK:
+            raise EdfaError(rc, "edfa_build_adjoint", lib().edfa_last_error_detail())
+        adj = Edfa.__new__(Edfa)
+        adj._keep = [self]
+        adj.Nf, adj.Ne = self.Nf, self.Ne
+        adj.opt = self.opt
+        adj._D = None
+        adj.h = h
+        return adj
 
     def set_profiling(self, on: bool):
         lib().edfa_set_profiling(self.h, 1 if on else 0)

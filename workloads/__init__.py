@@ -431,3 +431,31 @@ def config5_reassemble(sysd: System, logk: np.ndarray) -> System:
     out.extra.update(sysd.extra)
     out.extra["logk"] = logk.copy()
     return out
+
+
+def device_assembler(template: System, device="cuda"):
+    """Callable theta -> device system for the differentiable solve: re-assembles
+    the isotropic strong-flux system of `template`'s grid with k = exp(theta)
+    (host generator) and returns CUDA tensors (CSR triples, b, grid arrays)."""
+    import torch
+
+    def t(M):
+        return (torch.as_tensor(M.rowptr, dtype=torch.int64, device=device),
+                torch.as_tensor(M.col, dtype=torch.int32, device=device),
+                torch.as_tensor(M.val, dtype=torch.float64, device=device))
+
+    def assemble_theta(theta):
+        lk = theta.detach().double().cpu().numpy()
+        s = assemble(template.nx, template.ny, template.nz, iso_K(np.exp(lk)), h=template.h, dt=template.dt,
+                     stor=template.stor, name=template.name + " (theta)")
+        return dict(
+            A=t(s.A), B=t(s.B), C=t(s.C), D=t(s.D), Nf=s.Nf, Ne=s.Ne,
+            b=torch.as_tensor(s.f_phys, dtype=torch.float64, device=device),
+            cell_faces=torch.as_tensor(s.cell_faces, dtype=torch.int32, device=device).contiguous(),
+            face_cells=torch.as_tensor(s.face_cells, dtype=torch.int32, device=device).contiguous(),
+            face_dir=torch.as_tensor(s.face_dir.astype(np.int8), device=device).contiguous(),
+            face_pbar=torch.as_tensor(s.face_pbar, dtype=torch.float64, device=device),
+            W=torch.as_tensor(s.W, dtype=torch.float64, device=device).contiguous(),
+            host=s)
+
+    return assemble_theta
