@@ -124,6 +124,9 @@ typedef struct {
        backward, S~ forward, S~ backward */
     double sweep_ms[4];
     int64_t sweep_n[4];
+    /* launch shapes picked by the autotuner (lanes per local system, warps per
+       block of the local-solve kernel, warps per block of the Schur kernel) */
+    int32_t tuned_lanes, tuned_warps, tuned_schur_warps;
 } edfa_stats;
 
 /* Read-only views of what the handle computed (device pointers, valid until
@@ -165,6 +168,26 @@ EDFA_API int edfa_matvec(edfa_handle h, const double* x, double* y, edfa_stream 
  * (x then holds the last iterate).  info may be NULL. */
 EDFA_API int edfa_solve(edfa_handle h, const double* b, double* x, int32_t restart, double rtol,
                int32_t maxit, edfa_solve_info* info, edfa_stream stream);
+
+/* Batched solve of many independent systems held block-diagonally in one
+ * handle (the caller concatenates the systems: system i owns faces
+ * [face_off[i], face_off[i+1]) and cells [cell_off[i], cell_off[i+1]), with no
+ * coupling between systems; build the handle once over the concatenation, so
+ * the restriction sets, local solves, S~ and ILU(0) of all systems run in
+ * single launches).  One FGMRES(restart) per system, x0 = 0, stopping rule
+ * ||b_i - A_i x_i|| / ||b_i|| <= rtol per system; the systems advance in lock
+ * step (a system stops iterating once it has converged), reductions are per
+ * system and the Hessenberg/Givens updates run on the device.  One restart
+ * cycle is captured as a CUDA graph and replayed until every system has
+ * converged or reached maxit inner iterations.
+ * face_off, cell_off: host arrays of nsys+1 entries (face_off[nsys] = N_f,
+ * cell_off[nsys] = N_e).  iterations, true_rel: host arrays of nsys entries
+ * (may be NULL); cycles: host (may be NULL).  Workspace ((2 restart + 2) (N_f +
+ * N_e) doubles) is kept by the handle for further calls with the same layout.
+ * Returns EDFA_ERR_NOT_CONVERGED when some system did not converge. */
+EDFA_API int edfa_solve_batched(edfa_handle h, int32_t nsys, const int64_t* face_off, const int64_t* cell_off,
+                                const double* b, double* x, int32_t restart, double rtol, int32_t maxit,
+                                int32_t* iterations, double* true_rel, int32_t* cycles, edfa_stream stream);
 
 /* Residual-estimate history of the last edfa_solve (host array of
  * iterations+1 entries, hist[0] = 1); returns the number written. */

@@ -56,7 +56,8 @@ class Stats(C.Structure):
                 ("ms_ilu_a", C.c_float), ("ms_stage2", C.c_float), ("ms_solve", C.c_float),
                 ("n_local", C.c_int64), ("q_total", C.c_int64), ("q_max", C.c_int32),
                 ("s_nnz", C.c_int64), ("levels_a", C.c_int32), ("levels_s", C.c_int32),
-                ("sweep_ms", C.c_double * 4), ("sweep_n", C.c_int64 * 4)]
+                ("sweep_ms", C.c_double * 4), ("sweep_n", C.c_int64 * 4),
+                ("tuned_lanes", C.c_int32), ("tuned_warps", C.c_int32), ("tuned_schur_warps", C.c_int32)]
 
 
 class View(C.Structure):
@@ -70,6 +71,7 @@ _lib = None
 EXPORTS = ("edfa_default_options", "edfa_build", "edfa_setup", "edfa_apply", "edfa_matvec",
            "edfa_solve", "edfa_history", "edfa_get_view", "edfa_get_stats", "edfa_set_profiling",
            "edfa_launch_count", "edfa_qsets_noalloc", "edfa_build_adjoint", "edfa_grad_logk",
+           "edfa_solve_batched",
            "edfa_free", "edfa_strerror",
            "edfa_last_error_detail")
 
@@ -111,6 +113,9 @@ def lib(build_if_missing: bool = True):
         L.edfa_build_adjoint.restype = C.c_int
         L.edfa_grad_logk.argtypes = [C.c_int32, C.c_int32] + [vp] * 8 + [vp]
         L.edfa_grad_logk.restype = C.c_int
+        L.edfa_solve_batched.argtypes = [vp, C.c_int32, vp, vp, vp, vp, C.c_int32, C.c_double, C.c_int32,
+                                         vp, vp, vp, vp]
+        L.edfa_solve_batched.restype = C.c_int
         L.edfa_launch_count.argtypes = []
         L.edfa_launch_count.restype = C.c_int64
         L.edfa_strerror.argtypes = [C.c_int]
@@ -280,6 +285,26 @@ class Edfa:
         buf = (C.c_double * 100000)()
         n = lib().edfa_history(self.h, buf, 100000)
         return np.array(buf[:n])
+
+    def solve_batched(self, face_off, cell_off, b, x=None, restart=50, rtol=1e-8, maxit=2000, stream=None):
+        """One FGMRES per block-diagonal subsystem (edfa_solve_batched).
+        Returns (x, iterations[nsys], true_rel[nsys], cycles, rc)."""
+        import numpy as np
+        import torch
+        fo = np.ascontiguousarray(face_off, dtype=np.int64)
+        co = np.ascontiguousarray(cell_off, dtype=np.int64)
+        nsys = len(fo) - 1
+        if x is None:
+            x = torch.empty_like(b)
+        it = np.zeros(nsys, dtype=np.int32)
+        tr = np.zeros(nsys, dtype=np.float64)
+        cyc = C.c_int32(0)
+        rc = lib().edfa_solve_batched(self.h, nsys, fo.ctypes.data, co.ctypes.data, b.data_ptr(), x.data_ptr(),
+                                      int(restart), float(rtol), int(maxit), it.ctypes.data, tr.ctypes.data,
+                                      C.byref(cyc), C.c_void_p(_stream(stream)))
+        if rc not in (EDFA_OK, EDFA_ERR_NOT_CONVERGED):
+            raise EdfaError(rc, "edfa_solve_batched", lib().edfa_last_error_detail())
+        return x, it, tr, cyc.value, rc
 
     def adjoint(self, stream=None) -> "Edfa":
         """Handle for the transposed system [A C^T; B^T D^T] (edfa_build_adjoint)."""

@@ -71,6 +71,7 @@ int check_err(edfa_handle_s* h, cudaStream_t s)
 static void free_all(edfa_handle_s* h)
 {
     if (!h) return;
+    if (h->batch_del) h->batch_del(h->batch);
     for (auto& b : h->owned) cudaFree(b.p);
     h->owned.clear();
     if (h->err_host) cudaFreeHost(h->err_host);

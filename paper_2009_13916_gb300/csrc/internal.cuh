@@ -175,6 +175,9 @@ struct edfa_handle_s {
     edfa_stats stats{};
     std::vector<double> hist;
     std::vector<edfa::DBuf> owned;  // every device allocation, released by edfa_free
+    // workspace of the batched solve, reused across calls with the same layout
+    void* batch = nullptr;
+    void (*batch_del)(void*) = nullptr;
 };
 
 namespace edfa {

@@ -18,6 +18,9 @@
 //  * a zero, positive or non-finite pivot raises EDFA_ERR_BREAKDOWN with the
 //    cell index;
 //  * results are written coalesced, in the order of Q^(m).
+#include <mutex>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace edfa {
@@ -193,13 +196,73 @@ static int launch_local_t(edfa_handle_s* h, const LocalArgs<T>& a, int warps, cu
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
+// Autotuner: lanes per local system (LPC) and warps per block are chosen by
+// timing the candidates on a prefix sample of the cells (results for those
+// cells are overwritten by the full launch); the choice is cached per
+// (precision, right-hand sides, set-size pitch).
+struct TuneKey {
+    int tsize, nrhs, pitch;
+    bool operator==(const TuneKey& o) const { return tsize == o.tsize && nrhs == o.nrhs && pitch == o.pitch; }
+};
+struct TuneVal {
+    int lpc, warps;
+};
+static std::mutex g_tune_mu;
+static std::vector<std::pair<TuneKey, TuneVal>> g_tune;
+
+template <class T, int NRHS>
+static int launch_local_cfg(edfa_handle_s* h, const LocalArgs<T>& a, int lpc, int warps, cudaStream_t s)
+{
+    if (lpc == 8) return launch_local_t<T, NRHS, 8>(h, a, warps, s);
+    if (lpc == 16) return launch_local_t<T, NRHS, 16>(h, a, warps, s);
+    return launch_local_t<T, NRHS, 32>(h, a, warps, s);
+}
+
 template <class T, int NRHS>
 static int launch_local_n(edfa_handle_s* h, const LocalArgs<T>& a, cudaStream_t s)
 {
-    int warps = h->opt.warps_per_block > 0 ? h->opt.warps_per_block : 8;
-    if (a.pitch <= 40) return launch_local_t<T, NRHS, 8>(h, a, warps, s);
-    if (a.pitch <= 72) return launch_local_t<T, NRHS, 16>(h, a, warps, s);
-    return launch_local_t<T, NRHS, 32>(h, a, warps, s);
+    int lpc = a.pitch <= 40 ? 8 : (a.pitch <= 72 ? 16 : 32);
+    int warps = 8;
+    if (h->opt.warps_per_block > 0) {
+        warps = h->opt.warps_per_block;
+    } else if (a.Ne >= 32768) {
+        const TuneKey key{(int)sizeof(T), NRHS, a.pitch};
+        bool found = false;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            for (auto& kv : g_tune)
+                if (kv.first == key) { lpc = kv.second.lpc; warps = kv.second.warps; found = true; }
+        }
+        if (!found) {
+            LocalArgs<T> sample = a;
+            sample.Ne = 16384;
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            float best = 1e30f;
+            const int lpcs[3] = {8, 16, 32};
+            const int wps[2] = {4, 8};
+            for (int li = 0; li < 3; ++li)
+                for (int wi = 0; wi < 2; ++wi) {
+                    const int c = lpcs[li], w = wps[wi];
+                    if (launch_local_cfg<T, NRHS>(h, sample, c, w, s)) { cudaGetLastError(); continue; }
+                    cudaEventRecord(e0, s);
+                    if (launch_local_cfg<T, NRHS>(h, sample, c, w, s)) { cudaGetLastError(); continue; }
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best) { best = ms; lpc = c; warps = w; }
+                }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tune.push_back({key, TuneVal{lpc, warps}});
+        }
+    }
+    h->stats.tuned_lanes = lpc;
+    h->stats.tuned_warps = warps;
+    return launch_local_cfg<T, NRHS>(h, a, lpc, warps, s);
 }
 
 int run_local_solves(edfa_handle_s* h, cudaStream_t s)

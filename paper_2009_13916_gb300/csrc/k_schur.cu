@@ -18,7 +18,6 @@ namespace edfa {
 
 constexpr int kHS = 1024;      // hash capacity (columns of one S~ row, before load-factor limit)
 constexpr int kUCap = 512;     // two-sided: faces reached by G~_E A
-constexpr int kSWarps = 2;
 
 // ------------------------------------------------------------ X~ rows
 __global__ void k_q_count(const int32_t* qidx, int64_t tot, unsigned long long* cnt)
@@ -138,7 +137,7 @@ __device__ int hs_compact_sort(const int* tab, int* out, int cap, int lane)
     return n;
 }
 
-template <class T, int PASS>
+template <class T, int PASS, int kSWarps>
 __global__ void __launch_bounds__(kSWarps * 32) k_schur(SchurArgs<T> a)
 {
     __shared__ int s_tab[kSWarps][kHS];
@@ -309,14 +308,45 @@ static int schur_t(edfa_handle_s* h, const T* xval, const T* gval, T** h_val, cu
     cudaMemsetAsync(h->s_ptr, 0, ((size_t)Ne + 1) * sizeof(int64_t), s);
     a.cnt = h->s_ptr;
     a.rowmax = rowmax;
+    // autotuned tile: warps (rows) per block of the Schur kernel, timed on a
+    // prefix sample of the rows with the counting pass
+    int sw = 2;
+    if (Ne >= 32768) {
+        SchurArgs<T> sample = a;
+        sample.Ne = 8192;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        const int cands[2] = {1, 2};
+        for (int c : cands) {
+            for (int rep = 0; rep < 2; ++rep) {
+                if (rep == 1) cudaEventRecord(e0, s);
+                if (c == 1) (edfa::count_launch(), k_schur<T, 0, 1><<<(unsigned)(h->nsm * 8), 32, 0, s>>>(sample));
+                else (edfa::count_launch(), k_schur<T, 0, 2><<<(unsigned)(h->nsm * 4), 64, 0, s>>>(sample));
+            }
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; sw = c; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaMemsetAsync(rowmax, 0, sizeof(int), s);
+        cudaMemsetAsync(h->s_ptr, 0, ((size_t)Ne + 1) * sizeof(int64_t), s);
+    }
+    h->stats.tuned_schur_warps = sw;
     int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_schur<T, 0>, kSWarps * 32, 0);
+    if (sw == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_schur<T, 0, 1>, 32, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_schur<T, 0, 2>, 64, 0);
     if (per < 1) per = 1;
     long long grid = (long long)per * h->nsm;
-    long long need = (Ne + kSWarps - 1) / kSWarps;
+    long long need = (Ne + sw - 1) / sw;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    (edfa::count_launch(), k_schur<T, 0><<<(unsigned)grid, kSWarps * 32, 0, s>>>(a));
+    if (sw == 1) (edfa::count_launch(), k_schur<T, 0, 1><<<(unsigned)grid, 32, 0, s>>>(a));
+    else (edfa::count_launch(), k_schur<T, 0, 2><<<(unsigned)grid, 64, 0, s>>>(a));
     rc = scan_i64(h, h->s_ptr, Ne, s);
     if (rc) return rc;
     int64_t nnz = 0;
@@ -333,7 +363,8 @@ static int schur_t(edfa_handle_s* h, const T* xval, const T* gval, T** h_val, cu
     a.s_col = h->s_col;
     a.h_val = *h_val;
     a.d_map = h->d_map;
-    (edfa::count_launch(), k_schur<T, 1><<<(unsigned)grid, kSWarps * 32, 0, s>>>(a));
+    if (sw == 1) (edfa::count_launch(), k_schur<T, 1, 1><<<(unsigned)grid, 32, 0, s>>>(a));
+    else (edfa::count_launch(), k_schur<T, 1, 2><<<(unsigned)grid, 64, 0, s>>>(a));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 

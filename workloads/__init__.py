@@ -459,3 +459,51 @@ def device_assembler(template: System, device="cuda"):
             host=s)
 
     return assemble_theta
+
+
+def concat(systems, name="batch"):
+    """Block-diagonal concatenation of independent systems: faces of all systems
+    first (system by system), then cells.  Returns (System, face_off, cell_off)."""
+    Nf = sum(s.Nf for s in systems)
+    Ne = sum(s.Ne for s in systems)
+    fo = np.zeros(len(systems) + 1, np.int64)
+    co = np.zeros(len(systems) + 1, np.int64)
+    for i, s in enumerate(systems):
+        fo[i + 1] = fo[i] + s.Nf
+        co[i + 1] = co[i] + s.Ne
+
+    def cat(get, roff, coff, nrows, ncols):
+        rps, cols, vals = [np.zeros(1, np.int64)], [], []
+        base = 0
+        for i, s in enumerate(systems):
+            M = get(s)
+            rps.append(M.rowptr[1:] + base)
+            cols.append(M.col.astype(np.int64) + coff[i])
+            vals.append(M.val)
+            base += M.nnz
+        return CSR(nrows, ncols, np.concatenate(rps), np.concatenate(cols).astype(np.int32), np.concatenate(vals))
+
+    A = cat(lambda s: s.A, fo, fo, Nf, Nf)
+    B = cat(lambda s: s.B, fo, co, Nf, Ne)
+    Cm = cat(lambda s: s.C, co, fo, Ne, Nf)
+    D = cat(lambda s: s.D, co, co, Ne, Ne)
+    b = np.concatenate([np.concatenate([s.b[: s.Nf] for s in systems]),
+                        np.concatenate([s.b[s.Nf:] for s in systems])])
+    f = np.concatenate([np.concatenate([s.f_phys[: s.Nf] for s in systems]),
+                        np.concatenate([s.f_phys[s.Nf:] for s in systems])])
+    big = System(name=name, nx=0, ny=0, nz=0, h=(0, 0, 0), Nf=Nf, Ne=Ne, A=A, B=B, C=Cm, D=D, b=b, f_phys=f,
+                 K=np.concatenate([s.K for s in systems]), W=np.concatenate([s.W for s in systems]),
+                 cell_faces=np.concatenate([s.cell_faces + fo[i] for i, s in enumerate(systems)]),
+                 face_cells=np.concatenate([np.where(s.face_cells >= 0, s.face_cells + co[i], -1)
+                                            for i, s in enumerate(systems)]),
+                 face_dir=np.concatenate([s.face_dir for s in systems]),
+                 face_pbar=np.concatenate([s.face_pbar for s in systems]),
+                 dt=systems[0].dt, stor=systems[0].stor, fv_kind=systems[0].fv_kind)
+    big.extra.update(qmode=systems[0].extra.get("qmode", "nbr"))
+    return big, fo, co
+
+
+def sub_vector(v, sysd_list, fo, co, i):
+    """Unknowns of system i (faces then cells) out of a concatenated vector."""
+    Nf = int(fo[-1])
+    return np.concatenate([v[fo[i]:fo[i + 1]], v[Nf + co[i]:Nf + co[i + 1]]])
