@@ -16,6 +16,18 @@
 
 #include "internal.cuh"
 
+// lanes per row of the sweeps over A~ and S~ (1 = thread per row) and the
+// dependencies a thread-per-row sweep holds in registers per round
+#ifndef EDFA_LPR_A
+#define EDFA_LPR_A 4
+#endif
+#ifndef EDFA_LPR_S
+#define EDFA_LPR_S 8
+#endif
+#ifndef EDFA_KMAX_ROW
+#define EDFA_KMAX_ROW 8
+#endif
+
 namespace edfa {
 
 constexpr int kFacWarps = 4;
@@ -617,6 +629,94 @@ k_sweep(const int32_t* __restrict__ perm, int64_t nslots, const int64_t* __restr
     }
 }
 
+// Thread-per-row sweep (same contract as k_sweep): a thread owns one row; the
+// products of dependencies that are already final are summed while the late
+// ones are polled, and the row is finished and stored from inside the polling
+// loop as soon as its last dependency arrives, so only ~3 dependent FP64
+// operations follow the last arrival (no shuffle reduction, and no thread waits
+// for another row of its warp before storing).
+template <class T, class TB, class TO, int FWD, int KMAX>
+__global__ void __launch_bounds__(kSweepThreads)
+k_sweep_row(const int32_t* __restrict__ perm, int64_t nslots, const int64_t* __restrict__ rowptr,
+            const int32_t* __restrict__ col, const T* __restrict__ lu, const int64_t* __restrict__ diag,
+            const T* __restrict__ dinv, const TB* __restrict__ base, const int64_t* __restrict__ mptr,
+            const int32_t* __restrict__ mcol, const T* __restrict__ mval, const TO* __restrict__ mv, TO* out,
+            unsigned long long* ticket, DevErr* err)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        long long t0 = claim(ticket, 32);
+        if (t0 >= nslots) break;
+        const long long t = t0 + lane;
+        const int i = (t < nslots) ? perm[t] : -1;
+        if (i < 0) continue;
+        const T bi = (T)to_d(base[i]);
+        const T di = FWD ? T(1) : dinv[i];
+        const int64_t b = rowptr[i], e = rowptr[i + 1];
+        const int64_t d = diag[i];
+        const int64_t lo = FWD ? b : d + 1, hi = FWD ? d : e;
+        T acc = T(0);
+        if (mptr) {
+            const int64_t mb = mptr[i], me = mptr[i + 1];
+            T a2 = T(0);
+            int64_t p = mb;
+            for (; p + 1 < me; p += 2) {
+                acc = fma(mval[p], (T)mv[mcol[p]], acc);
+                a2 = fma(mval[p + 1], (T)mv[mcol[p + 1]], a2);
+            }
+            if (p < me) acc = fma(mval[p], (T)mv[mcol[p]], acc);
+            acc += a2;
+        }
+        bool done = false;
+        for (int64_t c0 = lo; c0 < hi || !done; c0 += KMAX) {
+            int cj[KMAX];
+            T lv[KMAX], xv[KMAX];
+            unsigned pending = 0;
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {
+                const int64_t p = c0 + k;
+                cj[k] = p < hi ? col[p] : -1;
+                lv[k] = p < hi ? lu[p] : T(0);
+            }
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) xv[k] = cj[k] >= 0 ? ld_poll(out + cj[k]) : T(0);
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {
+                if (cj[k] < 0) continue;
+                if (is_sentinel(xv[k])) pending |= 1u << k;
+                else acc = fma(lv[k], xv[k], acc);
+            }
+            const bool last = c0 + KMAX >= hi;
+            unsigned it = 0;
+            while (pending && it < (kSpinLimit << 2)) {
+#pragma unroll
+                for (int k = 0; k < KMAX; ++k)
+                    if ((pending >> k) & 1u) {
+                        const T v = ld_poll(out + cj[k]);
+                        if (!is_sentinel(v)) {
+                            acc = fma(lv[k], v, acc);
+                            pending &= ~(1u << k);
+                        }
+                    }
+                ++it;
+                if (last && !pending) {
+                    st_relaxed(out + i, (TO)((bi - acc) * di));
+                    done = true;
+                }
+                if ((it & 255u) == 0u && err_set(err)) break;
+            }
+            if (pending) {
+                raise_err(err, EDFA_ERR_TIMEOUT, i);
+                pending = 0;
+            }
+            if (last && !done) {
+                st_relaxed(out + i, (TO)((bi - acc) * di));
+                done = true;
+            }
+        }
+    }
+}
+
 template <class T, class TB, class TO, int FWD, int LPR>
 static int launch_sweep(edfa_handle_s* h, const Factor& f, const TB* base, const int64_t* mptr, const int32_t* mcol,
                         const T* mval, const TO* mv, TO* out, cudaStream_t s)
@@ -629,14 +729,15 @@ static int launch_sweep(edfa_handle_s* h, const Factor& f, const TB* base, const
     const T* dinv = nullptr;
     if constexpr (sizeof(T) == 8) { lu = (const T*)f.lu64; dinv = (const T*)f.dinv64; }
     else { lu = (const T*)f.lu32; dinv = (const T*)f.dinv32; }
-    auto fn = k_sweep<T, TB, TO, FWD, LPR, (LPR >= 32 ? 1 : (LPR >= 16 ? 2 : 4))>;
+    auto fn = (LPR == 1) ? k_sweep_row<T, TB, TO, FWD, (EDFA_KMAX_ROW)>
+                         : k_sweep<T, TB, TO, FWD, (LPR > 1 ? LPR : 2), (LPR >= 32 ? 1 : (LPR >= 16 ? 2 : 4))>;
     // resident warps: enough to hold ~3 dependency levels of rows in flight
     // (fewer warps means fewer pollers competing for L2), 2..16 per SM
     int wps = h->opt.sweep_warps_per_sm;
     if (wps <= 0) {
         // 8 warps per SM, more when a level holds many more rows than that
         // (wide levels of batched systems are throughput-bound)
-        constexpr int RPW = 32 / LPR;
+        constexpr int RPW = 32 / (LPR > 1 ? LPR : 1);
         const double per_level = p.nlevels > 0 ? (double)p.nslots / p.nlevels : 1.0;
         wps = (int)(per_level / RPW / h->nsm);
         if (wps < 8) wps = 8;
@@ -670,12 +771,6 @@ static int launch_sweep(edfa_handle_s* h, const Factor& f, const TB* base, const
 //   z_p  = S~^{-1} (r_p - C y)           (C y fused into the L sweep of S~)
 //   z_pi = A~^{-1} (r_pi - B z_p)        (B z_p fused into the L sweep of A)
 // variant 1 (upper block triangular): z_p = S~^{-1} r_p, then z_pi as above.
-#ifndef EDFA_LPR_A
-#define EDFA_LPR_A 4
-#endif
-#ifndef EDFA_LPR_S
-#define EDFA_LPR_S 8
-#endif
 template <class T>
 static int apply_impl(edfa_handle_s* h, const double* r, double* z, cudaStream_t s)
 {
