@@ -97,6 +97,10 @@ typedef struct {
                                application, FP64 Krylov vectors, Arnoldi and true residual */
     int32_t warps_per_block;/* local-solve launch shape; 0 = default */
     int32_t sweep_warps_per_sm; /* resident warps per SM of the sync-free ILU(0) sweeps; 0 = default (16) */
+    int32_t sweep_mode;     /* S~ triangular sweeps: 0 = automatic (one 16-CTA thread-block cluster
+                               holding the solution in distributed shared memory when N_e values fit
+                               and the cluster can be scheduled, else sync-free all-SM sweeps);
+                               1 = sync-free all-SM sweeps only */
 } edfa_options;
 
 typedef struct edfa_handle_s* edfa_handle;
@@ -120,13 +124,18 @@ typedef struct {
     int64_t s_nnz;                                 /* nnz of S~ */
     int32_t levels_a, levels_s;                    /* dependency depth of the ILU(0) sweeps */
     /* with profiling on (edfa_set_profiling): accumulated device time and
-       launch count of the triangular sweeps, kind 0..3 = A~ forward, A~
-       backward, S~ forward, S~ backward */
-    double sweep_ms[4];
-    int64_t sweep_n[4];
+       launch count of the triangular sweeps, kind 0..4 = A~ forward, A~
+       backward, S~ forward, S~ backward (sync-free all-SM sweeps), both S~
+       sweeps in one thread-block-cluster launch */
+    double sweep_ms[5];
+    int64_t sweep_n[5];
     /* launch shapes picked by the autotuner (lanes per local system, warps per
        block of the local-solve kernel, warps per block of the Schur kernel) */
     int32_t tuned_lanes, tuned_warps, tuned_schur_warps;
+    /* 1 when both S~ sweeps run in one 16-CTA cluster (edfa_options.sweep_mode),
+       with the bytes of their packed level chunks */
+    int32_t s_cluster;
+    int64_t s_cluster_bytes;
 } edfa_stats;
 
 /* Read-only views of what the handle computed (device pointers, valid until

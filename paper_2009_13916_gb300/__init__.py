@@ -43,7 +43,7 @@ class Options(C.Structure):
                 ("n_ent", C.c_int32), ("it_max", C.c_int32), ("qptr", C.c_void_p),
                 ("qidx", C.c_void_p), ("schur_form", C.c_int32), ("variant", C.c_int32),
                 ("precision", C.c_int32), ("warps_per_block", C.c_int32),
-                ("sweep_warps_per_sm", C.c_int32)]
+                ("sweep_warps_per_sm", C.c_int32), ("sweep_mode", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -56,8 +56,9 @@ class Stats(C.Structure):
                 ("ms_ilu_a", C.c_float), ("ms_stage2", C.c_float), ("ms_solve", C.c_float),
                 ("n_local", C.c_int64), ("q_total", C.c_int64), ("q_max", C.c_int32),
                 ("s_nnz", C.c_int64), ("levels_a", C.c_int32), ("levels_s", C.c_int32),
-                ("sweep_ms", C.c_double * 4), ("sweep_n", C.c_int64 * 4),
-                ("tuned_lanes", C.c_int32), ("tuned_warps", C.c_int32), ("tuned_schur_warps", C.c_int32)]
+                ("sweep_ms", C.c_double * 5), ("sweep_n", C.c_int64 * 5),
+                ("tuned_lanes", C.c_int32), ("tuned_warps", C.c_int32), ("tuned_schur_warps", C.c_int32),
+                ("s_cluster", C.c_int32), ("s_cluster_bytes", C.c_int64)]
 
 
 class View(C.Structure):
@@ -228,7 +229,7 @@ class Edfa:
 
     def __init__(self, A, B, C_, D, Nf: int, Ne: int, qmode="own", thresh=0.05, n_add=1, n_ent=4,
                  it_max=100, qsets=None, schur_form=0, variant=0, precision=0, warps_per_block=0,
-                 sweep_warps_per_sm=0, stream=None):
+                 sweep_warps_per_sm=0, sweep_mode=0, stream=None):
         self._keep = [A, B, C_, D]
         self.Nf, self.Ne = int(Nf), int(Ne)
         opt = Options()
@@ -245,6 +246,7 @@ class Edfa:
         opt.precision = int(precision)
         opt.warps_per_block = int(warps_per_block)
         opt.sweep_warps_per_sm = int(sweep_warps_per_sm)
+        opt.sweep_mode = int(sweep_mode)
         self.opt = opt
         self._D = D
         self.h = edfa_build(csr(*A, self.Nf), csr(*B, self.Ne), csr(*C_, self.Nf), csr(*D, self.Ne), opt,

@@ -141,6 +141,7 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     edfa_options o;
     if (opt) o = *opt; else edfa_default_options(&o);
     if (o.qmode < EDFA_Q_OWN || o.qmode > EDFA_Q_GIVEN) return EDFA_ERR_INVALID;
+    if (o.sweep_mode < 0 || o.sweep_mode > 1) return EDFA_ERR_INVALID;
     if (o.qmode == EDFA_Q_GIVEN && (!o.qptr || !o.qidx)) return EDFA_ERR_INVALID;
     if (o.qmode == EDFA_Q_THRESH && !(o.thresh >= 0.0)) return EDFA_ERR_INVALID;
     if (o.qmode == EDFA_Q_DYNAMIC && (o.n_add < 0 || o.n_ent < 0 || o.it_max < 0)) return EDFA_ERR_INVALID;
@@ -208,6 +209,8 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     TRY(stage2_values(h, s));
     TRY(factor_plan(h, h->fs, Ne, h->s_nnz, h->s_ptr, h->s_col, s));
     TRY(factor_numeric(h, h->fs, h->s_val, h->s_val32, s));
+    TRY(cluster_plan_build(h, s));
+    TRY(cluster_plan_fill(h, s));
     cudaEventRecord(h->ev[7], s);
 
     // application temporaries
@@ -227,6 +230,8 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     h->stats.q_total = h->qtot;
     h->stats.q_max = h->qmax;
     h->stats.s_nnz = h->s_nnz;
+    h->stats.s_cluster = h->cp.state == 1;
+    h->stats.s_cluster_bytes = h->cp.state == 1 ? h->cp.bytes : 0;
     h->stats.levels_a = h->fa.fwd.nlevels;
     h->stats.levels_s = h->fs.fwd.nlevels;
     *out = h;
@@ -248,6 +253,7 @@ int edfa_setup(edfa_handle h, const edfa_csr* D, edfa_stream stream)
     cudaEventRecord(h->ev[6], s);
     rc = stage2_values(h, s);
     if (!rc) rc = factor_numeric(h, h->fs, h->s_val, h->s_val32, s);
+    if (!rc) rc = cluster_plan_fill(h, s);
     cudaEventRecord(h->ev[7], s);
     if (!rc) rc = check_err(h, s);
     if (rc) return rc;

@@ -102,6 +102,7 @@ struct SweepPlan {
     int32_t* perm = nullptr;  // [nslots]
     int64_t nslots = 0;
     int32_t nlevels = 0;
+    int64_t* loff = nullptr;  // [nlevels+1] start of every (padded) level in perm
 };
 
 struct Factor {
@@ -116,6 +117,29 @@ struct Factor {
     double* dinv64 = nullptr;  // 1 / U_ii
     float* dinv32 = nullptr;
     SweepPlan fwd, bwd;
+};
+
+// Packed per-CTA level chunks of both S~ sweeps for the single-cluster solve
+// (k_cluster.cu).  state: -1 not built, 0 not usable (falls back to the
+// sync-free sweeps), 1 ready.
+struct ClusterPlan {
+    int state = -1;
+    int32_t cap = 0;           // value slots per CTA
+    int nlf = 0, nlb = 0;      // levels of the forward / backward plans
+    int64_t nlists = 0;        // 16 x (nlf + nlb) row lists
+    int32_t* posf = nullptr;   // [n] slot * 16 + owner CTA of each row
+    int32_t* rowof = nullptr;  // [16][cap] row held in each slot (-1: none)
+    int64_t* lofs = nullptr;   // [nlists+1] first row of every list in lrows
+    int32_t* lrows = nullptr;  // [2n]
+    int64_t* lbyte = nullptr;  // [nlists+1] byte offset of every list's chunks
+    int64_t* lchunk = nullptr; // [nlists+1] global index of every list's first chunk
+    int64_t* meta = nullptr;   // [16][2] first byte and chunk count of every CTA
+    unsigned char* chunks = nullptr;
+    int64_t bytes = 0;
+    uint16_t* sz = nullptr;    // [16][szstride] chunk sizes (16-byte units | 0x8000 on a level's last chunk)
+    int32_t szstride = 0;
+    void* bslot = nullptr;     // [16*cap] right-hand side in slot order
+    size_t smem = 0;           // dynamic shared memory per CTA
 };
 
 }  // namespace edfa
@@ -150,6 +174,7 @@ struct edfa_handle_s {
     int64_t* d_map = nullptr;  // position of each D entry in S~
     // ILU(0) factors
     edfa::Factor fa, fs;
+    edfa::ClusterPlan cp;
     // sweep synchronisation
     int* flags = nullptr;          // [max(Nf, Ne)] completion epochs
     unsigned long long* ticket = nullptr;  // work counter, zeroed before every sync-free launch
@@ -167,7 +192,8 @@ struct edfa_handle_s {
     edfa::DevErr* err_host = nullptr;
     cudaEvent_t ev[8] = {};
     // opt-in per-sweep device timing: event pairs recorded around every sweep
-    // launch (kind 0..3 = A forward, A backward, S~ forward, S~ backward)
+    // launch (kind 0..4 = A forward, A backward, S~ forward, S~ backward, both S~ sweeps
+    // in one cluster launch)
     int profiling = 0;
     std::vector<cudaEvent_t> prof_ev;
     std::vector<int> prof_kind;
@@ -211,6 +237,12 @@ int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64
 int factor_numeric(edfa_handle_s* h, Factor& f, const double* vals64, const float* vals32,
                    cudaStream_t s);
 int apply_prec(edfa_handle_s* h, const double* r, double* z, cudaStream_t s);
+// single-cluster S~ solves (k_cluster.cu)
+int cluster_plan_build(edfa_handle_s* h, cudaStream_t s);
+int cluster_plan_fill(edfa_handle_s* h, cudaStream_t s);
+template <class T>
+int s_cluster_solve(edfa_handle_s* h, const double* rp, const int64_t* mptr, const int32_t* mcol, const T* mval,
+                    const T* mv, T* out, cudaStream_t s, cudaEvent_t* pe);
 int matvec(edfa_handle_s* h, const double* x, double* y, cudaStream_t s);
 int to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
 int to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t s);

@@ -260,6 +260,9 @@ static int make_plan(edfa_handle_s* h, SweepPlan& plan, int32_t n, const int64_t
     if (n > 0) (edfa::count_launch(), k_level_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, level, off, cursor, plan.perm));
     plan.nslots = nslots;
     plan.nlevels = nlev;
+    rc = dalloc_t(h, &plan.loff, (size_t)nlev + 1);
+    if (rc) return rc;
+    cudaMemcpyAsync(plan.loff, off, ((size_t)nlev + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
     cudaFreeAsync(off, s);
     cudaFreeAsync(cursor, s);
     cudaFreeAsync(level, s);
@@ -717,6 +720,29 @@ k_sweep_row(const int32_t* __restrict__ perm, int64_t nslots, const int64_t* __r
     }
 }
 
+// per-launch sweep timing (edfa_set_profiling): a pair of events per launch,
+// tagged 0 A fwd, 1 A bwd, 2 S fwd, 3 S bwd, 4 S fwd+bwd in one cluster launch
+static cudaEvent_t* prof_begin(edfa_handle_s* h, int kind, cudaStream_t s)
+{
+    if (!h->profiling) return nullptr;
+    if (h->prof_used * 2 + 2 > h->prof_ev.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            h->prof_ev.push_back(e);
+        }
+        h->prof_kind.resize(h->prof_ev.size() / 2);
+    }
+    cudaEvent_t* pe = &h->prof_ev[2 * h->prof_used];
+    h->prof_kind[h->prof_used] = kind;
+    h->prof_used++;
+    if (s != (cudaStream_t)-1) cudaEventRecord(pe[0], s);
+    return pe;
+}
+
+// an event pair for a launcher that records both events itself
+static cudaEvent_t* prof_begin_pair(edfa_handle_s* h, int kind) { return prof_begin(h, kind, (cudaStream_t)-1); }
+
 template <class T, class TB, class TO, int FWD, int LPR>
 static int launch_sweep(edfa_handle_s* h, const Factor& f, const TB* base, const int64_t* mptr, const int32_t* mcol,
                         const T* mval, const TO* mv, TO* out, cudaStream_t s)
@@ -744,21 +770,7 @@ static int launch_sweep(edfa_handle_s* h, const Factor& f, const TB* base, const
         if (wps > 64) wps = 64;
     }
     int grid = resident_grid(h, (const void*)fn, kSweepThreads, 0, wps);
-    cudaEvent_t* pe = nullptr;
-    if (h->profiling) {
-        if (h->prof_used * 2 + 2 > h->prof_ev.size()) {
-            for (int k = 0; k < 64; ++k) {
-                cudaEvent_t e;
-                cudaEventCreate(&e);
-                h->prof_ev.push_back(e);
-            }
-            h->prof_kind.resize(h->prof_ev.size() / 2);
-        }
-        pe = &h->prof_ev[2 * h->prof_used];
-        h->prof_kind[h->prof_used] = (&f == &h->fs ? 2 : 0) + (FWD ? 0 : 1);
-        h->prof_used++;
-        cudaEventRecord(pe[0], s);
-    }
+    cudaEvent_t* pe = prof_begin(h, (&f == &h->fs ? 2 : 0) + (FWD ? 0 : 1), s);
     (edfa::count_launch(), fn<<<grid, kSweepThreads, 0, s>>>(p.perm, p.nslots, f.rowptr, f.col, lu, f.diag, dinv, base, mptr, mcol, mval, mv, out,
                             h->ticket, h->err));
     if (pe) cudaEventRecord(pe[1], s);
@@ -792,30 +804,31 @@ static int apply_impl(edfa_handle_s* h, const double* r, double* z, cudaStream_t
         if (rc) return rc;
         rc = launch_sweep<T, T, T, 0, EDFA_LPR_A>(h, h->fa, u2, nullptr, nullptr, (const T*)nullptr, (const T*)nullptr, u1, s);
         if (rc) return rc;
-        // w = L_S^{-1} (r_p - C y)
-        rc = launch_sweep<T, double, T, 1, EDFA_LPR_S>(h, h->fs, rp, h->C.rowptr, h->C.col, cval, u1, u2, s);
+    }
+    // z_p = U_S^{-1} L_S^{-1} (r_p - C y)   (C y omitted in the upper-triangular variant);
+    // the FP64 path writes z_p directly, the FP32 path into a working-precision copy
+    T* zpw;
+    if constexpr (sizeof(T) == 8) zpw = zp;
+    else zpw = (T*)h->tmp3;
+    const bool cpl = h->opt.variant == 0;
+    if (h->cp.state == 1) {
+        rc = s_cluster_solve<T>(h, rp, cpl ? h->C.rowptr : nullptr, cpl ? h->C.col : nullptr, cpl ? cval : nullptr,
+                                cpl ? (const T*)u1 : nullptr, zpw, s, prof_begin_pair(h, 4));
         if (rc) return rc;
     } else {
-        rc = launch_sweep<T, double, T, 1, EDFA_LPR_S>(h, h->fs, rp, nullptr, nullptr, (const T*)nullptr, (const T*)nullptr, u2, s);
+        if (cpl) rc = launch_sweep<T, double, T, 1, EDFA_LPR_S>(h, h->fs, rp, h->C.rowptr, h->C.col, cval, u1, u2, s);
+        else rc = launch_sweep<T, double, T, 1, EDFA_LPR_S>(h, h->fs, rp, nullptr, nullptr, (const T*)nullptr, (const T*)nullptr, u2, s);
+        if (rc) return rc;
+        rc = launch_sweep<T, T, T, 0, EDFA_LPR_S>(h, h->fs, u2, nullptr, nullptr, (const T*)nullptr, (const T*)nullptr, zpw, s);
         if (rc) return rc;
     }
-    // z_p = U_S^{-1} w  (written in the output precision)
-    if constexpr (sizeof(T) == 8) {
-        rc = launch_sweep<T, T, double, 0, EDFA_LPR_S>(h, h->fs, u2, nullptr, nullptr, (const T*)nullptr, (const double*)nullptr, zp, s);
+    // v = L_A^{-1} (r_pi - B z_p), z_pi = U_A^{-1} v
+    rc = launch_sweep<T, double, T, 1, EDFA_LPR_A>(h, h->fa, rpi, h->B.rowptr, h->B.col, bval, zpw, u2, s);
+    if (rc) return rc;
+    rc = launch_sweep<T, T, double, 0, EDFA_LPR_A>(h, h->fa, u2, nullptr, nullptr, (const T*)nullptr, (const double*)nullptr, zpi, s);
+    if constexpr (sizeof(T) == 4) {
         if (rc) return rc;
-        // v = L_A^{-1} (r_pi - B z_p)
-        rc = launch_sweep<T, double, T, 1, EDFA_LPR_A>(h, h->fa, rpi, h->B.rowptr, h->B.col, bval, zp, u2, s);
-        if (rc) return rc;
-        rc = launch_sweep<T, T, double, 0, EDFA_LPR_A>(h, h->fa, u2, nullptr, nullptr, (const T*)nullptr, (const double*)nullptr, zpi, s);
-    } else {
-        T* zp32 = (T*)h->tmp3;
-        rc = launch_sweep<T, T, T, 0, EDFA_LPR_S>(h, h->fs, u2, nullptr, nullptr, (const T*)nullptr, (const T*)nullptr, zp32, s);
-        if (rc) return rc;
-        rc = launch_sweep<T, double, T, 1, EDFA_LPR_A>(h, h->fa, rpi, h->B.rowptr, h->B.col, bval, zp32, u2, s);
-        if (rc) return rc;
-        rc = launch_sweep<T, T, double, 0, EDFA_LPR_A>(h, h->fa, u2, nullptr, nullptr, (const T*)nullptr, (const double*)nullptr, zpi, s);
-        if (rc) return rc;
-        rc = to_f64_launch(zp32, zp, Ne, s);
+        rc = to_f64_launch(zpw, zp, Ne, s);
     }
     if (rc) return rc;
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
