@@ -120,8 +120,11 @@ def measured_peaks():
 def sweep_traffic_from_profile(kind_name: str):
     """DRAM bytes per launch of the dominant sweep from the committed ncu summary,
     or None when the kernel source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "sweep_s_c2_64.txt")
-    src = os.path.join(ROOT, "paper_2009_13916_gb300", "csrc", "k_ilu.cu")
+    if kind_name == "s_cluster":
+        path, srcname = os.path.join(ROOT, "profiles", "k_s_cluster_c2_64.md"), "k_cluster.cu"
+    else:
+        path, srcname = os.path.join(ROOT, "profiles", "sweep_s_c2_64.txt"), "k_ilu.cu"
+    src = os.path.join(ROOT, "paper_2009_13916_gb300", "csrc", srcname)
     try:
         txt = open(path).read()
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -131,8 +134,8 @@ def sweep_traffic_from_profile(kind_name: str):
     for line in txt.splitlines():
         if ":" in line:
             k, v = line.split(":", 1)
-            vals[k.strip()] = v.strip()
-    if vals.get("k_ilu.cu sha256[:16]") != digest:
+            vals[k.strip().strip("-* `")] = v.strip().strip("` ")
+    if vals.get(f"{srcname} sha256[:16]") != digest:
         return None
     v = vals.get(f"dram_bytes_per_launch {kind_name}")
     return int(v) if v else None
@@ -160,8 +163,8 @@ def run_device(P, torch, sysd, blocks, b, precision, steps, warmup, profile):
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     infos, stats = [], []
-    sweep_ms = [0.0] * 4
-    sweep_n = [0] * 4
+    sweep_ms = [0.0] * 5
+    sweep_n = [0] * 5
     l0 = P.launch_count()
     ev[0].record(stream)
     for k in range(steps):
@@ -170,7 +173,7 @@ def run_device(P, torch, sysd, blocks, b, precision, steps, warmup, profile):
         st = h.stats()
         infos.append(info)
         stats.append(st)
-        for q in range(4):
+        for q in range(5):
             sweep_ms[q] += st.sweep_ms[q]
             sweep_n[q] += st.sweep_n[q]
         h.close()
@@ -331,30 +334,36 @@ def main():
     local_ms = st.ms_qsets + st.ms_local
     lsps = sysd.Ne * world / (local_ms / 1e3) if local_ms > 0 else None
 
-    # roofline of the dominant kernel: the S~ sweeps (sync-free ILU(0) triangular solves)
-    kinds = ["A~ forward sweep", "A~ backward sweep", "S~ forward sweep (fused C y)", "S~ backward sweep"]
+    # roofline of the dominant kernel among the triangular sweeps (timed per
+    # launch with CUDA events on the launching stream while profiling is on)
+    kinds = ["k_sweep (A~ forward)", "k_sweep (A~ backward)", "k_sweep (S~ forward, fused C y)",
+             "k_sweep (S~ backward)", "k_s_cluster (S~ forward + backward in one 16-CTA cluster)"]
     tot = r64["sweep_ms"]
-    dom = max(range(4), key=lambda q: tot[q])
+    dom = max(range(5), key=lambda q: tot[q])
     n_launch = r64["sweep_n"][dom]
     avg_ms = tot[dom] / n_launch if n_launch else float("nan")
     Ne, Nf = sysd.Ne, sysd.Nf
     nnz_half_s = (st.s_nnz - Ne) // 2
     nnz_half_a = (sysd.A.nnz - Nf) // 2
+    # algorithmic bytes: 4-byte column + 8-byte value per off-diagonal factor
+    # entry, the row pointers / diagonal positions / 1/U_ii a minimal CSR
+    # sweep reads, the right-hand side read and the solution written
     per_launch = {
         0: 12 * nnz_half_a + Nf * (8 + 8 + 4 + 8 + 8),
         1: 12 * nnz_half_a + Nf * (8 + 8 + 4 + 8 + 8 + 8),
         2: 12 * nnz_half_s + 12 * sysd.C.nnz + 8 * (Ne + 1) + Ne * (8 + 8 + 4 + 8 + 8) + 8 * Nf,
         3: 12 * nnz_half_s + Ne * (8 + 8 + 4 + 8 + 8 + 8),
+        4: 12 * 2 * nnz_half_s + Ne * (8 + 8 + 8 + 4),
     }
     peak, peak_src = measured_peaks()
     achieved = per_launch[dom] / (avg_ms / 1e3) / 1e9 if n_launch else None
-    traffic = sweep_traffic_from_profile(["a_fwd", "a_bwd", "s_fwd", "s_bwd"][dom])
-    roofline = {"bound": "hbm", "kernel": f"k_sweep ({kinds[dom]})", "achieved": achieved, "peak": peak,
+    traffic = sweep_traffic_from_profile(["a_fwd", "a_bwd", "s_fwd", "s_bwd", "s_cluster"][dom])
+    roofline = {"bound": "hbm", "kernel": kinds[dom], "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": per_launch[dom], "avg_launch_ms": avg_ms,
                 "launches_timed": n_launch,
-                "note": "latency-bound: dependency depth A 193 / S~ 694 levels per sweep"}
+                "note": f"latency-bound: dependency depth A {st.levels_a} / S~ {st.levels_s} levels per sweep"}
 
     out = {
         "metric": METRIC, "value": t64, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -367,7 +376,9 @@ def main():
         "iterations": info.iterations, "true_rel": true_rel, "converged": bool(info.converged),
         "local_solves_per_s": lsps,
         "phases_ms": {"qsets": st.ms_qsets, "local_solves": st.ms_local, "schur": st.ms_schur,
-                      "ilu_A": st.ms_ilu_a, "stage2": st.ms_stage2, "solve": st.ms_solve},
+                      "ilu_A": st.ms_ilu_a, "stage2": st.ms_stage2, "solve": st.ms_solve,
+                      "stage2_split": {"s_values": st.ms_s_values, "s_level_plans": st.ms_s_plan,
+                                       "s_ilu0": st.ms_s_factor, "s_cluster_pack": st.ms_s_cluster}},
         "variants": {"fp32_mixed": {"value": t32, "unit": "s", "iterations": info32.iterations,
                                     "true_rel": info32.true_rel, "converged": bool(info32.converged),
                                     "speedup_vs_fp64": t64 / t32 if t32 else None}},

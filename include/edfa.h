@@ -136,6 +136,9 @@ typedef struct {
        with the bytes of their packed level chunks */
     int32_t s_cluster;
     int64_t s_cluster_bytes;
+    /* Stage 2 split: S~ values, S~ level plans (build only), numeric ILU(0) of
+       S~, packing of the cluster sweep chunks */
+    float ms_s_values, ms_s_plan, ms_s_factor, ms_s_cluster;
 } edfa_stats;
 
 /* Read-only views of what the handle computed (device pointers, valid until

@@ -58,7 +58,9 @@ class Stats(C.Structure):
                 ("s_nnz", C.c_int64), ("levels_a", C.c_int32), ("levels_s", C.c_int32),
                 ("sweep_ms", C.c_double * 5), ("sweep_n", C.c_int64 * 5),
                 ("tuned_lanes", C.c_int32), ("tuned_warps", C.c_int32), ("tuned_schur_warps", C.c_int32),
-                ("s_cluster", C.c_int32), ("s_cluster_bytes", C.c_int64)]
+                ("s_cluster", C.c_int32), ("s_cluster_bytes", C.c_int64),
+                ("ms_s_values", C.c_float), ("ms_s_plan", C.c_float), ("ms_s_factor", C.c_float),
+                ("ms_s_cluster", C.c_float)]
 
 
 class View(C.Structure):

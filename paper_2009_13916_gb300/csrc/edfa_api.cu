@@ -207,8 +207,11 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     // Stage 2 (Algorithm 2) with the given D
     cudaEventRecord(h->ev[6], s);
     TRY(stage2_values(h, s));
+    cudaEventRecord(h->ev[8], s);
     TRY(factor_plan(h, h->fs, Ne, h->s_nnz, h->s_ptr, h->s_col, s));
+    cudaEventRecord(h->ev[9], s);
     TRY(factor_numeric(h, h->fs, h->s_val, h->s_val32, s));
+    cudaEventRecord(h->ev[10], s);
     TRY(cluster_plan_build(h, s));
     TRY(cluster_plan_fill(h, s));
     cudaEventRecord(h->ev[7], s);
@@ -226,6 +229,10 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     cudaEventElapsedTime(&ms, h->ev[3], h->ev[4]); h->stats.ms_schur = ms;
     cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]); h->stats.ms_ilu_a = ms;
     cudaEventElapsedTime(&ms, h->ev[6], h->ev[7]); h->stats.ms_stage2 = ms;
+    cudaEventElapsedTime(&ms, h->ev[6], h->ev[8]); h->stats.ms_s_values = ms;
+    cudaEventElapsedTime(&ms, h->ev[8], h->ev[9]); h->stats.ms_s_plan = ms;
+    cudaEventElapsedTime(&ms, h->ev[9], h->ev[10]); h->stats.ms_s_factor = ms;
+    cudaEventElapsedTime(&ms, h->ev[10], h->ev[7]); h->stats.ms_s_cluster = ms;
     h->stats.n_local = Ne;
     h->stats.q_total = h->qtot;
     h->stats.q_max = h->qmax;
@@ -252,7 +259,10 @@ int edfa_setup(edfa_handle h, const edfa_csr* D, edfa_stream stream)
     h->D = *D;
     cudaEventRecord(h->ev[6], s);
     rc = stage2_values(h, s);
+    cudaEventRecord(h->ev[8], s);
+    cudaEventRecord(h->ev[9], s);
     if (!rc) rc = factor_numeric(h, h->fs, h->s_val, h->s_val32, s);
+    cudaEventRecord(h->ev[10], s);
     if (!rc) rc = cluster_plan_fill(h, s);
     cudaEventRecord(h->ev[7], s);
     if (!rc) rc = check_err(h, s);
@@ -260,6 +270,10 @@ int edfa_setup(edfa_handle h, const edfa_csr* D, edfa_stream stream)
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev[6], h->ev[7]);
     h->stats.ms_stage2 = ms;
+    cudaEventElapsedTime(&ms, h->ev[6], h->ev[8]); h->stats.ms_s_values = ms;
+    h->stats.ms_s_plan = 0;
+    cudaEventElapsedTime(&ms, h->ev[9], h->ev[10]); h->stats.ms_s_factor = ms;
+    cudaEventElapsedTime(&ms, h->ev[10], h->ev[7]); h->stats.ms_s_cluster = ms;
     return EDFA_OK;
 }
 

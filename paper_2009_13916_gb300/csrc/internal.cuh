@@ -45,6 +45,14 @@ __device__ __forceinline__ int ld_acquire(const int* p)
     return v;
 }
 
+// relaxed load of a flag (polling; pair with an acquire fence once it is seen)
+__device__ __forceinline__ int ld_relaxed_i32(const int* p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void st_release(int* p, int v)
 {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -190,7 +198,7 @@ struct edfa_handle_s {
     // device error record and its pinned host mirror
     edfa::DevErr* err = nullptr;
     edfa::DevErr* err_host = nullptr;
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[12] = {};
     // opt-in per-sweep device timing: event pairs recorded around every sweep
     // launch (kind 0..4 = A forward, A backward, S~ forward, S~ backward, both S~ sweeps
     // in one cluster launch)

@@ -14,6 +14,8 @@
 // EDFA_ERR_TIMEOUT and finishes.
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "internal.cuh"
 
 // lanes per row of the sweeps over A~ and S~ (1 = thread per row) and the
@@ -30,7 +32,7 @@
 
 namespace edfa {
 
-constexpr int kFacWarps = 4;
+constexpr int kFacWarps = 2;
 constexpr int kSweepThreads = 64;
 
 // next c work items for this warp (the counter is zeroed before each launch)
@@ -44,11 +46,12 @@ __device__ __forceinline__ long long claim(unsigned long long* ticket, int c)
 
 // ------------------------------------------------------------ levels
 // level(i) = 1 + max level(j) over the stored j < i (fwd) or j > i (bwd).
-// Computed by frontier expansion (Kahn's algorithm) in one cooperative,
-// persistent kernel: every row keeps a count of its unfinished dependencies;
-// the rows of level L decrement the counts of their dependents, and a row whose
-// count reaches zero joins level L+1.  One grid barrier per level, O(nnz)
-// work, no polling of unfinished rows.
+// Computed by frontier expansion (Kahn's algorithm) in one persistent launch
+// of a single 16-CTA thread-block cluster: every row keeps a count of its
+// unfinished dependencies; the rows of level L decrement the counts of their
+// dependents, and a row whose count reaches zero joins level L+1.  One cluster
+// barrier (~0.2 us) per level instead of a grid-wide barrier (several us),
+// O(nnz) work, no polling of unfinished rows.
 
 // dependency counts and the dependents pattern (transpose of the dependency part)
 template <int FWD>
@@ -80,59 +83,70 @@ __global__ void k_dep_fill(int32_t n, const int64_t* __restrict__ rowptr, const 
     }
 }
 
-// grid-wide barrier for a cooperative launch (all blocks resident); bounded
-// wait, gives up with EDFA_ERR_TIMEOUT
-__device__ __forceinline__ void grid_barrier(unsigned* count, int* gen, DevErr* err)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int g = ld_acquire(gen);
-        __threadfence();
-        if (atomicAdd(count, 1u) == gridDim.x - 1) {
-            atomicExch(count, 0u);
-            __threadfence();
-            st_release(gen, g + 1);
-        } else {
-            unsigned it = 0;
-            while (ld_acquire(gen) == g) {
-                if (++it > (kSpinLimit << 2)) { raise_err(err, EDFA_ERR_TIMEOUT, -2); break; }
-                if ((it & 1023u) == 0u && err_set(err)) break;
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-}
+constexpr int kKahnCtas = 16, kKahnThreads = 1024;
 
-__global__ void __launch_bounds__(256)
+// G lanes per frontier row: the decrements of one row's dependents are issued
+// together (one atomic round trip per row, not one per dependent), and the
+// rows that become ready are appended with one atomic per warp.
+template <int G>
+__global__ void __launch_bounds__(kKahnThreads, 1)
 k_kahn(int32_t n, const int64_t* __restrict__ dptr, const int32_t* __restrict__ dcol, int* indeg, int* level,
-       int32_t* order, int* cnt, unsigned* bar_count, int* bar_gen, int* nlev_out, DevErr* err)
+       int32_t* order, int* cnt, int* nlev_out)
 {
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = tid; i < n; i += nth)
-        if (indeg[i] == 0) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i0 = tid - lane; i0 < n; i0 += nth) {  // warp-uniform trip count
+        const int64_t i = i0 + lane;
+        const bool ready = i < n && indeg[i] == 0;
+        const unsigned m = __ballot_sync(0xffffffffu, ready);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(&cnt[0], __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (ready) {
             level[i] = 0;
-            order[atomicAdd(&cnt[0], 1)] = (int32_t)i;
+            order[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
         }
-    grid_barrier(bar_count, bar_gen, err);
+    }
+    cl.sync();
+    const int64_t ngroups = nth / G;
+    const int64_t grp = tid / G;
+    const int gl = (int)(tid % G);
     int64_t start = 0;
     int L = 0;
-    for (;;) {
-        const int c = ld_acquire(&cnt[L]);
-        if (c == 0 || err_set(err)) break;
+    // every CTA reads the same count after the same barrier, so all leave the
+    // loop together; at most n levels
+    while (L < n) {
+        const int c = __ldcg(&cnt[L]);  // completed by other SMs before the barrier
+        if (c == 0) break;
         const int64_t end = start + c;
-        for (int64_t p = start + tid; p < end; p += nth) {
-            const int j = __ldcg(order + p);  // written by other SMs in the previous level
-            for (int64_t q = dptr[j]; q < dptr[j + 1]; ++q) {
-                const int i = dcol[q];
-                if (atomicSub(&indeg[i], 1) == 1) {
-                    level[i] = L + 1;
-                    order[end + atomicAdd(&cnt[L + 1], 1)] = (int32_t)i;
+        // warp-uniform trip count: every lane of a warp runs the same rounds
+        const int64_t rounds = (c + ngroups - 1) / ngroups;
+        for (int64_t rd = 0; rd < rounds; ++rd) {
+            const int64_t p = start + rd * ngroups + grp;
+            bool fin_any = false;
+            int fin_i[1] = {-1};
+            if (p < end) {
+                const int j = __ldcg(order + p);
+                const int64_t q0 = dptr[j], q1 = dptr[j + 1];
+                for (int64_t q = q0 + gl; q < q1; q += G) {
+                    const int i = dcol[q];
+                    if (atomicSub(&indeg[i], 1) == 1) {
+                        level[i] = L + 1;
+                        // rare second completion in the same lane: append directly
+                        if (fin_any) order[end + atomicAdd(&cnt[L + 1], 1)] = (int32_t)i;
+                        else { fin_any = true; fin_i[0] = i; }
+                    }
                 }
             }
+            const unsigned m = __ballot_sync(0xffffffffu, fin_any);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(&cnt[L + 1], __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (fin_any) order[end + base + __popc(m & ((1u << lane) - 1u))] = (int32_t)fin_i[0];
         }
-        grid_barrier(bar_count, bar_gen, err);
+        cl.sync();
         start = end;
         ++L;
     }
@@ -210,21 +224,28 @@ static int make_plan(edfa_handle_s* h, SweepPlan& plan, int32_t n, const int64_t
         if (fwd) (edfa::count_launch(), k_dep_fill<1><<<gb, 256, 0, s>>>(n, rowptr, col, dcur, dcol));
         else (edfa::count_launch(), k_dep_fill<0><<<gb, 256, 0, s>>>(n, rowptr, col, dcur, dcol));
     }
-    // cooperative frontier expansion
-    int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_kahn, 256, 0);
-    if (per < 1) per = 1;
-    if (per > 2) per = 2;
-    int grid = per * h->nsm;
-    unsigned* bar_count = (unsigned*)(misc + 0);
-    int* bar_gen = misc + 1;
+    // frontier expansion in one 16-CTA cluster; lanes per frontier row from
+    // the mean number of dependents
     int* nlev_d = misc + 2;
-    int32_t nn32 = n;
-    DevErr* errp = h->err;
-    void* args[] = {&nn32, &dptr, &dcol, &indeg, &level, &order, &cnt, &bar_count, &bar_gen, &nlev_d, &errp};
     if (n > 0) {
+        const double avg = (double)ndep / (double)n;
+        auto fn = avg > 12.0 ? k_kahn<32> : avg > 6.0 ? k_kahn<16> : avg > 3.0 ? k_kahn<8> : k_kahn<4>;
+        cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kKahnCtas, 1, 1);
+        cfg.blockDim = dim3(kKahnThreads, 1, 1);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kKahnCtas;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
         edfa::count_launch();
-        if (cudaLaunchCooperativeKernel((const void*)k_kahn, grid, 256, args, 0, s) != cudaSuccess) {
+        if (cudaLaunchKernelEx(&cfg, fn, (int32_t)n, (const int64_t*)dptr, (const int32_t*)dcol, indeg, level,
+                               order, cnt, nlev_d) != cudaSuccess) {
             cudaGetLastError();
             return EDFA_ERR_CUDA;
         }
@@ -309,32 +330,88 @@ int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64
 // ILU(0), IKJ order (Saad, Alg. 10.4): row i, for each stored k < i in
 // ascending order: l_ik = a_ik / u_kk, then a_ij -= l_ik u_kj for stored
 // j > k present in row k.  One warp per row, rows taken in level order.
-// The warp first waits for all rows it depends on (lanes in parallel), then
-// copies their U parts into shared memory with batched loads, and eliminates
-// from shared memory.  Rows whose data exceed the shared buffers fall back to
-// searching the U parts in global memory.
+// Per row the warp
+//   1. stages the row in shared memory with a column -> position hash,
+//   2. waits for every row it depends on (lanes poll in parallel, no sleep),
+//   3. gathers the U parts of all those rows into shared memory with one burst
+//      of 16-byte cp.async.cg copies (L2, never a stale L1 line),
+//   4. eliminates: a sequential loop over k whose inner updates are one
+//      lane per U entry with an O(1) hash lookup of the target position.
+// The critical path through the level DAG is one row latency per level, so
+// every step above is a single round trip.  Rows whose U data exceed the
+// shared buffers read the U parts from global memory in step 4 instead.
 constexpr int kFRow = 256;    // row entries held in shared memory
-constexpr int kFU = 1536;     // U-part entries of all dependencies held in shared memory
+constexpr int kFU = 1280;     // U-part entries of all dependencies (incl. 16-byte alignment padding)
+constexpr int kFHash = 512;   // column -> position hash slots
 
 template <class T>
-struct FacSmem {
-    T rv[kFRow];
-    T dk[kFRow];
-    T uv[kFU];
-    int rc[kFRow];
-    int uo[kFRow + 1];
-    int uc[kFU];
+struct alignas(16) FacSmem {
+    T rv[kFRow];       // the row being factored
+    T dk[kFRow];       // 1 / u_kk of every dependency
+    T uv[kFU];         // U values of the dependencies
+    int uc[kFU];       // U columns of the dependencies
+    long long ub[kFRow];  // first U entry of every dependency
+    int rc[kFRow];     // row columns
+    int oc[kFRow + 1]; // dependency u's columns start at uc[oc[u] + sc[u]]
+    int ov[kFRow + 1]; // ... and its values at uv[ov[u] + sv[u]]
+    int sc[kFRow];
+    int sv[kFRow];
+    int ul[kFRow];     // U length of every dependency
+    int hk[kFHash];    // hash keys (column, -1 empty)
+    int hp[kFHash];    // hash values (position in the row)
 };
+
+__device__ __forceinline__ int fac_hslot(int j) { return (int)(((unsigned)j * 2654435769u) >> 23); }  // 512 slots
+
+template <class T>
+__device__ __forceinline__ int fac_lookup(const FacSmem<T>& S, int j)
+{
+    int sl = fac_hslot(j);
+    for (int it = 0; it < kFHash; ++it) {
+        const int k = S.hk[sl];
+        if (k == j) return S.hp[sl];
+        if (k < 0) return -1;
+        sl = (sl + 1) & (kFHash - 1);
+    }
+    return -1;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+
+// copy nblk 16-byte blocks starting at element `first` of a global array of
+// `total` elements (E per block) to shared memory, all by the calling lane; a
+// block reaching past the end of the array is copied element by element
+template <class V>
+__device__ __forceinline__ void gather_blocks(V* dst, const V* src, long long first, int nblk, long long total,
+                                              bool async_ok)
+{
+    constexpr int E = 16 / (int)sizeof(V);
+    for (int q = 0; q < nblk; ++q) {
+        const long long g0 = first + (long long)q * E;
+        if (async_ok && g0 + E <= total) {
+            cp_async16(dst + q * E, src + g0);
+        } else {
+            for (int e = 0; e < E; ++e)
+                if (g0 + e < total) dst[q * E + e] = __ldcg(src + g0 + e);
+        }
+    }
+}
 
 template <class T>
 __global__ void __launch_bounds__(kFacWarps * 32)
-k_ilu0(int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+k_ilu0(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
        const int64_t* __restrict__ diag, const T* __restrict__ vals, T* lu, T* dinv, const int32_t* perm,
-       int64_t nslots, int* flags, int epoch, unsigned long long* ticket, DevErr* err)
+       int64_t nslots, int* flags, int epoch, unsigned long long* ticket, int async_ok, DevErr* err)
 {
     extern __shared__ __align__(16) unsigned char fsm_raw[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     FacSmem<T>& S = reinterpret_cast<FacSmem<T>*>(fsm_raw)[wid];
+    constexpr int VPB = 16 / (int)sizeof(T);
     for (;;) {
         long long t = claim(ticket, 1);
         if (t >= nslots) break;
@@ -347,91 +424,100 @@ k_ilu0(int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict_
             if (lane == 0) { raise_err(err, EDFA_ERR_BOUNDS, i); st_release(flags + i, epoch); }
             continue;
         }
-        for (int u = lane; u < len; u += 32) { S.rv[u] = vals[b + u]; S.rc[u] = col[b + u]; }
+        // 1. the row and its column hash
+        for (int k = lane; k < kFHash; k += 32) S.hk[k] = -1;
         __syncwarp();
-        // wait for every dependency (one lane per dependency)
-        for (int u = lane; u < dpos; u += 32) wait_flag(flags + S.rc[u], epoch, err, i);
-        __syncwarp();
-        // sizes of the dependencies' U parts and their dinv
-        int tot = 0;
-        for (int base0 = 0; base0 < dpos; base0 += 32) {
-            int u = base0 + lane;
-            int ul = 0;
-            if (u < dpos) {
-                int k = S.rc[u];
-                int64_t ub = ld_cg(diag + k) + 1;
-                ul = (int)(rowptr[k + 1] - ub);
-                S.dk[u] = ld_cg(dinv + k);
+        for (int u = lane; u < len; u += 32) {
+            const int j = col[b + u];
+            S.rv[u] = vals[b + u];
+            S.rc[u] = j;
+            int sl = fac_hslot(j);
+            for (int it = 0; it < kFHash; ++it) {
+                if (atomicCAS(&S.hk[sl], -1, j) == -1) { S.hp[sl] = u; break; }
+                sl = (sl + 1) & (kFHash - 1);
             }
-            int x = ul;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            if (u < dpos) S.uo[u] = tot + x - ul;
-            tot += __shfl_sync(0xffffffffu, x, 31);
         }
-        if (lane == 0) S.uo[dpos] = tot;
         __syncwarp();
-        const bool in_smem = tot <= kFU;
-        if (in_smem) {
-            // flattened copy of all U parts: entry q belongs to dependency u with uo[u] <= q < uo[u+1]
-            for (int q0 = 0; q0 < tot; q0 += 4 * 32) {
-                int cc[4];
-                T vv[4];
-                int qq[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    int q = q0 + r * 32 + lane;
-                    qq[r] = q;
-                    cc[r] = -1;
-                    if (q < tot) {
-                        int lo = 0, hi = dpos - 1;
-                        while (lo < hi) {
-                            int mid = (lo + hi + 1) >> 1;
-                            if (S.uo[mid] <= q) lo = mid; else hi = mid - 1;
-                        }
-                        int k = S.rc[lo];
-                        int64_t src = ld_cg(diag + k) + 1 + (q - S.uo[lo]);
-                        cc[r] = col[src];
-                        vv[r] = ld_cg(lu + src);
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    if (qq[r] < tot) { S.uc[qq[r]] = cc[r]; S.uv[qq[r]] = vv[r]; }
+        // 2. wait for the dependencies (bounded; no sleep: one row latency per
+        // level).  Relaxed polls, then one acquire fence: acquire loads in a
+        // spin loop would keep invalidating the L1 of every warp on the SM.
+        {
+            bool done = false;
+            for (unsigned it = 0; it < (kSpinLimit << 2); ++it) {
+                bool ok = true;
+                for (int u = lane; u < dpos; u += 32) ok &= ld_relaxed_i32(flags + S.rc[u]) == epoch;
+                if (__all_sync(0xffffffffu, ok)) { done = true; break; }
+                if ((it & 255u) == 255u && err_set(err)) break;
             }
+            if (!done && lane == 0) raise_err(err, EDFA_ERR_TIMEOUT, i);
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
             __syncwarp();
         }
+        // dependency metadata: U ranges, their aligned blocks, 1/u_kk
+        int totc = 0, totv = 0;
+        for (int base0 = 0; base0 < dpos; base0 += 32) {
+            const int u = base0 + lane;
+            int pc = 0, pv = 0;
+            if (u < dpos) {
+                const int k = S.rc[u];
+                const long long ubk = diag[k] + 1;
+                const int ulen = (int)(rowptr[k + 1] - ubk);
+                S.dk[u] = ld_cg(dinv + k);
+                S.ub[u] = ubk;
+                S.ul[u] = ulen;
+                const int sc = (int)(ubk & 3), sv = (int)(ubk % VPB);
+                S.sc[u] = sc;
+                S.sv[u] = sv;
+                pc = (sc + ulen + 3) & ~3;
+                pv = (sv + ulen + VPB - 1) / VPB * VPB;
+            }
+            int xc = pc, xv = pv;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int yc = __shfl_up_sync(0xffffffffu, xc, o);
+                const int yv = __shfl_up_sync(0xffffffffu, xv, o);
+                if (lane >= o) { xc += yc; xv += yv; }
+            }
+            if (u < dpos) { S.oc[u] = totc + xc - pc; S.ov[u] = totv + xv - pv; }
+            totc += __shfl_sync(0xffffffffu, xc, 31);
+            totv += __shfl_sync(0xffffffffu, xv, 31);
+        }
+        if (lane == 0) { S.oc[dpos] = totc; S.ov[dpos] = totv; }
+        __syncwarp();
+        // 3. gather every dependency's U part in one burst
+        const bool in_smem = totc <= kFU && totv <= kFU;
+        if (in_smem) {
+            // one lane per dependency issues all of its copies
+            for (int u = lane; u < dpos; u += 32) {
+                const long long ubk = S.ub[u];
+                gather_blocks(S.uc + S.oc[u], col, ubk - S.sc[u], (S.oc[u + 1] - S.oc[u]) / 4, nnz, async_ok != 0);
+                gather_blocks(S.uv + S.ov[u], (const T*)lu, ubk - S.sv[u], (S.ov[u + 1] - S.ov[u]) / VPB, nnz,
+                              async_ok != 0);
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncwarp();
+            // target position in row i of every gathered U entry (padding
+            // entries get a position too, never used), off the sequential path
+            for (int q = lane; q < totc; q += 32) S.uc[q] = fac_lookup(S, S.uc[q]);
+        }
+        __syncwarp();
+        // 4. eliminate
         for (int tt = 0; tt < dpos; ++tt) {
             const T lik = S.rv[tt] * S.dk[tt];
+            const int n_u = S.ul[tt];
             __syncwarp();
             if (lane == 0) S.rv[tt] = lik;
             if (in_smem) {
-                const int ub = S.uo[tt], ue = S.uo[tt + 1];
-                for (int u = tt + 1 + lane; u < len; u += 32) {
-                    int j = S.rc[u];
-                    int lo = ub, hi = ue - 1;
-                    while (lo <= hi) {
-                        int mid = (lo + hi) >> 1;
-                        int cm = S.uc[mid];
-                        if (cm == j) { S.rv[u] -= lik * S.uv[mid]; break; }
-                        if (cm < j) lo = mid + 1; else hi = mid - 1;
-                    }
+                const int c0 = S.oc[tt] + S.sc[tt], v0 = S.ov[tt] + S.sv[tt];
+                for (int q = lane; q < n_u; q += 32) {
+                    const int pos = S.uc[c0 + q];
+                    if (pos >= 0) S.rv[pos] -= lik * S.uv[v0 + q];
                 }
             } else {
-                const int k = S.rc[tt];
-                const int64_t ub = ld_cg(diag + k) + 1, ue = rowptr[k + 1];
-                for (int u = tt + 1 + lane; u < len; u += 32) {
-                    int j = S.rc[u];
-                    int64_t lo = ub, hi = ue - 1;
-                    while (lo <= hi) {
-                        int64_t mid = (lo + hi) >> 1;
-                        int cm = col[mid];
-                        if (cm == j) { S.rv[u] -= lik * ld_cg(lu + mid); break; }
-                        if (cm < j) lo = mid + 1; else hi = mid - 1;
-                    }
+                const long long ubk = S.ub[tt];
+                for (int q = lane; q < n_u; q += 32) {
+                    const int pos = fac_lookup(S, __ldcg(col + ubk + q));
+                    if (pos >= 0) S.rv[pos] -= lik * ld_cg(lu + ubk + q);
                 }
             }
             __syncwarp();
@@ -459,20 +545,23 @@ int factor_numeric(edfa_handle_s* h, Factor& f, const double* vals64, const floa
         cudaMemsetAsync(h->flags, 0, (size_t)nmax * sizeof(int), s);
     }
     cudaMemsetAsync(h->ticket, 0, sizeof(unsigned long long), s);
-    if (h->opt.precision == 1) {
+    // 16-byte copies need 16-byte aligned column and value arrays
+    const bool f32 = h->opt.precision == 1;
+    const int async_ok = ((uintptr_t)f.col % 16 == 0) && ((uintptr_t)(f32 ? (void*)f.lu32 : (void*)f.lu64) % 16 == 0);
+    if (f32) {
         size_t smem = sizeof(FacSmem<float>) * kFacWarps;
         cudaFuncSetAttribute(k_ilu0<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int grid = resident_grid(h, (const void*)k_ilu0<float>, kFacWarps * 32, smem, 32);
-        (edfa::count_launch(), k_ilu0<float><<<grid, kFacWarps * 32, smem, s>>>(f.n, f.rowptr, f.col, f.diag, vals32, f.lu32, f.dinv32,
-                                                          f.fwd.perm, f.fwd.nslots, h->flags, h->epoch, h->ticket,
-                                                          h->err));
+        (edfa::count_launch(), k_ilu0<float><<<grid, kFacWarps * 32, smem, s>>>(f.n, f.nnz, f.rowptr, f.col, f.diag, vals32,
+                                                          f.lu32, f.dinv32, f.fwd.perm, f.fwd.nslots, h->flags,
+                                                          h->epoch, h->ticket, async_ok, h->err));
     } else {
         size_t smem = sizeof(FacSmem<double>) * kFacWarps;
         cudaFuncSetAttribute(k_ilu0<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int grid = resident_grid(h, (const void*)k_ilu0<double>, kFacWarps * 32, smem, 32);
-        (edfa::count_launch(), k_ilu0<double><<<grid, kFacWarps * 32, smem, s>>>(f.n, f.rowptr, f.col, f.diag, vals64, f.lu64,
-                                                           f.dinv64, f.fwd.perm, f.fwd.nslots, h->flags, h->epoch,
-                                                           h->ticket, h->err));
+        (edfa::count_launch(), k_ilu0<double><<<grid, kFacWarps * 32, smem, s>>>(f.n, f.nnz, f.rowptr, f.col, f.diag, vals64,
+                                                           f.lu64, f.dinv64, f.fwd.perm, f.fwd.nslots, h->flags,
+                                                           h->epoch, h->ticket, async_ok, h->err));
     }
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
