@@ -132,8 +132,8 @@ def sweep_traffic_from_profile(kind_name: str):
         return None
     vals = {}
     for line in txt.splitlines():
-        if ":" in line:
-            k, v = line.split(":", 1)
+        if ": " in line:
+            k, v = line.split(": ", 1)
             vals[k.strip().strip("-* `")] = v.strip().strip("` ")
     if vals.get(f"{srcname} sha256[:16]") != digest:
         return None

@@ -1,0 +1,98 @@
+"""The single-cluster S~ sweeps against the oracle and against the sync-free
+sweeps, including the degenerate shapes of its data layout: fewer rows than
+CTAs, levels longer than the in-block sort handles, both block variants and
+both precisions, and a new D through edfa_setup (re-packed values)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from helpers import gpu_handle
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _apply(h, r):
+    torch = _torch()
+    return h.apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _check(sysd, mode, variant=0, precision=0):
+    """cluster sweeps vs the oracle's application and vs the sync-free sweeps"""
+    _torch()
+    ref = O.edfa_pipeline(sysd, mode=mode, variant=variant, solve=False)
+    r = W.Stream(5).normal(sysd.n)
+    z_ref = ref["prec"].apply(r)
+    h_cl = gpu_handle(sysd, mode=mode, variant=variant, precision=precision)
+    assert h_cl.stats().s_cluster == 1
+    z_cl = _apply(h_cl, r)
+    # a second handle with the all-SM sweeps only
+    import paper_2009_13916_gb300 as P
+    A, B, C, D = P.system_to_device(sysd)
+    h_sf = P.Edfa(A, B, C, D, sysd.Nf, sysd.Ne, qmode=mode, thresh=sysd.extra.get("thresh", 0.05),
+                  variant=variant, precision=precision, sweep_mode=1)
+    assert h_sf.stats().s_cluster == 0
+    z_sf = _apply(h_sf, r)
+    tol = 1e-9 if precision == 0 else 2e-4
+    assert _rel(z_cl, z_ref) <= tol
+    # same arithmetic per row, only the order of the partial sums differs
+    assert _rel(z_cl, z_sf) <= (1e-13 if precision == 0 else 1e-5)
+    h_cl.close()
+    h_sf.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cluster_sweep_matches_oracle_and_syncfree(variant, precision):
+    s = W.Stream(11)
+    n = (12, 10, 9)
+    Ne = int(np.prod(n))
+    m = np.exp(2.0 * s.normal(Ne))
+    q = s.normal(4 * Ne).reshape(Ne, 4)
+    sysd = W.assemble(*n, W.rotated_K(m, 0.1, q))
+    _check(sysd, "nbr", variant=variant, precision=precision)
+
+
+def test_cluster_sweep_fewer_rows_than_ctas():
+    # 8 cells: half of the 16 CTAs own no row at all
+    _check(W.brick(2, seed=4), "nbr")
+
+
+def test_cluster_sweep_levels_longer_than_sort_block():
+    # 8300 independent 2x2x2 bricks: the first forward level holds > 8192 rows
+    sysd, _, _ = W.concat([W.brick(2, seed=1 + k % 7) for k in range(8300)])
+    _check(sysd, "own")
+
+
+def test_cluster_sweep_after_new_D():
+    torch = _torch()
+    import paper_2009_13916_gb300 as P
+    sysd = W.brick(6, seed=3, sigma=1.0)
+    h = gpu_handle(sysd, mode="nbr")
+    assert h.stats().s_cluster == 1
+    # new storage term (diagonal of D): Stage 2 refactors S~ and re-packs the chunk values
+    D2 = sysd.D.to_scipy().tocsr().copy()
+    D2.setdiag(D2.diagonal() * 3.0)
+    D2.sort_indices()
+    Dt = (torch.as_tensor(D2.indptr, dtype=torch.int64, device="cuda"),
+          torch.as_tensor(D2.indices, dtype=torch.int32, device="cuda"),
+          torch.as_tensor(D2.data, dtype=torch.float64, device="cuda"))
+    h.setup(Dt)
+    q = O.qsets("nbr", sysd.A, sysd.B, sysd.C)
+    x, _ = O.local_solves(sysd.A, sysd.B, sysd.C, *q)
+    S = O.schur(0, sysd.A, sysd.C, D2, *q, x)
+    prec = O.Prec(sysd.A, sysd.B, sysd.C, D2, S=S)
+    r = W.Stream(9).normal(sysd.n)
+    assert _rel(_apply(h, r), prec.apply(r)) <= 1e-9
+    h.close()
