@@ -121,7 +121,7 @@ def sweep_traffic_from_profile(kind_name: str):
     """DRAM bytes per launch of the dominant sweep from the committed ncu summary,
     or None when the kernel source changed since the counters were taken."""
     if kind_name == "s_cluster":
-        path, srcname = os.path.join(ROOT, "profiles", "k_s_cluster_c2_64.md"), "k_cluster.cu"
+        path, srcname = os.path.join(ROOT, "profiles", "k_s_df_c2_64.md"), "k_cluster.cu"
     else:
         path, srcname = os.path.join(ROOT, "profiles", "sweep_s_c2_64.txt"), "k_ilu.cu"
     src = os.path.join(ROOT, "paper_2009_13916_gb300", "csrc", srcname)
@@ -337,7 +337,7 @@ def main():
     # roofline of the dominant kernel among the triangular sweeps (timed per
     # launch with CUDA events on the launching stream while profiling is on)
     kinds = ["k_sweep (A~ forward)", "k_sweep (A~ backward)", "k_sweep (S~ forward, fused C y)",
-             "k_sweep (S~ backward)", "k_s_cluster (S~ forward + backward in one 16-CTA cluster)"]
+             "k_sweep (S~ backward)", "k_s_df (S~ forward + backward in one 16-CTA cluster, dataflow)"]
     tot = r64["sweep_ms"]
     dom = max(range(5), key=lambda q: tot[q])
     n_launch = r64["sweep_n"][dom]
@@ -353,7 +353,7 @@ def main():
         1: 12 * nnz_half_a + Nf * (8 + 8 + 4 + 8 + 8 + 8),
         2: 12 * nnz_half_s + 12 * sysd.C.nnz + 8 * (Ne + 1) + Ne * (8 + 8 + 4 + 8 + 8) + 8 * Nf,
         3: 12 * nnz_half_s + Ne * (8 + 8 + 4 + 8 + 8 + 8),
-        4: 12 * 2 * nnz_half_s + Ne * (8 + 8 + 8 + 4),
+        4: 12 * 2 * nnz_half_s + Ne * (8 + 8 + 8 + 4),  # both S~ sweeps in one launch
     }
     peak, peak_src = measured_peaks()
     achieved = per_launch[dom] / (avg_ms / 1e3) / 1e9 if n_launch else None

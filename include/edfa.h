@@ -98,9 +98,10 @@ typedef struct {
     int32_t warps_per_block;/* local-solve launch shape; 0 = default */
     int32_t sweep_warps_per_sm; /* resident warps per SM of the sync-free ILU(0) sweeps; 0 = default (16) */
     int32_t sweep_mode;     /* S~ triangular sweeps: 0 = automatic (one 16-CTA thread-block cluster
-                               holding the solution in distributed shared memory when N_e values fit
-                               and the cluster can be scheduled, else sync-free all-SM sweeps);
-                               1 = sync-free all-SM sweeps only */
+                               holding the solution in distributed shared memory, rows polling their
+                               dependencies there, when N_e values fit and the cluster can be
+                               scheduled; else sync-free all-SM sweeps); 1 = sync-free all-SM sweeps
+                               only; 2 = the cluster with one barrier per dependency level */
 } edfa_options;
 
 typedef struct edfa_handle_s* edfa_handle;

@@ -141,7 +141,7 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     edfa_options o;
     if (opt) o = *opt; else edfa_default_options(&o);
     if (o.qmode < EDFA_Q_OWN || o.qmode > EDFA_Q_GIVEN) return EDFA_ERR_INVALID;
-    if (o.sweep_mode < 0 || o.sweep_mode > 1) return EDFA_ERR_INVALID;
+    if (o.sweep_mode < 0 || o.sweep_mode > 2) return EDFA_ERR_INVALID;
     if (o.qmode == EDFA_Q_GIVEN && (!o.qptr || !o.qidx)) return EDFA_ERR_INVALID;
     if (o.qmode == EDFA_Q_THRESH && !(o.thresh >= 0.0)) return EDFA_ERR_INVALID;
     if (o.qmode == EDFA_Q_DYNAMIC && (o.n_add < 0 || o.n_ent < 0 || o.it_max < 0)) return EDFA_ERR_INVALID;

@@ -148,6 +148,15 @@ struct ClusterPlan {
     int32_t szstride = 0;
     void* bslot = nullptr;     // [16*cap] right-hand side in slot order
     size_t smem = 0;           // dynamic shared memory per CTA
+    int kind = 0;              // 1 dataflow (row records), 2 level-synchronous (TMA chunks)
+    // dataflow variant
+    unsigned char* rec = nullptr;  // [2n] fixed-size row records in processing order
+    int64_t* fidx = nullptr;       // [n] forward record of every row
+    int64_t* bidx = nullptr;       // [16][cap] backward record of every slot (-1: none)
+    int64_t* rmeta = nullptr;      // [16][2] first record and rows per CTA
+    int64_t* ovoff = nullptr;      // [2n+1] overflow offsets (dependencies beyond the inline ones)
+    int32_t* ovf_dep = nullptr;
+    void* ovf_val = nullptr;
 };
 
 }  // namespace edfa

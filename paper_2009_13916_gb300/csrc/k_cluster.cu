@@ -632,18 +632,321 @@ k_s_cluster(const T* __restrict__ bslot, const unsigned char* __restrict__ chunk
     }
 }
 
-// ------------------------------------------------------------ host side
+// ------------------------------------------------------------ dataflow variant
+// The same two sweeps without a barrier per level: every row polls the values
+// it depends on directly in the distributed shared memory (a slot holds the
+// all-ones NaN until its row is done; no arithmetic produces that pattern),
+// so a level costs one value hop (local shared memory ~30 ns, remote ~0.3 us)
+// instead of a cluster barrier plus the skew of the slowest CTA.  Rows are
+// claimed in level order through a per-CTA ticket; each lane group prefetches
+// its row's fixed-size record (dependency slots and factor values) from HBM
+// while earlier rows finish.  Claiming in level order keeps it deadlock free:
+// the in-flight row of smallest (phase, level) has all its dependencies done.
+// Between the phases one cluster-wide step moves every w_i into its backward
+// record and resets the slots to the sentinel.
+//
+// Row record (kDfDeps dependencies inline, the rest in an overflow array):
+//   0: int slot, int count, int64 overflow offset
+//  16: T aux (forward: right-hand side; backward: w_i), 24: T 1/U_ii
+//  32: int dep[kDfDeps] (slot * 16 + owner)
+// 160: T val[kDfDeps]
+constexpr int kDfThreads = 1024;
+constexpr int kDfDeps = 32;
+
 template <class T>
-static const void* cluster_kernel()
+__host__ __device__ constexpr int df_rb()
 {
-    return (const void*)k_s_cluster<T, T, kClLpr>;
+    return 160 + kDfDeps * (int)sizeof(T);
 }
 
-static cudaLaunchConfig_t cluster_cfg(size_t smem, cudaStream_t s, cudaLaunchAttribute* attr)
+__device__ __forceinline__ bool df_sent(double v) { return __double_as_longlong(v) == -1ll; }
+__device__ __forceinline__ bool df_sent(float v) { return __float_as_int(v) == -1; }
+template <class T>
+__device__ __forceinline__ T df_sentinel();
+template <>
+__device__ __forceinline__ double df_sentinel<double>() { return __longlong_as_double(-1ll); }
+template <>
+__device__ __forceinline__ float df_sentinel<float>() { return __int_as_float(-1); }
+
+__device__ __forceinline__ double df_ld_local(uint32_t a, double)
+{
+    double v;
+    asm volatile("ld.volatile.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float df_ld_local(uint32_t a, float)
+{
+    float v;
+    asm volatile("ld.volatile.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ double df_ld_remote(uint32_t a, uint32_t rank, double)
+{
+    double v;
+    asm volatile(
+        "{\n\t.reg .b32 ra;\n\tmapa.shared::cluster.u32 ra, %1, %2;\n\tld.relaxed.cluster.shared::cluster.f64 %0, [ra];\n\t}"
+        : "=d"(v)
+        : "r"(a), "r"(rank));
+    return v;
+}
+__device__ __forceinline__ float df_ld_remote(uint32_t a, uint32_t rank, float)
+{
+    float v;
+    asm volatile(
+        "{\n\t.reg .b32 ra;\n\tmapa.shared::cluster.u32 ra, %1, %2;\n\tld.relaxed.cluster.shared::cluster.f32 %0, [ra];\n\t}"
+        : "=f"(v)
+        : "r"(a), "r"(rank));
+    return v;
+}
+__device__ __forceinline__ void df_st(uint32_t a, double v)
+{
+    asm volatile("st.relaxed.cluster.shared::cta.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ void df_st(uint32_t a, float v)
+{
+    asm volatile("st.relaxed.cluster.shared::cta.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
+// value of dependency t (slot * 16 + owner), or the sentinel while not ready
+template <class T>
+__device__ __forceinline__ T df_value(uint32_t xs_s, int t, int rank)
+{
+    const uint32_t a = xs_s + (uint32_t)((t >> 4) * (int)sizeof(T));
+    const int r = t & (kCl - 1);
+    return r == rank ? df_ld_local(a, T(0)) : df_ld_remote(a, (uint32_t)r, T(0));
+}
+
+template <class T, int LPR, int SLEEP>
+__device__ __forceinline__ void df_row(const unsigned char* __restrict__ rc, uint32_t xs_s, int cap, int rank,
+                                       bool bwd, int gl, unsigned gmask, const int32_t* __restrict__ ovf_dep,
+                                       const T* __restrict__ ovf_val, DevErr* err)
+{
+    constexpr int KMAX = kDfDeps / LPR;
+    const int4 hd = *(const int4*)rc;
+    const int slot = hd.x, cnt = hd.y;
+    const long long ovf = (long long)(((unsigned long long)(unsigned)hd.w << 32) | (unsigned)hd.z);
+    const T aux = *(const T*)(rc + 16);
+    const T dv = *(const T*)(rc + 24);
+    const int32_t* dep = (const int32_t*)(rc + 32);
+    const T* val = (const T*)(rc + 160);
+    int t[KMAX];
+    T v[KMAX], x[KMAX];
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) {
+        const int p = gl + q * LPR;
+        const bool on = p < cnt;
+        t[q] = on ? dep[p] : -1;
+        v[q] = on ? val[p] : T(0);
+        x[q] = T(0);
+        if (on && (unsigned)(t[q] >> 4) >= (unsigned)cap) {
+            raise_err(err, EDFA_ERR_BOUNDS, slot);
+            t[q] = -1;
+        }
+    }
+    // poll until every dependency of the row is done (bounded)
+    unsigned pend = 0;
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) pend |= (t[q] >= 0 ? 1u : 0u) << q;
+    for (unsigned it = 0;; ++it) {
+#pragma unroll
+        for (int q = 0; q < KMAX; ++q)
+            if (pend & (1u << q)) {
+                const T y = df_value<T>(xs_s, t[q], rank);
+                if (!df_sent(y)) {
+                    x[q] = y;
+                    pend &= ~(1u << q);
+                }
+            }
+        if (!__any_sync(gmask, pend != 0)) break;
+        if (it >= kSpinLimit || ((it & 255u) == 255u && err_set(err))) {
+            if (it >= kSpinLimit) raise_err(err, EDFA_ERR_TIMEOUT, slot);
+            break;
+        }
+        // rows whose dependencies are not close to done back off, leaving the
+        // distributed-shared-memory request slots to the rows on the critical path
+        if (SLEEP > 0 && it > 0) __nanosleep(SLEEP);
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) acc = fma(v[q], x[q], acc);
+    // dependencies beyond the inline ones (long rows)
+    for (int p = kDfDeps + gl; p < cnt; p += LPR) {
+        const int tt = ovf_dep[ovf + p - kDfDeps];
+        const T vv = ovf_val[ovf + p - kDfDeps];
+        if ((unsigned)(tt >> 4) >= (unsigned)cap) {
+            raise_err(err, EDFA_ERR_BOUNDS, slot);
+            continue;
+        }
+        T y = df_value<T>(xs_s, tt, rank);
+        for (unsigned it = 0; df_sent(y) && it < kSpinLimit; ++it) {
+            if ((it & 255u) == 255u && err_set(err)) break;
+            y = df_value<T>(xs_s, tt, rank);
+        }
+        acc = fma(vv, y, acc);
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o);
+    if (gl == 0 && (unsigned)slot < (unsigned)cap) {
+        T y = aux - acc;
+        if (bwd) y *= dv;
+        df_st(xs_s + (uint32_t)(slot * (int)sizeof(T)), y);
+    }
+}
+
+template <class T, class TO, int LPR, int THREADS, int SLEEP>
+__global__ void __launch_bounds__(THREADS, 1)
+k_s_df(unsigned char* __restrict__ rec, const int64_t* __restrict__ rmeta, int32_t cap,
+       const int32_t* __restrict__ ovf_dep, const T* __restrict__ ovf_val, const int64_t* __restrict__ bidx,
+       const int32_t* __restrict__ rowof, TO* __restrict__ out, DevErr* err)
+{
+    constexpr int RPW = 32 / LPR;
+    constexpr int RB = df_rb<T>();
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ int ticket[2];
+    T* xs = (T*)sm;
+    const uint32_t xs_s = smem_u32(xs);
+    const int rank = (int)cgx::this_cluster().block_rank();
+    const int64_t base = rmeta[2 * rank], nr = rmeta[2 * rank + 1];
+    for (int sl = threadIdx.x; sl < cap; sl += blockDim.x) xs[sl] = df_sentinel<T>();
+    if (threadIdx.x < 2) ticket[threadIdx.x] = 0;
+    cluster_arrive();  // every slot of the cluster holds the sentinel before any poll
+    cluster_wait();
+    const int lane = threadIdx.x & 31;
+    const int g = lane / LPR, gl = lane % LPR;
+    const unsigned gmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (g * LPR));
+    for (int ph = 0; ph < 2; ++ph) {
+        const int64_t pbase = base + ph * nr;
+        for (;;) {
+            int k0 = 0;
+            if (lane == 0) k0 = atomicAdd(&ticket[ph], RPW);
+            k0 = __shfl_sync(0xffffffffu, k0, 0);
+            if (k0 >= nr) break;
+            const int k = k0 + g;
+            if (k < nr)
+                df_row<T, LPR, SLEEP>(rec + (pbase + k) * RB, xs_s, cap, rank, ph == 1, gl, gmask, ovf_dep, ovf_val,
+                                      err);
+            __syncwarp();
+        }
+        cluster_arrive();  // every row of this phase is done in the whole cluster
+        cluster_wait();
+        if (ph == 0) {
+            // w_i into the backward records, then every slot back to the sentinel
+            for (int sl = threadIdx.x; sl < cap; sl += blockDim.x) {
+                const int64_t p = bidx[(int64_t)rank * cap + sl];
+                if (p >= 0) *(T*)(rec + p * RB + 16) = xs[sl];
+            }
+            __syncthreads();
+            for (int sl = threadIdx.x; sl < cap; sl += blockDim.x) xs[sl] = df_sentinel<T>();
+            cluster_arrive();
+            cluster_wait();
+        }
+    }
+    for (int sl = threadIdx.x; sl < cap; sl += blockDim.x) {
+        const int i = rowof[(int64_t)rank * cap + sl];
+        if (i >= 0) out[i] = (TO)xs[sl];
+    }
+}
+
+// ---- dataflow plan: record indices, overflow, records
+__global__ void k_df_idx(int64_t nrec, int nlt, int nlf, const int64_t* __restrict__ lofs,
+                         const int32_t* __restrict__ lrows, const int32_t* __restrict__ posf, int32_t cap,
+                         int64_t* __restrict__ fidx, int64_t* __restrict__ bidx)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= nrec) return;
+    const int i = lrows[p];
+    const int q = posf[i];
+    const int r = q & (kCl - 1);
+    if (p < lofs[(int64_t)r * nlt + nlf]) fidx[i] = p;
+    else bidx[(int64_t)r * cap + (q >> 4)] = p;
+}
+
+__global__ void k_df_ovf_count(int64_t nrec, int nlt, int nlf, const int64_t* __restrict__ lofs,
+                               const int32_t* __restrict__ lrows, const int32_t* __restrict__ posf,
+                               const int64_t* __restrict__ rowptr, const int64_t* __restrict__ diag,
+                               int64_t* __restrict__ ovc)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= nrec) return;
+    const int i = lrows[p];
+    const int r = posf[i] & (kCl - 1);
+    const int bwd = p >= lofs[(int64_t)r * nlt + nlf];
+    const int64_t c = row_hi(bwd, i, rowptr, diag) - row_lo(bwd, i, rowptr, diag);
+    ovc[p] = c > kDfDeps ? c - kDfDeps : 0;
+}
+
+__global__ void k_df_rmeta(int nlt, int nlf, const int64_t* __restrict__ lofs, int64_t* __restrict__ rmeta)
+{
+    const int r = threadIdx.x;
+    if (r >= kCl) return;
+    rmeta[2 * r] = lofs[(int64_t)r * nlt];
+    rmeta[2 * r + 1] = lofs[(int64_t)r * nlt + nlf] - lofs[(int64_t)r * nlt];
+}
+
+template <class T>
+__global__ void k_df_write(int64_t nrec, int nlt, int nlf, const int64_t* __restrict__ lofs,
+                           const int32_t* __restrict__ lrows, const int32_t* __restrict__ posf,
+                           const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           const int64_t* __restrict__ diag, const T* __restrict__ lu, const T* __restrict__ dinv,
+                           const int64_t* __restrict__ ovoff, unsigned char* __restrict__ rec,
+                           int32_t* __restrict__ ovf_dep, T* __restrict__ ovf_val)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= nrec) return;
+    const int i = lrows[p];
+    const int q = posf[i];
+    const int r = q & (kCl - 1);
+    const int bwd = p >= lofs[(int64_t)r * nlt + nlf];
+    const int64_t lo = row_lo(bwd, i, rowptr, diag), hi = row_hi(bwd, i, rowptr, diag);
+    const int cnt = (int)(hi - lo);
+    unsigned char* rc = rec + p * df_rb<T>();
+    const long long ov = ovoff[p];
+    *(int4*)rc = make_int4(q >> 4, cnt, (int)(unsigned)(ov & 0xffffffffll), (int)(ov >> 32));
+    *(T*)(rc + 24) = bwd ? dinv[i] : T(1);
+    int32_t* dep = (int32_t*)(rc + 32);
+    T* val = (T*)(rc + 160);
+    for (int k = 0; k < cnt; ++k) {
+        const int d = posf[col[lo + k]];
+        if (k < kDfDeps) {
+            dep[k] = d;
+            val[k] = lu[lo + k];
+        } else {
+            ovf_dep[ov + k - kDfDeps] = d;
+            ovf_val[ov + k - kDfDeps] = lu[lo + k];
+        }
+    }
+}
+
+// forward right-hand side into the forward records: aux_i = base_i - (M v)_i
+template <class T, class TB>
+__global__ void k_df_rhs(int32_t n, const int64_t* __restrict__ fidx, unsigned char* __restrict__ rec,
+                         const TB* __restrict__ base, const int64_t* __restrict__ mptr,
+                         const int32_t* __restrict__ mcol, const T* __restrict__ mval, const T* __restrict__ mv)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T acc = T(0), a2 = T(0);
+    if (mptr) {
+        int64_t p = mptr[i];
+        const int64_t e = mptr[i + 1];
+        for (; p + 1 < e; p += 2) {
+            acc = fma(mval[p], mv[mcol[p]], acc);
+            a2 = fma(mval[p + 1], mv[mcol[p + 1]], a2);
+        }
+        if (p < e) acc = fma(mval[p], mv[mcol[p]], acc);
+    }
+    *(T*)(rec + fidx[i] * df_rb<T>() + 16) = (T)base[i] - (acc + a2);
+}
+
+// ------------------------------------------------------------ host side
+constexpr int kDfLpr = 8;     // lanes per row of the dataflow kernel
+constexpr int kDfSleep = 64;  // back-off between unsuccessful polls (ns; measured best of 0, 64, 200)
+
+static cudaLaunchConfig_t cluster_cfg(size_t smem, int threads, cudaStream_t s, cudaLaunchAttribute* attr)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kCl, 1, 1);
-    cfg.blockDim = dim3(kClThreads, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -655,22 +958,29 @@ static cudaLaunchConfig_t cluster_cfg(size_t smem, cudaStream_t s, cudaLaunchAtt
     return cfg;
 }
 
-// can one cluster with this much shared memory per CTA be scheduled?
-template <class T>
-static bool cluster_schedulable(size_t smem)
+// can one 16-CTA cluster of this kernel with this much shared memory per CTA
+// be scheduled?  (sets the kernel's cluster and shared-memory attributes)
+static bool cluster_schedulable(const void* fn, int threads, size_t smem)
 {
-    const void* fn = cluster_kernel<T>();
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    // the attribute is an upper bound shared by every handle: set it to the device maximum
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess) {
+    // the attribute is an upper bound shared by every handle: set it to the
+    // device maximum less the kernel's static shared memory
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;
+    if ((int64_t)smem > dyn_max ||
+        cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = cluster_cfg(smem, nullptr, attr);
+    cudaLaunchConfig_t cfg = cluster_cfg(smem, threads, nullptr, attr);
     int ncl = 0;
     if (cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) != cudaSuccess) {
         cudaGetLastError();
@@ -679,18 +989,20 @@ static bool cluster_schedulable(size_t smem)
     return ncl > 0;
 }
 
+// owner blocks, value slots and the per-(phase, level, CTA) row lists shared
+// by both cluster variants; returns the slot capacity (0: does not fit)
 template <class T>
-static int plan_build_t(edfa_handle_s* h, cudaStream_t s)
+static int plan_common(edfa_handle_s* h, int64_t min_extra_smem, int32_t* cap_out, cudaStream_t s)
 {
     ClusterPlan& cp = h->cp;
     Factor& f = h->fs;
     const int64_t nsf = f.fwd.nslots, nsb = f.bwd.nslots;
     const int nlf = f.fwd.nlevels, nlb = f.bwd.nlevels, nlt = nlf + nlb;
+    *cap_out = 0;
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     // quick reject before any work: the values alone must fit
-    const int64_t ring = (int64_t)kRing * kChunk + 16 * (kRing + 1);
-    if (pad16(((int64_t)f.n + kCl - 1) / kCl * sizeof(T)) + ring + 16 > optin) return EDFA_OK;
+    if (pad16(((int64_t)f.n + kCl - 1) / kCl * sizeof(T)) + min_extra_smem > optin) return EDFA_OK;
 
     // owner blocks: sort every forward level by row index (the order of rows
     // within a level is free for the sweeps), then deal index blocks
@@ -718,9 +1030,7 @@ static int plan_build_t(edfa_handle_s* h, cudaStream_t s)
     int64_t mx = 0;
     for (int r = 0; r < kCl; ++r) mx = htot[r] > mx ? htot[r] : mx;
     const int32_t cap = (int32_t)((mx + 3) & ~(int64_t)3);  // 16-byte rows for 4- and 8-byte values
-    const int64_t fixed = pad16((int64_t)cap * sizeof(T)) + ring;
-    if (fixed + 16 > optin) return EDFA_OK;  // does not fit: the sync-free sweeps stay in use
-    if (!cluster_schedulable<T>((size_t)(fixed + 16))) return EDFA_OK;
+    if (pad16((int64_t)cap * sizeof(T)) + min_extra_smem > optin) return EDFA_OK;
     rc = dalloc_t(h, &cp.rowof, (size_t)kCl * cap);
     if (rc) return rc;
     cudaMemsetAsync(cp.rowof, 0xFF, (size_t)kCl * cap * sizeof(int32_t), s);
@@ -729,9 +1039,6 @@ static int plan_build_t(edfa_handle_s* h, cudaStream_t s)
     const int64_t nlists = (int64_t)kCl * nlt;
     rc = dalloc_t(h, &cp.lofs, (size_t)nlists + 1);
     if (!rc) rc = dalloc_t(h, &cp.lrows, (size_t)2 * f.n);
-    if (!rc) rc = dalloc_t(h, &cp.lbyte, (size_t)nlists + 1);
-    if (!rc) rc = dalloc_t(h, &cp.lchunk, (size_t)nlists + 1);
-    if (!rc) rc = dalloc_t(h, &cp.meta, 2 * kCl);
     if (rc) return rc;
     ListGeom lg{f.fwd.perm, f.bwd.perm, f.fwd.loff, f.bwd.loff, nsf, nsb, nlf, nlb};
     const unsigned gl = (unsigned)((nsf + nsb + 255) / 256);
@@ -740,14 +1047,44 @@ static int plan_build_t(edfa_handle_s* h, cudaStream_t s)
     rc = scan_i64(h, cp.lofs, nlists, s);
     if (rc) return rc;
     unsigned long long* cursor = nullptr;
-    int* bad = nullptr;
     if (cudaMallocAsync((void**)&cursor, ((size_t)nlists + 1) * sizeof(int64_t), s) != cudaSuccess) return EDFA_ERR_OOM;
-    if (cudaMallocAsync((void**)&bad, sizeof(int), s) != cudaSuccess) return EDFA_ERR_OOM;
-    cudaMemsetAsync(bad, 0, sizeof(int), s);
     cudaMemcpyAsync(cursor, cp.lofs, ((size_t)nlists + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
     (edfa::count_launch(), k_cp_lists<1><<<gl, 256, 0, s>>>(lg, cp.posf, cursor, cp.lrows));
+    cudaFreeAsync(cursor, s);
+    cp.cap = cap;
+    cp.nlf = nlf;
+    cp.nlb = nlb;
+    cp.nlists = nlists;
+    *cap_out = cap;
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
+// level-synchronous variant: packed chunks streamed by TMA
+template <class T>
+static int plan_levelsync_t(edfa_handle_s* h, cudaStream_t s)
+{
+    ClusterPlan& cp = h->cp;
+    const Factor& f = h->fs;
+    const int64_t ring = (int64_t)kRing * kChunk + 16 * (kRing + 1);
+    int32_t cap = 0;
+    int rc = plan_common<T>(h, ring + 16, &cap, s);
+    if (rc || cap == 0) return rc;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    const int64_t fixed = pad16((int64_t)cap * sizeof(T)) + ring;
+    const void* fn = (const void*)k_s_cluster<T, T, kClLpr>;
+    if (!cluster_schedulable(fn, kClThreads, (size_t)(fixed + 16))) return EDFA_OK;
+    const int nlt = cp.nlf + cp.nlb;
+    const int64_t nlists = cp.nlists;
+    rc = dalloc_t(h, &cp.lbyte, (size_t)nlists + 1);
+    if (!rc) rc = dalloc_t(h, &cp.lchunk, (size_t)nlists + 1);
+    if (!rc) rc = dalloc_t(h, &cp.meta, 2 * kCl);
+    if (rc) return rc;
+    int* bad = nullptr;
+    if (cudaMallocAsync((void**)&bad, sizeof(int), s) != cudaSuccess) return EDFA_ERR_OOM;
+    cudaMemsetAsync(bad, 0, sizeof(int), s);
     const unsigned gL = (unsigned)((nlists + 127) / 128);
-    (edfa::count_launch(), k_cp_size<T><<<gL, 128, 0, s>>>(nlists, nlt, nlf, cp.lofs, cp.lrows, f.rowptr, f.diag,
+    (edfa::count_launch(), k_cp_size<T><<<gL, 128, 0, s>>>(nlists, nlt, cp.nlf, cp.lofs, cp.lrows, f.rowptr, f.diag,
                                                           cp.lbyte, cp.lchunk, bad));
     rc = scan_i64(h, cp.lbyte, nlists, s);
     if (!rc) rc = scan_i64(h, cp.lchunk, nlists, s);
@@ -759,7 +1096,6 @@ static int plan_build_t(edfa_handle_s* h, cudaStream_t s)
     cudaMemcpyAsync(meta, cp.meta, sizeof meta, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&total, cp.lbyte + nlists, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(cursor, s);
     cudaFreeAsync(bad, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return EDFA_ERR_CUDA;
     if (hbad) return EDFA_OK;
@@ -768,19 +1104,58 @@ static int plan_build_t(edfa_handle_s* h, cudaStream_t s)
     const int32_t szstride = (int32_t)((maxch + 7) & ~(int64_t)7);
     const int64_t smem = fixed + pad16((int64_t)szstride * 2);
     if (smem > optin) return EDFA_OK;
-    if (!cluster_schedulable<T>((size_t)smem)) return EDFA_OK;
+    if (!cluster_schedulable(fn, kClThreads, (size_t)smem)) return EDFA_OK;
     rc = dalloc(h, (void**)&cp.chunks, (size_t)total);
     if (!rc) rc = dalloc_t(h, &cp.sz, (size_t)kCl * szstride);
     if (!rc) rc = dalloc(h, &cp.bslot, (size_t)kCl * cap * sizeof(T));
     if (rc) return rc;
-    cp.cap = cap;
-    cp.nlf = nlf;
-    cp.nlb = nlb;
-    cp.nlists = nlists;
     cp.szstride = szstride;
     cp.smem = (size_t)smem;
     cp.bytes = total;
     cp.state = 1;
+    cp.kind = 2;
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
+// dataflow variant: fixed-size row records in processing order
+template <class T>
+static int plan_dataflow_t(edfa_handle_s* h, cudaStream_t s)
+{
+    ClusterPlan& cp = h->cp;
+    const Factor& f = h->fs;
+    int32_t cap = 0;
+    int rc = plan_common<T>(h, 64, &cap, s);
+    if (rc || cap == 0) return rc;
+    const size_t smem = (size_t)pad16((int64_t)cap * sizeof(T));
+    if (!cluster_schedulable((const void*)k_s_df<T, T, kDfLpr, kDfThreads, kDfSleep>, kDfThreads, smem)) return EDFA_OK;
+    const int nlt = cp.nlf + cp.nlb;
+    const int64_t nrec = 2 * (int64_t)f.n;
+    rc = dalloc_t(h, &cp.fidx, (size_t)f.n);
+    if (!rc) rc = dalloc_t(h, &cp.bidx, (size_t)kCl * cap);
+    if (!rc) rc = dalloc_t(h, &cp.rmeta, 2 * kCl);
+    if (!rc) rc = dalloc_t(h, &cp.ovoff, (size_t)nrec + 1);
+    if (rc) return rc;
+    cudaMemsetAsync(cp.bidx, 0xFF, (size_t)kCl * cap * sizeof(int64_t), s);
+    const unsigned gr = (unsigned)((nrec + 255) / 256);
+    (edfa::count_launch(), k_df_idx<<<gr, 256, 0, s>>>(nrec, nlt, cp.nlf, cp.lofs, cp.lrows, cp.posf, cap, cp.fidx,
+                                                     cp.bidx));
+    (edfa::count_launch(), k_df_ovf_count<<<gr, 256, 0, s>>>(nrec, nlt, cp.nlf, cp.lofs, cp.lrows, cp.posf, f.rowptr,
+                                                           f.diag, cp.ovoff));
+    rc = scan_i64(h, cp.ovoff, nrec, s);
+    if (rc) return rc;
+    (edfa::count_launch(), k_df_rmeta<<<1, 32, 0, s>>>(nlt, cp.nlf, cp.lofs, cp.rmeta));
+    int64_t novf = 0;
+    cudaMemcpyAsync(&novf, cp.ovoff + nrec, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return EDFA_ERR_CUDA;
+    rc = dalloc(h, (void**)&cp.rec, (size_t)nrec * df_rb<T>());
+    if (!rc) rc = dalloc_t(h, &cp.ovf_dep, (size_t)(novf > 0 ? novf : 1));
+    if (!rc) rc = dalloc(h, &cp.ovf_val, (size_t)(novf > 0 ? novf : 1) * sizeof(T));
+    if (rc) return rc;
+    cudaMemsetAsync(cp.rec, 0, (size_t)nrec * df_rb<T>(), s);
+    cp.smem = smem;
+    cp.bytes = nrec * df_rb<T>() + novf * (4 + (int64_t)sizeof(T));
+    cp.state = 1;
+    cp.kind = 1;
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
@@ -788,8 +1163,31 @@ int cluster_plan_build(edfa_handle_s* h, cudaStream_t s)
 {
     h->cp.state = 0;
     const Factor& f = h->fs;
-    if (h->opt.sweep_mode != 0 || f.n <= 0 || f.fwd.nlevels <= 0 || f.bwd.nlevels <= 0) return EDFA_OK;
-    return h->opt.precision == 1 ? plan_build_t<float>(h, s) : plan_build_t<double>(h, s);
+    const int mode = h->opt.sweep_mode;
+    if (mode == 1 || f.n <= 0 || f.fwd.nlevels <= 0 || f.bwd.nlevels <= 0) return EDFA_OK;
+    const bool f32 = h->opt.precision == 1;
+    if (mode == 2) return f32 ? plan_levelsync_t<float>(h, s) : plan_levelsync_t<double>(h, s);
+    return f32 ? plan_dataflow_t<float>(h, s) : plan_dataflow_t<double>(h, s);
+}
+
+template <class T>
+static int fill_t(edfa_handle_s* h, const T* lu, const T* dinv, cudaStream_t s)
+{
+    ClusterPlan& cp = h->cp;
+    const Factor& f = h->fs;
+    const int nlt = cp.nlf + cp.nlb;
+    if (cp.kind == 2) {
+        const unsigned gL = (unsigned)((cp.nlists + 127) / 128);
+        (edfa::count_launch(), k_cp_write<T><<<gL, 128, 0, s>>>(cp.nlists, nlt, cp.nlf, cp.lofs, cp.lrows, f.rowptr,
+                                                               f.col, f.diag, lu, dinv, cp.posf, cp.lbyte, cp.lchunk,
+                                                               cp.chunks, cp.sz, cp.szstride));
+    } else {
+        const int64_t nrec = 2 * (int64_t)f.n;
+        (edfa::count_launch(), k_df_write<T><<<(unsigned)((nrec + 127) / 128), 128, 0, s>>>(
+            nrec, nlt, cp.nlf, cp.lofs, cp.lrows, cp.posf, f.rowptr, f.col, f.diag, lu, dinv, cp.ovoff, cp.rec,
+            cp.ovf_dep, (T*)cp.ovf_val));
+    }
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
 int cluster_plan_fill(edfa_handle_s* h, cudaStream_t s)
@@ -797,17 +1195,8 @@ int cluster_plan_fill(edfa_handle_s* h, cudaStream_t s)
     ClusterPlan& cp = h->cp;
     if (cp.state != 1) return EDFA_OK;
     const Factor& f = h->fs;
-    const int nlt = cp.nlf + cp.nlb;
-    const unsigned gL = (unsigned)((cp.nlists + 127) / 128);
-    if (h->opt.precision == 1)
-        (edfa::count_launch(), k_cp_write<float><<<gL, 128, 0, s>>>(cp.nlists, nlt, cp.nlf, cp.lofs, cp.lrows, f.rowptr,
-                                                                   f.col, f.diag, f.lu32, f.dinv32, cp.posf, cp.lbyte,
-                                                                   cp.lchunk, cp.chunks, cp.sz, cp.szstride));
-    else
-        (edfa::count_launch(), k_cp_write<double><<<gL, 128, 0, s>>>(cp.nlists, nlt, cp.nlf, cp.lofs, cp.lrows,
-                                                                    f.rowptr, f.col, f.diag, f.lu64, f.dinv64, cp.posf,
-                                                                    cp.lbyte, cp.lchunk, cp.chunks, cp.sz, cp.szstride));
-    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+    if (h->opt.precision == 1) return fill_t<float>(h, f.lu32, f.dinv32, s);
+    return fill_t<double>(h, f.lu64, f.dinv64, s);
 }
 
 template <class T>
@@ -816,16 +1205,27 @@ int s_cluster_solve(edfa_handle_s* h, const double* rp, const int64_t* mptr, con
 {
     ClusterPlan& cp = h->cp;
     const Factor& f = h->fs;
-    (edfa::count_launch(), k_cp_rhs<T, double><<<(unsigned)((f.n + 255) / 256), 256, 0, s>>>(
-        f.n, cp.posf, cp.cap, rp, mptr, mcol, mval, mv, (T*)cp.bslot));
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = cluster_cfg(cp.smem, s, attr);
-    if (pe) cudaEventRecord(pe[0], s);
-    edfa::count_launch();
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_s_cluster<T, T, kClLpr>, (const T*)cp.bslot,
-                                       (const unsigned char*)cp.chunks, (const uint16_t*)cp.sz,
-                                       (const int64_t*)cp.meta, cp.szstride, cp.cap, cp.nlf, cp.nlb,
-                                       (const int32_t*)cp.rowof, out, h->err);
+    cudaError_t e;
+    if (cp.kind == 2) {
+        (edfa::count_launch(), k_cp_rhs<T, double><<<(unsigned)((f.n + 255) / 256), 256, 0, s>>>(
+            f.n, cp.posf, cp.cap, rp, mptr, mcol, mval, mv, (T*)cp.bslot));
+        cudaLaunchConfig_t cfg = cluster_cfg(cp.smem, kClThreads, s, attr);
+        if (pe) cudaEventRecord(pe[0], s);
+        edfa::count_launch();
+        e = cudaLaunchKernelEx(&cfg, k_s_cluster<T, T, kClLpr>, (const T*)cp.bslot, (const unsigned char*)cp.chunks,
+                               (const uint16_t*)cp.sz, (const int64_t*)cp.meta, cp.szstride, cp.cap, cp.nlf, cp.nlb,
+                               (const int32_t*)cp.rowof, out, h->err);
+    } else {
+        (edfa::count_launch(), k_df_rhs<T, double><<<(unsigned)((f.n + 255) / 256), 256, 0, s>>>(
+            f.n, cp.fidx, cp.rec, rp, mptr, mcol, mval, mv));
+        cudaLaunchConfig_t cfg = cluster_cfg(cp.smem, kDfThreads, s, attr);
+        if (pe) cudaEventRecord(pe[0], s);
+        edfa::count_launch();
+        e = cudaLaunchKernelEx(&cfg, k_s_df<T, T, kDfLpr, kDfThreads, kDfSleep>, cp.rec, (const int64_t*)cp.rmeta, cp.cap,
+                               (const int32_t*)cp.ovf_dep, (const T*)cp.ovf_val, (const int64_t*)cp.bidx,
+                               (const int32_t*)cp.rowof, out, h->err);
+    }
     if (pe) cudaEventRecord(pe[1], s);
     if (e != cudaSuccess) {
         cudaGetLastError();
