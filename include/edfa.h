@@ -101,7 +101,9 @@ typedef struct {
                                holding the solution in distributed shared memory, rows polling their
                                dependencies there, when N_e values fit and the cluster can be
                                scheduled; else sync-free all-SM sweeps); 1 = sync-free all-SM sweeps
-                               only; 2 = the cluster with one barrier per dependency level */
+                               only, also for A~ (no chain decomposition); 2 = the cluster with one
+                               barrier per dependency level.  In modes 0 and 2 the A~ sweeps run as a
+                               few phases of independent chains when their DAG allows it */
 } edfa_options;
 
 typedef struct edfa_handle_s* edfa_handle;

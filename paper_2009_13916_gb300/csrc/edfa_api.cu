@@ -200,7 +200,9 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     TRY(build_schur(h, s));
     cudaEventRecord(h->ev[4], s);
     TRY(factor_plan(h, h->fa, Nf, A->nnz, A->rowptr, A->col, s));
+    if (o.sweep_mode != 1) TRY(chain_plan_build(h, h->fa, s));
     TRY(factor_numeric(h, h->fa, A->val, h->a32, s));
+    TRY(chain_plan_values(h, h->fa, s));
     cudaEventRecord(h->ev[5], s);
     TRY(check_err(h, s));
 

@@ -113,6 +113,21 @@ struct SweepPlan {
     int64_t* loff = nullptr;  // [nlevels+1] start of every (padded) level in perm
 };
 
+// Phases of independent chains of a triangular sweep (k_chain.cu): rows of
+// phase p at positions off[p] + k * nc[p] + c (chain c, step k).
+struct ChainPlan {
+    int ok = 0;
+    int nph = 0;
+    int64_t npos = 0;
+    int64_t off[16] = {}, nc[16] = {};
+    int maxlen[16] = {};
+    int32_t* rowat = nullptr;  // [npos] row at every position (-1: padding)
+    int64_t* posof = nullptr;  // [n] position of every row
+    int* pred = nullptr;       // [n] chain predecessor (-1: head)
+    void* m = nullptr;         // [npos] factor entry at the chain predecessor
+    void* dv = nullptr;        // [npos] 1/u_ii (backward only)
+};
+
 struct Factor {
     // pattern (not owned unless owned_pattern)
     int32_t n = 0;
@@ -125,6 +140,7 @@ struct Factor {
     double* dinv64 = nullptr;  // 1 / U_ii
     float* dinv32 = nullptr;
     SweepPlan fwd, bwd;
+    ChainPlan chf, chb;  // chain decomposition of the sweeps (k_chain.cu), used when ok
 };
 
 // Packed per-CTA level chunks of both S~ sweeps for the single-cluster solve
@@ -254,6 +270,12 @@ int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64
 int factor_numeric(edfa_handle_s* h, Factor& f, const double* vals64, const float* vals32,
                    cudaStream_t s);
 int apply_prec(edfa_handle_s* h, const double* r, double* z, cudaStream_t s);
+// chain-decomposed sweeps (k_chain.cu)
+int chain_plan_build(edfa_handle_s* h, Factor& f, cudaStream_t s);
+int chain_plan_values(edfa_handle_s* h, Factor& f, cudaStream_t s);
+template <class T, class TB, class TO, int FWD>
+int chain_sweep(edfa_handle_s* h, const Factor& f, const TB* base, const int64_t* mptr, const int32_t* mcol,
+                const T* mval, const TO* mvec, TO* out, cudaStream_t s);
 // single-cluster S~ solves (k_cluster.cu)
 int cluster_plan_build(edfa_handle_s* h, cudaStream_t s);
 int cluster_plan_fill(edfa_handle_s* h, cudaStream_t s);

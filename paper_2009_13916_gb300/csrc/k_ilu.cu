@@ -866,6 +866,22 @@ static int launch_sweep(edfa_handle_s* h, const Factor& f, const TB* base, const
     return EDFA_OK;
 }
 
+// sweep of the A~ factor: chain-decomposed when its DAG collapses to a few
+// phases of chains (k_chain.cu), else the level-scheduled sync-free sweep
+template <class T, class TB, class TO, int FWD>
+static int a_sweep(edfa_handle_s* h, const TB* base, const int64_t* mptr, const int32_t* mcol, const T* mval,
+                   const TO* mv, TO* out, cudaStream_t s)
+{
+    const Factor& f = h->fa;
+    if ((FWD ? f.chf.ok : f.chb.ok) != 0) {
+        cudaEvent_t* pe = prof_begin(h, FWD ? 0 : 1, s);
+        const int rc = chain_sweep<T, TB, TO, FWD>(h, f, base, mptr, mcol, mval, mv, out, s);
+        if (pe) cudaEventRecord(pe[1], s);
+        return rc;
+    }
+    return launch_sweep<T, TB, TO, FWD, EDFA_LPR_A>(h, f, base, mptr, mcol, mval, mv, out, s);
+}
+
 // ------------------------------------------------------------ block apply
 // z = P^{-1} r, Eq. (EDFA_prec):
 //   y    = A~^{-1} r_pi                  (L sweep, U sweep of ILU(0)(A))
@@ -889,9 +905,9 @@ static int apply_impl(edfa_handle_s* h, const double* r, double* z, cudaStream_t
     int rc;
     if (h->opt.variant == 0) {
         // y = A~^{-1} r_pi
-        rc = launch_sweep<T, double, T, 1, EDFA_LPR_A>(h, h->fa, rpi, nullptr, nullptr, (const T*)nullptr, (const T*)nullptr, u2, s);
+        rc = a_sweep<T, double, T, 1>(h, rpi, nullptr, nullptr, (const T*)nullptr, (const T*)nullptr, u2, s);
         if (rc) return rc;
-        rc = launch_sweep<T, T, T, 0, EDFA_LPR_A>(h, h->fa, u2, nullptr, nullptr, (const T*)nullptr, (const T*)nullptr, u1, s);
+        rc = a_sweep<T, T, T, 0>(h, u2, nullptr, nullptr, (const T*)nullptr, (const T*)nullptr, u1, s);
         if (rc) return rc;
     }
     // z_p = U_S^{-1} L_S^{-1} (r_p - C y)   (C y omitted in the upper-triangular variant);
@@ -912,9 +928,9 @@ static int apply_impl(edfa_handle_s* h, const double* r, double* z, cudaStream_t
         if (rc) return rc;
     }
     // v = L_A^{-1} (r_pi - B z_p), z_pi = U_A^{-1} v
-    rc = launch_sweep<T, double, T, 1, EDFA_LPR_A>(h, h->fa, rpi, h->B.rowptr, h->B.col, bval, zpw, u2, s);
+    rc = a_sweep<T, double, T, 1>(h, rpi, h->B.rowptr, h->B.col, bval, (const T*)zpw, u2, s);
     if (rc) return rc;
-    rc = launch_sweep<T, T, double, 0, EDFA_LPR_A>(h, h->fa, u2, nullptr, nullptr, (const T*)nullptr, (const double*)nullptr, zpi, s);
+    rc = a_sweep<T, T, double, 0>(h, u2, nullptr, nullptr, (const T*)nullptr, (const double*)nullptr, zpi, s);
     if constexpr (sizeof(T) == 4) {
         if (rc) return rc;
         rc = to_f64_launch(zpw, zp, Ne, s);
