@@ -70,6 +70,12 @@ def lib():
                                        C.c_void_p, C.c_void_p, P(C.c_int32)]
         L.orc_schur.argtypes = [C.c_int, P(_CSR), P(_CSR), P(_CSR), C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p, P(_CSR)]
+        L.orc_filter_vectors.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                         P(C.c_void_p), P(C.c_void_p), P(C.c_void_p)]
+        L.orc_filter_rows.argtypes = [P(_CSR), C.c_double, P(_CSR)]
+        L.orc_htilde.argtypes = [C.c_int, P(_CSR), P(_CSR), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_void_p, P(_CSR)]
+        L.orc_d_minus_h.argtypes = [P(_CSR), P(_CSR), P(_CSR)]
         L.orc_ilu0.argtypes = [P(_CSR), C.c_void_p, P(C.c_int32)]
         L.orc_ilu0_solve.argtypes = [P(_CSR), C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_ilu0_solve.restype = None
@@ -198,6 +204,96 @@ def schur(form, A, C_, D, qptr, qidx, xval, gval=None) -> Mat:
     return Mat(n, ncols, rp, col, val)
 
 
+def _take_csr(out) -> Mat:
+    n, ncols, nnz = out.nrows, out.ncols, out.nnz
+    rp = np.ctypeslib.as_array(C.cast(out.rowptr, C.POINTER(C.c_int64)), shape=(n + 1,)).copy()
+    col = np.ctypeslib.as_array(C.cast(out.col, C.POINTER(C.c_int32)), shape=(max(nnz, 1),))[:nnz].copy()
+    val = np.ctypeslib.as_array(C.cast(out.val, C.POINTER(C.c_double)), shape=(max(nnz, 1),))[:nnz].copy()
+    lib().orc_free_csr(C.byref(out))
+    return Mat(n, ncols, rp, col, val)
+
+
+def filter_vectors(ptr, idx, val, tau):
+    """Pre-filtration (Algorithm 1): drop entries of each segment (column of
+    X~ or row of G~) with |v| < tau * ||segment||_2."""
+    ptr = np.ascontiguousarray(ptr, np.int64)
+    idx = np.ascontiguousarray(idx, np.int32)
+    val = np.ascontiguousarray(val, np.float64)
+    nseg = len(ptr) - 1
+    op, oi, ov = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    rc = lib().orc_filter_vectors(nseg, _ptr(ptr), _ptr(idx), _ptr(val), float(tau),
+                                  C.byref(op), C.byref(oi), C.byref(ov))
+    if rc:
+        raise RuntimeError("orc_filter_vectors failed")
+    optr = _take_int(op, nseg + 1, np.int64)
+    n = int(optr[-1])
+    oidx = _take_int(oi, n, np.int32)
+    oval = np.ctypeslib.as_array(C.cast(ov, C.POINTER(C.c_double)), shape=(max(n, 1),))[:n].copy()
+    lib().orc_free(ov)
+    return optr, oidx, oval
+
+
+def filter_rows(M, tau) -> Mat:
+    """Post-filtration (Algorithms 1 and 2): drop off-diagonal entries with
+    |m_ij| < tau * ||row i||_2."""
+    M = Mat.of(M)
+    out = _CSR()
+    if lib().orc_filter_rows(C.byref(M.c), float(tau), C.byref(out)):
+        raise RuntimeError("orc_filter_rows failed")
+    return _take_csr(out)
+
+
+def htilde(form, A, C_, Ne, xptr, xidx, xval, gptr=None, gidx=None, gval=None) -> Mat:
+    """H~ = C X~ (form 0) or G~ A F~ (form 1) on its structural pattern."""
+    A, C_ = Mat.of(A), Mat.of(C_)
+    xptr = np.ascontiguousarray(xptr, np.int64)
+    xidx = np.ascontiguousarray(xidx, np.int32)
+    xval = np.ascontiguousarray(xval, np.float64)
+    if gval is not None:
+        gptr = np.ascontiguousarray(gptr, np.int64)
+        gidx = np.ascontiguousarray(gidx, np.int32)
+        gval = np.ascontiguousarray(gval, np.float64)
+    out = _CSR()
+    rc = lib().orc_htilde(int(form), C.byref(A.c), C.byref(C_.c), int(Ne), _ptr(xptr), _ptr(xidx), _ptr(xval),
+                          _ptr(gptr), _ptr(gidx), _ptr(gval), C.byref(out))
+    if rc:
+        raise RuntimeError("orc_htilde failed")
+    return _take_csr(out)
+
+
+def d_minus_h(D, H) -> Mat:
+    """S~ = D - H~ on pattern(H~) u pattern(D) u diagonal (Algorithm 2)."""
+    D, H = Mat.of(D), Mat.of(H)
+    out = _CSR()
+    if lib().orc_d_minus_h(C.byref(D.c), C.byref(H.c), C.byref(out)):
+        raise RuntimeError("orc_d_minus_h failed")
+    return _take_csr(out)
+
+
+FILTERS = {"none": 0, "pre": 1, "post_h": 2, "post_s": 3}
+
+
+def schur_filtered(form, A, C_, D, qptr, qidx, xval, gval=None, filt="none", tau=0.0):
+    """S~ with one of the paper's filtrations (Sec. 3, Algorithms 1 and 2):
+    'pre' filters every X~ column (and G~ row) before H~ is formed, 'post_h'
+    filters the rows of H~ (Stage 1), 'post_s' the rows of S~ (Stage 2).
+    Returns (S~, H~ after filtration)."""
+    Ne = D.nrows
+    xptr, xidx, xv = qptr, qidx, xval
+    gptr, gidx, gv = (qptr, qidx, gval) if form == 1 else (None, None, None)
+    if filt == "pre":
+        xptr, xidx, xv = filter_vectors(qptr, qidx, xval, tau)
+        if form == 1:
+            gptr, gidx, gv = filter_vectors(qptr, qidx, gval, tau)
+    H = htilde(form, A, C_, Ne, xptr, xidx, xv, gptr, gidx, gv)
+    if filt == "post_h":
+        H = filter_rows(H, tau)
+    S = d_minus_h(D, H)
+    if filt == "post_s":
+        S = filter_rows(S, tau)
+    return S, H
+
+
 def ilu0(M):
     M = Mat.of(M)
     lu = np.empty(M.nnz)
@@ -302,11 +398,15 @@ def qsets_for(sysd, mode=None, thresh=None, dyn=None):
 
 
 def edfa_pipeline(sysd, mode=None, form=0, variant=0, restart=50, rtol=1e-8, maxit=2000, b=None,
-                  dyn=None, solve=True):
-    """The whole hot path on the CPU: Q sets, local solves, S~, ILU(0)s, FGMRES."""
+                  dyn=None, solve=True, filt="none", tau=0.0):
+    """The whole hot path on the CPU: Q sets, local solves, S~ (optionally
+    filtered), ILU(0)s, FGMRES."""
     qptr, qidx = qsets_for(sysd, mode, dyn=dyn)
     xval, gval = local_solves(sysd.A, sysd.B, sysd.C, qptr, qidx, True, form == 1)
-    S = schur(form, sysd.A, sysd.C, sysd.D, qptr, qidx, xval, gval)
+    if filt == "none":
+        S = schur(form, sysd.A, sysd.C, sysd.D, qptr, qidx, xval, gval)
+    else:
+        S, _ = schur_filtered(form, sysd.A, sysd.C, sysd.D, qptr, qidx, xval, gval, filt, tau)
     P = Prec(sysd.A, sysd.B, sysd.C, sysd.D, S=S, variant=variant)
     out = dict(qptr=qptr, qidx=qidx, xval=xval, gval=gval, S=S, prec=P)
     if solve:

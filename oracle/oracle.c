@@ -461,6 +461,209 @@ ORC_EXPORT int orc_schur(int form, const orc_csr* A, const orc_csr* C, const orc
     return 0;
 }
 
+/* ------------------------------------------------------- filtration */
+/* Pre- and post-filtration (Sec. 3, implementation details; Algorithm 1 and
+ * Algorithm 2): an entry is discarded when its absolute value is smaller than
+ * tau times the Euclidean norm of the vector it belongs to; diagonal entries
+ * of a square matrix are always kept.  A kept entry satisfies
+ * |v| >= tau * ||row||_2 (so tau = 0 keeps everything).  The norm is summed
+ * over the stored entries in storage order. */
+
+/* Pre-filtration of the local solution vectors: segment m (entries
+ * ptr[m]..ptr[m+1] of idx/val, e.g. column m of X~ on Q^(m) or row m of G~)
+ * loses every entry with |v| < tau ||segment m||_2.  Output malloc'd. */
+ORC_EXPORT int orc_filter_vectors(int32_t nseg, const int64_t* ptr, const int32_t* idx, const double* val,
+                                  double tau, int64_t** optr, int32_t** oidx, double** oval)
+{
+    int64_t tot = ptr[nseg];
+    int64_t* op = (int64_t*)malloc(((size_t)nseg + 1) * sizeof(int64_t));
+    int32_t* oi = (int32_t*)malloc((size_t)(tot ? tot : 1) * sizeof(int32_t));
+    double* ov = (double*)malloc((size_t)(tot ? tot : 1) * sizeof(double));
+    if (!op || !oi || !ov) { free(op); free(oi); free(ov); return -1; }
+    int64_t n = 0;
+    op[0] = 0;
+    for (int32_t m = 0; m < nseg; ++m) {
+        double ss = 0.0;
+        for (int64_t p = ptr[m]; p < ptr[m + 1]; ++p) ss += val[p] * val[p];
+        double lim = tau * sqrt(ss);
+        for (int64_t p = ptr[m]; p < ptr[m + 1]; ++p)
+            if (!(fabs(val[p]) < lim)) { oi[n] = idx[p]; ov[n] = val[p]; ++n; }
+        op[m + 1] = n;
+    }
+    *optr = op;
+    *oidx = oi;
+    *oval = ov;
+    return 0;
+}
+
+/* Post-filtration of the rows of a square CSR matrix (H~ or S~): entry
+ * (i, j), j != i, is discarded when |m_ij| < tau ||row i||_2. */
+ORC_EXPORT int orc_filter_rows(const orc_csr* M, double tau, orc_ocsr* out)
+{
+    const int32_t n = M->nrows;
+    int64_t tot = M->rowptr[n];
+    out->nrows = n;
+    out->ncols = M->ncols;
+    out->rowptr = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
+    out->col = (int32_t*)malloc((size_t)(tot ? tot : 1) * sizeof(int32_t));
+    out->val = (double*)malloc((size_t)(tot ? tot : 1) * sizeof(double));
+    if (!out->rowptr || !out->col || !out->val) return -1;
+    int64_t k = 0;
+    out->rowptr[0] = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        double ss = 0.0;
+        for (int64_t p = M->rowptr[i]; p < M->rowptr[i + 1]; ++p) ss += M->val[p] * M->val[p];
+        double lim = tau * sqrt(ss);
+        for (int64_t p = M->rowptr[i]; p < M->rowptr[i + 1]; ++p)
+            if (M->col[p] == i || !(fabs(M->val[p]) < lim)) {
+                out->col[k] = M->col[p];
+                out->val[k] = M->val[p];
+                ++k;
+            }
+        out->rowptr[i + 1] = k;
+    }
+    out->nnz = k;
+    return 0;
+}
+
+/* H~ alone, on its structural product pattern (Eq. sparse_S):
+ *   form 0: H~ = C X~, X~ column m stored on (xptr, xidx, xval)
+ *   form 1: H~ = G~ A F~ = -(G~ A) X~, G~ row m stored on (gptr, gidx, gval)
+ * X~ and G~ may carry different patterns (after pre-filtration). */
+ORC_EXPORT int orc_htilde(int form, const orc_csr* A, const orc_csr* C, int32_t Ne,
+                          const int64_t* xptr, const int32_t* xidx, const double* xval,
+                          const int64_t* gptr, const int32_t* gidx, const double* gval, orc_ocsr* H)
+{
+    const int32_t Nf = C->ncols;
+    int64_t tot = xptr[Ne];
+    int64_t* xr_ptr = (int64_t*)calloc((size_t)Nf + 1, sizeof(int64_t));
+    int32_t* xr_col = (int32_t*)malloc((size_t)(tot ? tot : 1) * sizeof(int32_t));
+    double* xr_val = (double*)malloc((size_t)(tot ? tot : 1) * sizeof(double));
+    int64_t* pos = (int64_t*)malloc(((size_t)Nf + 1) * sizeof(int64_t));
+    double* acc = (double*)calloc((size_t)Ne, sizeof(double));
+    char* mark = (char*)calloc((size_t)Ne, 1);
+    double* af = (double*)calloc((size_t)Nf, sizeof(double));
+    char* markf = (char*)calloc((size_t)Nf, 1);
+    if (!xr_ptr || !xr_col || !xr_val || !pos || !acc || !mark || !af || !markf) return -1;
+    /* row-wise copy of X~: for each face f, (m, X~[f,m]) with m ascending */
+    for (int64_t p = 0; p < tot; ++p) xr_ptr[xidx[p] + 1]++;
+    for (int32_t f = 0; f < Nf; ++f) xr_ptr[f + 1] += xr_ptr[f];
+    memcpy(pos, xr_ptr, ((size_t)Nf + 1) * sizeof(int64_t));
+    for (int32_t m = 0; m < Ne; ++m)
+        for (int64_t p = xptr[m]; p < xptr[m + 1]; ++p) {
+            int64_t t = pos[xidx[p]]++;
+            xr_col[t] = m;
+            xr_val[t] = xval[p];
+        }
+    ilist cols = {0}, fcols = {0}, hcol = {0};
+    int64_t vcap = 1024, vn = 0;
+    double* hval = (double*)malloc((size_t)vcap * sizeof(double));
+    H->nrows = Ne;
+    H->ncols = Ne;
+    H->rowptr = (int64_t*)malloc(((size_t)Ne + 1) * sizeof(int64_t));
+    if (!hval || !H->rowptr) return -1;
+    H->rowptr[0] = 0;
+    for (int32_t E = 0; E < Ne; ++E) {
+        cols.n = 0;
+        if (form == 0) {
+            for (int64_t p = C->rowptr[E]; p < C->rowptr[E + 1]; ++p) {
+                int32_t f = C->col[p];
+                double cv = C->val[p];
+                for (int64_t t = xr_ptr[f]; t < xr_ptr[f + 1]; ++t) {
+                    int32_t m = xr_col[t];
+                    if (!mark[m]) { mark[m] = 1; il_push(&cols, m); }
+                    acc[m] += cv * xr_val[t];
+                }
+            }
+        } else {
+            fcols.n = 0;
+            for (int64_t p = gptr[E]; p < gptr[E + 1]; ++p) {
+                int32_t f = gidx[p];
+                double gv = gval[p];
+                for (int64_t q = A->rowptr[f]; q < A->rowptr[f + 1]; ++q) {
+                    int32_t g = A->col[q];
+                    if (!markf[g]) { markf[g] = 1; il_push(&fcols, g); }
+                    af[g] += gv * A->val[q];
+                }
+            }
+            for (int64_t i = 0; i < fcols.n; ++i) {
+                int32_t g = fcols.v[i];
+                double tv = af[g];
+                for (int64_t t = xr_ptr[g]; t < xr_ptr[g + 1]; ++t) {
+                    int32_t m = xr_col[t];
+                    if (!mark[m]) { mark[m] = 1; il_push(&cols, m); }
+                    acc[m] += tv * (-xr_val[t]);
+                }
+                af[g] = 0.0;
+                markf[g] = 0;
+            }
+        }
+        int64_t n = sort_unique(cols.v, cols.n);
+        for (int64_t i = 0; i < n; ++i) {
+            int32_t m = cols.v[i];
+            il_push(&hcol, m);
+            if (vn == vcap) { vcap *= 2; hval = (double*)realloc(hval, (size_t)vcap * sizeof(double)); }
+            hval[vn++] = acc[m];
+            acc[m] = 0.0;
+            mark[m] = 0;
+        }
+        H->rowptr[E + 1] = hcol.n;
+    }
+    H->nnz = hcol.n;
+    H->col = hcol.v ? hcol.v : (int32_t*)malloc(sizeof(int32_t));
+    H->val = hval;
+    free(xr_ptr); free(xr_col); free(xr_val); free(pos); free(acc); free(mark); free(af); free(markf);
+    free(cols.v); free(fcols.v);
+    return 0;
+}
+
+/* S~ = D - H~ on pattern(H~) u pattern(D) u diagonal (Eq. sparse_S,
+ * Algorithm 2), columns ascending; each value is (-h) + d. */
+ORC_EXPORT int orc_d_minus_h(const orc_csr* D, const orc_csr* H, orc_ocsr* S)
+{
+    const int32_t Ne = D->nrows;
+    double* acc = (double*)calloc((size_t)(Ne ? Ne : 1), sizeof(double));
+    char* mark = (char*)calloc((size_t)(Ne ? Ne : 1), 1);
+    ilist cols = {0}, scol = {0};
+    int64_t vcap = 1024, vn = 0;
+    double* sval = (double*)malloc((size_t)vcap * sizeof(double));
+    S->nrows = Ne;
+    S->ncols = Ne;
+    S->rowptr = (int64_t*)malloc(((size_t)Ne + 1) * sizeof(int64_t));
+    if (!acc || !mark || !sval || !S->rowptr) return -1;
+    S->rowptr[0] = 0;
+    for (int32_t E = 0; E < Ne; ++E) {
+        cols.n = 0;
+        for (int64_t p = H->rowptr[E]; p < H->rowptr[E + 1]; ++p) {
+            int32_t m = H->col[p];
+            mark[m] = 1;
+            il_push(&cols, m);
+            acc[m] = -H->val[p];
+        }
+        for (int64_t p = D->rowptr[E]; p < D->rowptr[E + 1]; ++p) {
+            int32_t m = D->col[p];
+            if (!mark[m]) { mark[m] = 1; il_push(&cols, m); }
+            acc[m] += D->val[p];
+        }
+        if (!mark[E]) { mark[E] = 1; il_push(&cols, E); }
+        int64_t n = sort_unique(cols.v, cols.n);
+        for (int64_t i = 0; i < n; ++i) {
+            int32_t m = cols.v[i];
+            il_push(&scol, m);
+            if (vn == vcap) { vcap *= 2; sval = (double*)realloc(sval, (size_t)vcap * sizeof(double)); }
+            sval[vn++] = acc[m];
+            acc[m] = 0.0;
+            mark[m] = 0;
+        }
+        S->rowptr[E + 1] = scol.n;
+    }
+    S->nnz = scol.n;
+    S->col = scol.v ? scol.v : (int32_t*)malloc(sizeof(int32_t));
+    S->val = sval;
+    free(acc); free(mark); free(cols.v);
+    return 0;
+}
+
 /* ------------------------------------------------------------ ILU(0) */
 /* ILU(0) in the natural ordering (Saad, "Iterative Methods for Sparse Linear
  * Systems", Alg. 10.4, IKJ variant): L (unit lower) and U share the pattern

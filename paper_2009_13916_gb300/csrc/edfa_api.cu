@@ -456,7 +456,7 @@ int edfa_set_profiling(edfa_handle h, int32_t on)
     if (!h) return EDFA_ERR_INVALID;
     h->profiling = on ? 1 : 0;
     h->prof_used = 0;
-    for (int k = 0; k < 4; ++k) { h->stats.sweep_ms[k] = 0; h->stats.sweep_n[k] = 0; }
+    for (int k = 0; k < 5; ++k) { h->stats.sweep_ms[k] = 0; h->stats.sweep_n[k] = 0; }
     return EDFA_OK;
 }
 

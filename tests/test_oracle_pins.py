@@ -348,3 +348,104 @@ def test_adjoint_gradient_matches_finite_differences():
         lm[e] -= h
         fd = (loss(lp) - loss(lm)) / (2 * h)
         assert g[e] == pytest.approx(fd, rel=1e-6, abs=1e-12)
+
+
+# ------------------------------------------------------------ filtration
+# Pre- and post-filtration (Sec. 3, implementation details; Algorithms 1 and
+# 2): drop entries below tau times the Euclidean norm of their row (column of
+# X~, row of G~, H~ or S~), the diagonal of H~ and S~ always kept.
+def _pattern(M):
+    return {(i, int(j)) for i in range(M.nrows) for j in M.col[M.rowptr[i]:M.rowptr[i + 1]]}
+
+
+def _filter_dense_rows(M, struct, tau, keep_diag):
+    """Zero the entries of dense M (structural mask struct) that the paper's
+    rule discards; returns (values, mask)."""
+    out = M.copy()
+    mask = struct.copy()
+    for i in range(M.shape[0]):
+        lim = tau * np.sqrt(np.sum(M[i][struct[i]] ** 2))
+        drop = struct[i] & (np.abs(M[i]) < lim)
+        if keep_diag:
+            drop[i] = False
+        # no entry may sit at the threshold up to rounding, or the decision is fragile
+        near = struct[i] & (np.abs(np.abs(M[i]) - lim) <= 1e-9 * max(lim, 1e-300))
+        assert not near.any()
+        out[i][drop] = 0.0
+        mask[i][drop] = False
+    return out, mask
+
+
+@pytest.mark.parametrize("filt", ["pre", "post_h", "post_s"])
+@pytest.mark.parametrize("form", [0, 1])
+def test_filtration_zero_tolerance_is_unfiltered(filt, form):
+    sysd = full_tensor()
+    qptr, qidx = O.qsets("nbr", sysd.A, sysd.B, sysd.C)
+    x, g = O.local_solves(sysd.A, sysd.B, sysd.C, qptr, qidx, True, True)
+    S0 = O.schur(form, sysd.A, sysd.C, sysd.D, qptr, qidx, x, g)
+    S1, _ = O.schur_filtered(form, sysd.A, sysd.C, sysd.D, qptr, qidx, x, g, filt, 0.0)
+    assert np.array_equal(S0.rowptr, S1.rowptr) and np.array_equal(S0.col, S1.col)
+    assert np.array_equal(S0.val, S1.val)
+
+
+@pytest.mark.parametrize("tau", [1e-3, 3e-2])
+def test_filtration_against_dense_definitions(tau):
+    # Q^(m) = all faces: X~ = A^{-1} B exactly, so every filtered S~ has a dense
+    # definition computed here from numpy solves
+    sysd = full_tensor(n=(3, 2, 2), seed=21)
+    Ad, Cd, Dd = (M.dense() for M in (sysd.A, sysd.C, sysd.D))
+    Bd = sysd.B.dense()
+    qptr, qidx = all_faces_q(sysd)
+    x, g = O.local_solves(sysd.A, sysd.B, sysd.C, qptr, qidx, True, False)
+    X = np.linalg.solve(Ad, Bd)
+    Cs, Ds = Cd != 0, Dd != 0
+    eye = np.eye(sysd.Ne, dtype=bool)
+    # pre-filtration of the columns of X~ (no diagonal for an N_f x N_e block)
+    Xf, Xm = _filter_dense_rows(X.T, np.ones_like(X.T, dtype=bool), tau, keep_diag=False)
+    Xf, Xm = Xf.T, Xm.T
+    H = Cd @ Xf
+    Hs = (Cs.astype(int) @ Xm.astype(int)) > 0
+    ref = {"pre": (Dd - H, Hs | Ds | eye)}
+    # post-filtration of the rows of H~ = C X~
+    H = Cd @ X
+    Hs = (Cs.astype(int) @ np.ones_like(X, dtype=int)) > 0
+    Hf, Hm = _filter_dense_rows(H, Hs, tau, keep_diag=True)
+    ref["post_h"] = (Dd - Hf, Hm | Ds | eye)
+    # post-filtration of the rows of S~ = D - H~
+    S = Dd - H
+    Sf, Sm = _filter_dense_rows(S, Hs | Ds | eye, tau, keep_diag=True)
+    ref["post_s"] = (Sf, Sm)
+    for filt, (Sref, Mref) in ref.items():
+        Sg, _ = O.schur_filtered(0, sysd.A, sysd.C, sysd.D, qptr, qidx, x, None, filt, tau)
+        assert _pattern(Sg) == {(int(i), int(j)) for i, j in zip(*np.nonzero(Mref))}, filt
+        np.testing.assert_allclose(Sg.to_scipy().toarray(), Sref, atol=1e-10 * np.abs(Sref).max())
+
+
+def test_filtration_limits_and_monotonicity():
+    sysd = full_tensor(n=(4, 3, 3), seed=8)
+    qptr, qidx = O.qsets("nbr", sysd.A, sysd.B, sysd.C)
+    x, g = O.local_solves(sysd.A, sysd.B, sysd.C, qptr, qidx, True, True)
+    S0 = O.schur(0, sysd.A, sysd.C, sysd.D, qptr, qidx, x, g).to_scipy().toarray()
+    Dd = sysd.D.dense()
+    H0 = Dd - S0
+    big = 1e30
+    # tau -> infinity: post_s keeps the diagonal of S~ only
+    Sg, _ = O.schur_filtered(0, sysd.A, sysd.C, sysd.D, qptr, qidx, x, g, "post_s", big)
+    assert np.array_equal(Sg.to_scipy().toarray(), np.diag(np.diag(S0)))
+    # post_h keeps only the diagonal of H~: S~ = D - diag(H~) on pattern(D) u diagonal
+    Sg, _ = O.schur_filtered(0, sysd.A, sysd.C, sysd.D, qptr, qidx, x, g, "post_h", big)
+    ref = Dd - np.diag(np.diag(H0))
+    np.testing.assert_allclose(Sg.to_scipy().toarray(), ref, atol=1e-13 * np.abs(ref).max())
+    assert _pattern(Sg) == {(int(i), int(j)) for i, j in zip(*np.nonzero((Dd != 0) | np.eye(sysd.Ne, dtype=bool)))}
+    # pre-filtration that drops every entry of X~: S~ = D
+    Sg, _ = O.schur_filtered(0, sysd.A, sysd.C, sysd.D, qptr, qidx, x, g, "pre", big)
+    assert np.array_equal(Sg.to_scipy().toarray(), Dd)
+    # patterns shrink as tau grows
+    for filt in ("pre", "post_h", "post_s"):
+        prev = None
+        for tau in (0.0, 1e-4, 1e-3, 1e-2, 1e-1):
+            Sg, _ = O.schur_filtered(0, sysd.A, sysd.C, sysd.D, qptr, qidx, x, g, filt, tau)
+            pat = _pattern(Sg)
+            if prev is not None:
+                assert pat <= prev, (filt, tau)
+            prev = pat
