@@ -104,7 +104,23 @@ typedef struct {
                                only, also for A~ (no chain decomposition); 2 = the cluster with one
                                barrier per dependency level.  In modes 0 and 2 the A~ sweeps run as a
                                few phases of independent chains when their DAG allows it */
+    int32_t filtration;     /* sparsification of S~ (Sec. 3, implementation details): one of
+                               EDFA_FILT_*; an entry is discarded when its absolute value is below
+                               tau_filt times the Euclidean norm of the vector it belongs to, and
+                               diagonal entries of H~ and S~ are always kept */
+    double tau_filt;        /* filtration tolerance (>= 0; 0 keeps every entry) */
 } edfa_options;
+
+/* Filtration of the approximate Schur complement (Algorithms 1 and 2). */
+enum {
+    EDFA_FILT_NONE = 0,
+    EDFA_FILT_PRE = 1,     /* pre-filtration: every local solution X~ column m (and G~ row m in the
+                              two-sided form) before H~ is formed (Stage 1) */
+    EDFA_FILT_POST_H = 2,  /* post-filtration of the rows of H~ (Stage 1; S~ = D - H~ keeps the
+                              pattern of D) */
+    EDFA_FILT_POST_S = 3   /* post-filtration of the rows of S~ = D - H~ (Stage 2: the pattern of S~,
+                              its ILU(0) levels and sweep plans are rebuilt by every edfa_setup) */
+};
 
 typedef struct edfa_handle_s* edfa_handle;
 
@@ -139,8 +155,10 @@ typedef struct {
        with the bytes of their packed level chunks */
     int32_t s_cluster;
     int64_t s_cluster_bytes;
-    /* Stage 2 split: S~ values, S~ level plans (build only), numeric ILU(0) of
-       S~, packing of the cluster sweep chunks */
+    /* Stage 2 split: S~ values; S~ pattern (post-filtration of S~), level
+       plans and cluster-record layout (edfa_build, and every edfa_setup with
+       post-filtration of S~); numeric ILU(0) of S~; writing of the cluster
+       sweep records */
     float ms_s_values, ms_s_plan, ms_s_factor, ms_s_cluster;
 } edfa_stats;
 

@@ -20,6 +20,7 @@ __all__ = ["EdfaError", "Csr", "Options", "SolveInfo", "Stats", "Edfa", "lib", "
            "edfa_build", "edfa_setup", "edfa_apply", "edfa_matvec", "edfa_solve", "edfa_free"]
 
 QMODES = {"own": 0, "nbr": 1, "crow": 2, "thresh": 3, "dynamic": 4, "given": 5}
+FILTERS = {"none": 0, "pre": 1, "post_h": 2, "post_s": 3}
 
 EDFA_OK = 0
 EDFA_ERR_NOT_CONVERGED = 5
@@ -43,7 +44,8 @@ class Options(C.Structure):
                 ("n_ent", C.c_int32), ("it_max", C.c_int32), ("qptr", C.c_void_p),
                 ("qidx", C.c_void_p), ("schur_form", C.c_int32), ("variant", C.c_int32),
                 ("precision", C.c_int32), ("warps_per_block", C.c_int32),
-                ("sweep_warps_per_sm", C.c_int32), ("sweep_mode", C.c_int32)]
+                ("sweep_warps_per_sm", C.c_int32), ("sweep_mode", C.c_int32),
+                ("filtration", C.c_int32), ("tau_filt", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -231,7 +233,7 @@ class Edfa:
 
     def __init__(self, A, B, C_, D, Nf: int, Ne: int, qmode="own", thresh=0.05, n_add=1, n_ent=4,
                  it_max=100, qsets=None, schur_form=0, variant=0, precision=0, warps_per_block=0,
-                 sweep_warps_per_sm=0, sweep_mode=0, stream=None):
+                 sweep_warps_per_sm=0, sweep_mode=0, filtration="none", tau_filt=0.0, stream=None):
         self._keep = [A, B, C_, D]
         self.Nf, self.Ne = int(Nf), int(Ne)
         opt = Options()
@@ -249,6 +251,8 @@ class Edfa:
         opt.warps_per_block = int(warps_per_block)
         opt.sweep_warps_per_sm = int(sweep_warps_per_sm)
         opt.sweep_mode = int(sweep_mode)
+        opt.filtration = FILTERS[filtration] if isinstance(filtration, str) else int(filtration)
+        opt.tau_filt = float(tau_filt)
         self.opt = opt
         self._D = D
         self.h = edfa_build(csr(*A, self.Nf), csr(*B, self.Ne), csr(*C_, self.Nf), csr(*D, self.Ne), opt,

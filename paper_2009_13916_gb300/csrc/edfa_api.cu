@@ -74,6 +74,8 @@ static void free_all(edfa_handle_s* h)
     if (h->batch_del) h->batch_del(h->batch);
     for (auto& b : h->owned) cudaFree(b.p);
     h->owned.clear();
+    for (auto& b : h->owned_s2) cudaFree(b.p);
+    h->owned_s2.clear();
     if (h->err_host) cudaFreeHost(h->err_host);
     if (h->hbuf_host) cudaFreeHost(h->hbuf_host);
     for (auto& e : h->ev)
@@ -102,6 +104,8 @@ void edfa_default_options(edfa_options* o)
     o->variant = 0;
     o->precision = 0;
     o->warps_per_block = 0;
+    o->filtration = EDFA_FILT_NONE;
+    o->tau_filt = 0.0;
 }
 
 const char* edfa_strerror(int code)
@@ -147,6 +151,9 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     if (o.qmode == EDFA_Q_DYNAMIC && (o.n_add < 0 || o.n_ent < 0 || o.it_max < 0)) return EDFA_ERR_INVALID;
     if (o.schur_form < 0 || o.schur_form > 1 || o.variant < 0 || o.variant > 1 || o.precision < 0 ||
         o.precision > 1)
+        return EDFA_ERR_INVALID;
+    if (o.filtration < EDFA_FILT_NONE || o.filtration > EDFA_FILT_POST_S || !(o.tau_filt >= 0.0) ||
+        !std::isfinite(o.tau_filt))
         return EDFA_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
 
@@ -197,6 +204,7 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     cudaEventRecord(h->ev[2], s);
     TRY(check_err(h, s));
     cudaEventRecord(h->ev[3], s);
+    TRY(prefilter(h, s));
     TRY(build_schur(h, s));
     cudaEventRecord(h->ev[4], s);
     TRY(factor_plan(h, h->fa, Nf, A->nnz, A->rowptr, A->col, s));
@@ -210,11 +218,11 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     cudaEventRecord(h->ev[6], s);
     TRY(stage2_values(h, s));
     cudaEventRecord(h->ev[8], s);
-    TRY(factor_plan(h, h->fs, Ne, h->s_nnz, h->s_ptr, h->s_col, s));
+    TRY(stage2_pattern(h, s));
+    TRY(stage2_symbolic(h, s));
     cudaEventRecord(h->ev[9], s);
-    TRY(factor_numeric(h, h->fs, h->s_val, h->s_val32, s));
+    TRY(factor_numeric(h, h->fs, h->sf_val, h->sf_val32, s));
     cudaEventRecord(h->ev[10], s);
-    TRY(cluster_plan_build(h, s));
     TRY(cluster_plan_fill(h, s));
     cudaEventRecord(h->ev[7], s);
 
@@ -238,7 +246,7 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     h->stats.n_local = Ne;
     h->stats.q_total = h->qtot;
     h->stats.q_max = h->qmax;
-    h->stats.s_nnz = h->s_nnz;
+    h->stats.s_nnz = h->sf_nnz;
     h->stats.s_cluster = h->cp.state == 1;
     h->stats.s_cluster_bytes = h->cp.state == 1 ? h->cp.bytes : 0;
     h->stats.levels_a = h->fa.fwd.nlevels;
@@ -259,11 +267,15 @@ int edfa_setup(edfa_handle h, const edfa_csr* D, edfa_stream stream)
     if (!rc) rc = check_err(h, s);
     if (rc) return rc;
     h->D = *D;
+    const bool replan = h->opt.filtration == EDFA_FILT_POST_S;
     cudaEventRecord(h->ev[6], s);
     rc = stage2_values(h, s);
     cudaEventRecord(h->ev[8], s);
+    // post-filtration of S~ changes its pattern with D: new levels and records
+    if (!rc && replan) rc = stage2_pattern(h, s);
+    if (!rc && replan) rc = stage2_symbolic(h, s);
     cudaEventRecord(h->ev[9], s);
-    if (!rc) rc = factor_numeric(h, h->fs, h->s_val, h->s_val32, s);
+    if (!rc) rc = factor_numeric(h, h->fs, h->sf_val, h->sf_val32, s);
     cudaEventRecord(h->ev[10], s);
     if (!rc) rc = cluster_plan_fill(h, s);
     cudaEventRecord(h->ev[7], s);
@@ -274,6 +286,14 @@ int edfa_setup(edfa_handle h, const edfa_csr* D, edfa_stream stream)
     h->stats.ms_stage2 = ms;
     cudaEventElapsedTime(&ms, h->ev[6], h->ev[8]); h->stats.ms_s_values = ms;
     h->stats.ms_s_plan = 0;
+    if (replan) {
+        cudaEventElapsedTime(&ms, h->ev[8], h->ev[9]);
+        h->stats.ms_s_plan = ms;
+        h->stats.s_nnz = h->sf_nnz;
+        h->stats.levels_s = h->fs.fwd.nlevels;
+        h->stats.s_cluster = h->cp.state == 1;
+        h->stats.s_cluster_bytes = h->cp.state == 1 ? h->cp.bytes : 0;
+    }
     cudaEventElapsedTime(&ms, h->ev[9], h->ev[10]); h->stats.ms_s_factor = ms;
     cudaEventElapsedTime(&ms, h->ev[10], h->ev[7]); h->stats.ms_s_cluster = ms;
     return EDFA_OK;
@@ -432,11 +452,12 @@ int edfa_get_view(edfa_handle h, edfa_view* v)
     v->xval = h->xval;
     v->gval = h->gval;
     v->xval_f32 = h->xval32;
-    v->s_nnz = h->s_nnz;
-    v->s_rowptr = h->s_ptr;
-    v->s_col = h->s_col;
-    v->s_val = h->s_val;
-    v->s_val_f32 = h->s_val32;
+    // the S~ the preconditioner factorises (after post-filtration of S~, if any)
+    v->s_nnz = h->sf_nnz;
+    v->s_rowptr = h->sf_ptr;
+    v->s_col = h->sf_col;
+    v->s_val = h->sf_val;
+    v->s_val_f32 = h->sf_val32;
     return EDFA_OK;
 }
 

@@ -195,6 +195,17 @@ struct edfa_handle_s {
     int32_t qmax = 0;
     double *xval = nullptr, *gval = nullptr;
     float *xval32 = nullptr, *gval32 = nullptr;
+    // X~ and G~ as the Schur product reads them: the restriction sets and the
+    // local solutions, or what pre-filtration kept of them (own patterns)
+    int64_t* x_ptr = nullptr;
+    int32_t* x_idx = nullptr;
+    int64_t x_tot = 0;
+    double* xf64 = nullptr;
+    float* xf32 = nullptr;
+    int64_t* g_ptr = nullptr;
+    int32_t* g_idx = nullptr;
+    double* gf64 = nullptr;
+    float* gf32 = nullptr;
     // X~ rows: cells whose set holds each face
     int64_t* xr_ptr = nullptr;
     int32_t* xr_cell = nullptr;
@@ -205,6 +216,14 @@ struct edfa_handle_s {
     double *h_val = nullptr, *s_val = nullptr;
     float *h_val32 = nullptr, *s_val32 = nullptr;
     int64_t* d_map = nullptr;  // position of each D entry in S~
+    // the S~ the inner ILU(0) factorises: (s_ptr, s_col, s_val) itself or,
+    // with post-filtration of S~, a filtered copy rebuilt at every Stage 2
+    int64_t sf_nnz = 0;
+    int64_t* sf_ptr = nullptr;
+    int32_t* sf_col = nullptr;
+    double* sf_val = nullptr;
+    float* sf_val32 = nullptr;
+    int64_t* sf_cnt = nullptr;  // [Ne+1] row counts of the filtered copy
     // ILU(0) factors
     edfa::Factor fa, fs;
     edfa::ClusterPlan cp;
@@ -234,6 +253,9 @@ struct edfa_handle_s {
     edfa_stats stats{};
     std::vector<double> hist;
     std::vector<edfa::DBuf> owned;  // every device allocation, released by edfa_free
+    // allocations of the S~ factor plan (sweep levels, cluster records): kept
+    // apart so that a Stage 2 that changes the pattern of S~ can replace them
+    std::vector<edfa::DBuf> owned_s2;
     // workspace of the batched solve, reused across calls with the same layout
     void* batch = nullptr;
     void (*batch_del)(void*) = nullptr;
@@ -265,6 +287,12 @@ int build_qsets_dynamic(edfa_handle_s* h, cudaStream_t s);
 int run_local_solves(edfa_handle_s* h, cudaStream_t s);
 int build_schur(edfa_handle_s* h, cudaStream_t s);
 int stage2_values(edfa_handle_s* h, cudaStream_t s);
+// filtration (k_filter.cu)
+int prefilter(edfa_handle_s* h, cudaStream_t s);
+template <class T>
+int postfilter_h(edfa_handle_s* h, T* h_val, cudaStream_t s);
+int stage2_pattern(edfa_handle_s* h, cudaStream_t s);
+int stage2_symbolic(edfa_handle_s* h, cudaStream_t s);
 int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64_t* rowptr,
                 const int32_t* col, cudaStream_t s);
 int factor_numeric(edfa_handle_s* h, Factor& f, const double* vals64, const float* vals32,

@@ -69,9 +69,11 @@ struct SchurArgs {
     int32_t Ne;
     Csr<T> A, C;
     Csr<double> D;
-    const int64_t* qptr;
-    const int32_t* qidx;
+    const int64_t* xptr;  // X~ column m on (xptr, xidx): Q^(m), or what pre-filtration kept of it
+    const int32_t* xidx;
     const T* xval;
+    const int64_t* gptr;  // G~ row m on (gptr, gidx) (two-sided form)
+    const int32_t* gidx;
     const T* gval;
     const int64_t* xr_ptr;
     const int32_t* xr_cell;
@@ -161,22 +163,22 @@ __global__ void __launch_bounds__(kSWarps * 32) k_schur(SchurArgs<T> a)
             int* ut = key;  // reuse as a second hash table
             for (int i = lane; i < kHS; i += 32) ut[i] = -1;
             __syncwarp();
-            for (int64_t p = a.qptr[E]; p < a.qptr[E + 1]; ++p) {
-                int f = a.qidx[p];
+            for (int64_t p = a.gptr[E]; p < a.gptr[E + 1]; ++p) {
+                int f = a.gidx[p];
                 for (int64_t q = a.A.rowptr[f] + lane; q < a.A.rowptr[f + 1]; q += 32) hs_insert(ut, a.A.col[q]);
             }
             __syncwarp();
             nu = hs_compact_sort(ut, ul, kUCap, lane);
             if (nu < 0) { overflow = true; nu = 0; }
             // u_g = sum_{f in Q^(E)} G~[E,f] A[f,g]  (A symmetric: row g of A), ascending f
-            const int64_t qb = a.qptr[E], qe = a.qptr[E + 1];
+            const int64_t qb = a.gptr[E], qe = a.gptr[E + 1];
             for (int t = lane; t < nu; t += 32) {
                 int gidx = ul[t];
                 int64_t pa = a.A.rowptr[gidx], ea = a.A.rowptr[gidx + 1];
                 int64_t pq = qb;
                 T acc = T(0);
                 while (pa < ea && pq < qe) {
-                    int ca = a.A.col[pa], cq = a.qidx[pq];
+                    int ca = a.A.col[pa], cq = a.gidx[pq];
                     if (ca == cq) { acc = fma(a.gval[pq], a.A.val[pa], acc); ++pa; ++pq; }
                     else if (ca < cq) ++pa;
                     else ++pq;
@@ -222,13 +224,13 @@ __global__ void __launch_bounds__(kSWarps * 32) k_schur(SchurArgs<T> a)
         for (int t = lane; t < n; t += 32) {
             const int m = key[t];
             a.s_col[sb + t] = m;
-            const int64_t qb = a.qptr[m], qe = a.qptr[m + 1];
+            const int64_t qb = a.xptr[m], qe = a.xptr[m + 1];
             T acc = T(0);
             if (a.form == 0) {
                 // H~[E,m] = sum over f in C_E and Q^(m), ascending f
                 int64_t pc = a.C.rowptr[E], ec = a.C.rowptr[E + 1], pq = qb;
                 while (pc < ec && pq < qe) {
-                    int cc = a.C.col[pc], cq = a.qidx[pq];
+                    int cc = a.C.col[pc], cq = a.xidx[pq];
                     if (cc == cq) { acc = fma(a.C.val[pc], a.xval[pq], acc); ++pc; ++pq; }
                     else if (cc < cq) ++pc;
                     else ++pq;
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(kSWarps * 32) k_schur(SchurArgs<T> a)
             } else {
                 // H~[E,m] = -sum_{g in Q^(m)} u_g X~[g,m]
                 for (int64_t pq = qb; pq < qe; ++pq) {
-                    int pos = bsearch_i(ul, nu, a.qidx[pq]);
+                    int pos = bsearch_i(ul, nu, a.xidx[pq]);
                     if (pos >= 0) acc = fma(-uv[pos], a.xval[pq], acc);
                 }
             }
@@ -268,17 +270,17 @@ static int schur_t(edfa_handle_s* h, const T* xval, const T* gval, T** h_val, cu
     const int32_t Ne = h->Ne, Nf = h->Nf;
     // X~ row pattern
     int rc = dalloc_t(h, &h->xr_ptr, (size_t)Nf + 1);
-    if (!rc) rc = dalloc_t(h, &h->xr_cell, (size_t)(h->qtot > 0 ? h->qtot : 1));
+    if (!rc) rc = dalloc_t(h, &h->xr_cell, (size_t)(h->x_tot > 0 ? h->x_tot : 1));
     if (rc) return rc;
     cudaMemsetAsync(h->xr_ptr, 0, ((size_t)Nf + 1) * sizeof(int64_t), s);
-    if (h->qtot > 0)
-        (edfa::count_launch(), k_q_count<<<(unsigned)((h->qtot + 255) / 256), 256, 0, s>>>(h->qidx, h->qtot, (unsigned long long*)h->xr_ptr));
+    if (h->x_tot > 0)
+        (edfa::count_launch(), k_q_count<<<(unsigned)((h->x_tot + 255) / 256), 256, 0, s>>>(h->x_idx, h->x_tot, (unsigned long long*)h->xr_ptr));
     rc = scan_i64(h, h->xr_ptr, Nf, s);
     if (rc) return rc;
     unsigned long long* cursor = nullptr;
     if (cudaMallocAsync((void**)&cursor, ((size_t)Nf + 1) * sizeof(int64_t), s) != cudaSuccess) return EDFA_ERR_OOM;
     cudaMemcpyAsync(cursor, h->xr_ptr, ((size_t)Nf + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
-    if (Ne > 0) (edfa::count_launch(), k_q_fill<<<(Ne + 255) / 256, 256, 0, s>>>(Ne, h->qptr, h->qidx, cursor, h->xr_cell));
+    if (Ne > 0) (edfa::count_launch(), k_q_fill<<<(Ne + 255) / 256, 256, 0, s>>>(Ne, h->x_ptr, h->x_idx, cursor, h->xr_cell));
     if (Nf > 0) (edfa::count_launch(), k_row_sort2<<<(Nf + 255) / 256, 256, 0, s>>>(h->xr_ptr, h->xr_cell, Nf));
     cudaFreeAsync(cursor, s);
 
@@ -293,9 +295,11 @@ static int schur_t(edfa_handle_s* h, const T* xval, const T* gval, T** h_val, cu
         a.C = Csr<float>{h->C.nrows, h->C.ncols, h->C.nnz, h->C.rowptr, h->C.col, h->c32};
     }
     a.D = csr_of(h->D);
-    a.qptr = h->qptr;
-    a.qidx = h->qidx;
+    a.xptr = h->x_ptr;
+    a.xidx = h->x_idx;
     a.xval = xval;
+    a.gptr = h->g_ptr;
+    a.gidx = h->g_idx;
     a.gval = gval;
     a.xr_ptr = h->xr_ptr;
     a.xr_cell = h->xr_cell;
@@ -365,17 +369,20 @@ static int schur_t(edfa_handle_s* h, const T* xval, const T* gval, T** h_val, cu
     a.d_map = h->d_map;
     if (sw == 1) (edfa::count_launch(), k_schur<T, 1, 1><<<(unsigned)grid, 32, 0, s>>>(a));
     else (edfa::count_launch(), k_schur<T, 1, 2><<<(unsigned)grid, 64, 0, s>>>(a));
-    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return EDFA_ERR_CUDA;
+    // post-filtration of H~ (Algorithm 1, Stage 1): compacts the S~ pattern
+    if (h->opt.filtration == EDFA_FILT_POST_H) return postfilter_h<T>(h, *h_val, s);
+    return EDFA_OK;
 }
 
 int build_schur(edfa_handle_s* h, cudaStream_t s)
 {
     if (h->opt.precision == 1) {
-        int rc = schur_t<float>(h, h->xval32, h->gval32, &h->h_val32, s);
+        int rc = schur_t<float>(h, h->xf32, h->gf32, &h->h_val32, s);
         if (!rc) rc = dalloc_t(h, &h->s_val32, (size_t)(h->s_nnz > 0 ? h->s_nnz : 1));
         return rc;
     }
-    int rc = schur_t<double>(h, h->xval, h->gval, &h->h_val, s);
+    int rc = schur_t<double>(h, h->xf64, h->gf64, &h->h_val, s);
     if (!rc) rc = dalloc_t(h, &h->s_val, (size_t)(h->s_nnz > 0 ? h->s_nnz : 1));
     return rc;
 }
