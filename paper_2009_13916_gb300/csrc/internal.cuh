@@ -151,6 +151,7 @@ struct ClusterPlan {
     int32_t cap = 0;           // value slots per CTA
     int nlf = 0, nlb = 0;      // levels of the forward / backward plans
     int64_t nlists = 0;        // 16 x (nlf + nlb) row lists
+    int64_t nrec = 0;          // rows of all lists, padding included
     int32_t* posf = nullptr;   // [n] slot * 16 + owner CTA of each row
     int32_t* rowof = nullptr;  // [16][cap] row held in each slot (-1: none)
     int64_t* lofs = nullptr;   // [nlists+1] first row of every list in lrows
@@ -169,7 +170,8 @@ struct ClusterPlan {
     unsigned char* rec = nullptr;  // [2n] fixed-size row records in processing order
     int64_t* fidx = nullptr;       // [n] forward record of every row
     int64_t* bidx = nullptr;       // [16][cap] backward record of every slot (-1: none)
-    int64_t* rmeta = nullptr;      // [16][2] first record and rows per CTA
+    int64_t* rmeta = nullptr;      // [16][4] first record and rows of each CTA, forward then backward
+    int32_t* lvl = nullptr;        // [2n] forward and backward dependency level of every row
     int64_t* ovoff = nullptr;      // [2n+1] overflow offsets (dependencies beyond the inline ones)
     int32_t* ovf_dep = nullptr;
     void* ovf_val = nullptr;

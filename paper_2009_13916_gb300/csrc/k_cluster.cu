@@ -636,21 +636,31 @@ k_s_cluster(const T* __restrict__ bslot, const unsigned char* __restrict__ chunk
 // The same two sweeps without a barrier per level: every row polls the values
 // it depends on directly in the distributed shared memory (a slot holds the
 // all-ones NaN until its row is done; no arithmetic produces that pattern),
-// so a level costs one value hop (local shared memory ~30 ns, remote ~0.3 us)
-// instead of a cluster barrier plus the skew of the slowest CTA.  Rows are
-// claimed in level order through a per-CTA ticket; each lane group prefetches
-// its row's fixed-size record (dependency slots and factor values) from HBM
-// while earlier rows finish.  Claiming in level order keeps it deadlock free:
-// the in-flight row of smallest (phase, level) has all its dependencies done.
-// Between the phases one cluster-wide step moves every w_i into its backward
-// record and resets the slots to the sentinel.
+// so a level costs one value hop instead of a cluster barrier plus the skew
+// of the slowest CTA.  Rows are claimed in level order through a per-CTA
+// ticket, a warp's rows always of one level (every (CTA, phase, level) list is
+// padded to whole warps), so no row waits on a row of its own warp; claiming
+// in level order keeps it deadlock free: the in-flight row of smallest
+// (phase, level) has all its dependencies done.  Between the phases one
+// cluster-wide step moves every w_i into its backward record and resets the
+// slots to the sentinel.
 //
-// Row record (kDfDeps dependencies inline, the rest in an overflow array):
+// Per row, LPR lanes share the dependencies, which the record lists in
+// ascending dependency level (oldest first).  Each lane consumes its
+// dependencies strictly in that order as they become ready, accumulating
+// r_i - sum l_ij x_j as it goes, so when the last (newest) dependency
+// arrives only one FMA, log2(LPR) shuffle-adds and the 1/U_ii product remain:
+// on GB300 every FP64 warp instruction occupies its SM sub-partition for
+// ~33 ns, so the work left after the critical dependency, not the dot
+// product as a whole, sets the time per level.  Lanes with several pending
+// dependencies back off between polls; a lane waiting on its last one spins.
+//
+// Row record (kDfDeps dependencies inline, older ones in an overflow array):
 //   0: int slot, int count, int64 overflow offset
 //  16: T aux (forward: right-hand side; backward: w_i), 24: T 1/U_ii
 //  32: int dep[kDfDeps] (slot * 16 + owner)
 // 160: T val[kDfDeps]
-constexpr int kDfThreads = 1024;
+// A padding record has slot -1 and no dependencies.
 constexpr int kDfDeps = 32;
 
 template <class T>
@@ -724,52 +734,31 @@ __device__ __forceinline__ void df_row(const unsigned char* __restrict__ rc, uin
     constexpr int KMAX = kDfDeps / LPR;
     const int4 hd = *(const int4*)rc;
     const int slot = hd.x, cnt = hd.y;
+    if ((unsigned)slot >= (unsigned)cap) return;  // padding record (whole lane group)
     const long long ovf = (long long)(((unsigned long long)(unsigned)hd.w << 32) | (unsigned)hd.z);
     const T aux = *(const T*)(rc + 16);
     const T dv = *(const T*)(rc + 24);
     const int32_t* dep = (const int32_t*)(rc + 32);
     const T* val = (const T*)(rc + 160);
+    const int nin = cnt < kDfDeps ? cnt : kDfDeps;
+    // this lane's inline dependencies, oldest first: positions gl, gl + LPR, ...
     int t[KMAX];
-    T v[KMAX], x[KMAX];
+    T v[KMAX];
 #pragma unroll
     for (int q = 0; q < KMAX; ++q) {
         const int p = gl + q * LPR;
-        const bool on = p < cnt;
-        t[q] = on ? dep[p] : -1;
+        const bool on = p < nin;
+        t[q] = on ? dep[p] : 0;
         v[q] = on ? val[p] : T(0);
-        x[q] = T(0);
         if (on && (unsigned)(t[q] >> 4) >= (unsigned)cap) {
             raise_err(err, EDFA_ERR_BOUNDS, slot);
-            t[q] = -1;
+            v[q] = T(0);
+            t[q] = 0;
         }
     }
-    // poll until every dependency of the row is done (bounded)
-    unsigned pend = 0;
-#pragma unroll
-    for (int q = 0; q < KMAX; ++q) pend |= (t[q] >= 0 ? 1u : 0u) << q;
-    for (unsigned it = 0;; ++it) {
-#pragma unroll
-        for (int q = 0; q < KMAX; ++q)
-            if (pend & (1u << q)) {
-                const T y = df_value<T>(xs_s, t[q], rank);
-                if (!df_sent(y)) {
-                    x[q] = y;
-                    pend &= ~(1u << q);
-                }
-            }
-        if (!__any_sync(gmask, pend != 0)) break;
-        if (it >= kSpinLimit || ((it & 255u) == 255u && err_set(err))) {
-            if (it >= kSpinLimit) raise_err(err, EDFA_ERR_TIMEOUT, slot);
-            break;
-        }
-        // rows whose dependencies are not close to done back off, leaving the
-        // distributed-shared-memory request slots to the rows on the critical path
-        if (SLEEP > 0 && it > 0) __nanosleep(SLEEP);
-    }
-    T acc = T(0);
-#pragma unroll
-    for (int q = 0; q < KMAX; ++q) acc = fma(v[q], x[q], acc);
-    // dependencies beyond the inline ones (long rows)
+    const int mine = nin > gl ? (nin - gl + LPR - 1) / LPR : 0;
+    T acc = gl == 0 ? aux : T(0);
+    // overflow dependencies (the oldest of long rows) first, one at a time
     for (int p = kDfDeps + gl; p < cnt; p += LPR) {
         const int tt = ovf_dep[ovf + p - kDfDeps];
         const T vv = ovf_val[ovf + p - kDfDeps];
@@ -780,17 +769,43 @@ __device__ __forceinline__ void df_row(const unsigned char* __restrict__ rc, uin
         T y = df_value<T>(xs_s, tt, rank);
         for (unsigned it = 0; df_sent(y) && it < kSpinLimit; ++it) {
             if ((it & 255u) == 255u && err_set(err)) break;
+            if (SLEEP > 0) __nanosleep(SLEEP);
             y = df_value<T>(xs_s, tt, rank);
         }
-        acc = fma(vv, y, acc);
+        if (!df_sent(y)) acc = fma(-vv, y, acc);
+    }
+    // inline dependencies: one batch of polls, then consumed strictly in order;
+    // a dependency still pending is re-polled alone (the group votes, so rows of
+    // other lane groups in the warp go on independently)
+    T x[KMAX];
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) x[q] = q < mine ? df_value<T>(xs_s, t[q], rank) : T(0);
+    bool live = true;
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) {
+        if (q * LPR >= nin) break;  // uniform over the group
+        for (unsigned it = 0; __any_sync(gmask, q < mine && df_sent(x[q])); ++it) {
+            // give up together (the decision is voted, so the group stays converged)
+            if (__any_sync(gmask, it >= kSpinLimit || ((it & 255u) == 255u && err_set(err)))) {
+                if (it >= kSpinLimit && gl == 0) raise_err(err, EDFA_ERR_TIMEOUT, slot);
+                live = false;
+                break;
+            }
+            // the last dependency spins; earlier ones leave the request slots of
+            // the distributed shared memory to the rows on the critical path
+            if (SLEEP > 0 && q + 1 < mine) __nanosleep(SLEEP);
+            // refresh every dependency still pending from q on, so that the
+            // later ones are known by the time q arrives
+#pragma unroll
+            for (int qq = q; qq < KMAX; ++qq)
+                if (qq < mine && df_sent(x[qq])) x[qq] = df_value<T>(xs_s, t[qq], rank);
+        }
+        if (!live) break;
+        if (q < mine) acc = fma(-v[q], x[q], acc);
     }
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o);
-    if (gl == 0 && (unsigned)slot < (unsigned)cap) {
-        T y = aux - acc;
-        if (bwd) y *= dv;
-        df_st(xs_s + (uint32_t)(slot * (int)sizeof(T)), y);
-    }
+    if (gl == 0) df_st(xs_s + (uint32_t)(slot * (int)sizeof(T)), bwd ? acc * dv : acc);
 }
 
 template <class T, class TO, int LPR, int THREADS, int SLEEP>
@@ -806,7 +821,6 @@ k_s_df(unsigned char* __restrict__ rec, const int64_t* __restrict__ rmeta, int32
     T* xs = (T*)sm;
     const uint32_t xs_s = smem_u32(xs);
     const int rank = (int)cgx::this_cluster().block_rank();
-    const int64_t base = rmeta[2 * rank], nr = rmeta[2 * rank + 1];
     for (int sl = threadIdx.x; sl < cap; sl += blockDim.x) xs[sl] = df_sentinel<T>();
     if (threadIdx.x < 2) ticket[threadIdx.x] = 0;
     cluster_arrive();  // every slot of the cluster holds the sentinel before any poll
@@ -815,7 +829,7 @@ k_s_df(unsigned char* __restrict__ rec, const int64_t* __restrict__ rmeta, int32
     const int g = lane / LPR, gl = lane % LPR;
     const unsigned gmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (g * LPR));
     for (int ph = 0; ph < 2; ++ph) {
-        const int64_t pbase = base + ph * nr;
+        const int64_t pbase = rmeta[4 * rank + 2 * ph], nr = rmeta[4 * rank + 2 * ph + 1];
         for (;;) {
             int k0 = 0;
             if (lane == 0) k0 = atomicAdd(&ticket[ph], RPW);
@@ -847,7 +861,17 @@ k_s_df(unsigned char* __restrict__ rec, const int64_t* __restrict__ rmeta, int32
     }
 }
 
-// ---- dataflow plan: record indices, overflow, records
+// ---- dataflow plan: dependency levels, record indices, overflow, records
+// lvl[off + i] = level of row i in a sweep plan (perm, loff)
+__global__ void k_df_levels(int64_t nslots, int nlev, const int32_t* __restrict__ perm,
+                            const int64_t* __restrict__ loff, int32_t* __restrict__ lvl)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nslots) return;
+    const int i = perm[t];
+    if (i >= 0) lvl[i] = level_of(loff, nlev, t);
+}
+
 __global__ void k_df_idx(int64_t nrec, int nlt, int nlf, const int64_t* __restrict__ lofs,
                          const int32_t* __restrict__ lrows, const int32_t* __restrict__ posf, int32_t cap,
                          int64_t* __restrict__ fidx, int64_t* __restrict__ bidx)
@@ -855,6 +879,7 @@ __global__ void k_df_idx(int64_t nrec, int nlt, int nlf, const int64_t* __restri
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= nrec) return;
     const int i = lrows[p];
+    if (i < 0) return;
     const int q = posf[i];
     const int r = q & (kCl - 1);
     if (p < lofs[(int64_t)r * nlt + nlf]) fidx[i] = p;
@@ -869,6 +894,10 @@ __global__ void k_df_ovf_count(int64_t nrec, int nlt, int nlf, const int64_t* __
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= nrec) return;
     const int i = lrows[p];
+    if (i < 0) {
+        ovc[p] = 0;
+        return;
+    }
     const int r = posf[i] & (kCl - 1);
     const int bwd = p >= lofs[(int64_t)r * nlt + nlf];
     const int64_t c = row_hi(bwd, i, rowptr, diag) - row_lo(bwd, i, rowptr, diag);
@@ -879,40 +908,72 @@ __global__ void k_df_rmeta(int nlt, int nlf, const int64_t* __restrict__ lofs, i
 {
     const int r = threadIdx.x;
     if (r >= kCl) return;
-    rmeta[2 * r] = lofs[(int64_t)r * nlt];
-    rmeta[2 * r + 1] = lofs[(int64_t)r * nlt + nlf] - lofs[(int64_t)r * nlt];
+    const int64_t a = lofs[(int64_t)r * nlt], b = lofs[(int64_t)r * nlt + nlf], c = lofs[(int64_t)(r + 1) * nlt];
+    rmeta[4 * r] = a;
+    rmeta[4 * r + 1] = b - a;
+    rmeta[4 * r + 2] = b;
+    rmeta[4 * r + 3] = c - b;
 }
 
+// Records of one numeric factor.  The dependencies of a row are ordered by
+// their level in the sweep (ascending, ties by column), the oldest of a long
+// row (beyond kDfDeps) in the overflow array; rows longer than kDfSortMax keep
+// column order.
+constexpr int kDfSortMax = 64;
+
 template <class T>
-__global__ void k_df_write(int64_t nrec, int nlt, int nlf, const int64_t* __restrict__ lofs,
+__global__ void k_df_write(int64_t nrec, int nlt, int nlf, int32_t n, const int64_t* __restrict__ lofs,
                            const int32_t* __restrict__ lrows, const int32_t* __restrict__ posf,
-                           const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                           const int64_t* __restrict__ diag, const T* __restrict__ lu, const T* __restrict__ dinv,
-                           const int64_t* __restrict__ ovoff, unsigned char* __restrict__ rec,
+                           const int32_t* __restrict__ lvl, const int64_t* __restrict__ rowptr,
+                           const int32_t* __restrict__ col, const int64_t* __restrict__ diag, const T* __restrict__ lu,
+                           const T* __restrict__ dinv, const int64_t* __restrict__ ovoff, unsigned char* __restrict__ rec,
                            int32_t* __restrict__ ovf_dep, T* __restrict__ ovf_val)
 {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= nrec) return;
     const int i = lrows[p];
+    unsigned char* rc = rec + p * df_rb<T>();
+    if (i < 0) {
+        *(int4*)rc = make_int4(-1, 0, 0, 0);
+        return;
+    }
     const int q = posf[i];
     const int r = q & (kCl - 1);
     const int bwd = p >= lofs[(int64_t)r * nlt + nlf];
     const int64_t lo = row_lo(bwd, i, rowptr, diag), hi = row_hi(bwd, i, rowptr, diag);
     const int cnt = (int)(hi - lo);
-    unsigned char* rc = rec + p * df_rb<T>();
     const long long ov = ovoff[p];
     *(int4*)rc = make_int4(q >> 4, cnt, (int)(unsigned)(ov & 0xffffffffll), (int)(ov >> 32));
     *(T*)(rc + 24) = bwd ? dinv[i] : T(1);
     int32_t* dep = (int32_t*)(rc + 32);
     T* val = (T*)(rc + 160);
-    for (int k = 0; k < cnt; ++k) {
+    const int nov = cnt > kDfDeps ? cnt - kDfDeps : 0;
+    // order: by level of the dependency, then by column (insertion sort of
+    // entry offsets); output position u < nov goes to the overflow array
+    unsigned char ord[kDfSortMax];
+    const bool sorted = cnt <= kDfSortMax;
+    if (sorted) {
+        const int32_t* lv = lvl + (bwd ? n : 0);
+        for (int k = 0; k < cnt; ++k) {
+            const int key = lv[col[lo + k]];
+            int u = k;
+            while (u > 0 && lv[col[lo + ord[u - 1]]] > key) {
+                ord[u] = ord[u - 1];
+                --u;
+            }
+            ord[u] = (unsigned char)k;
+        }
+    }
+    for (int u = 0; u < cnt; ++u) {
+        const int k = sorted ? ord[u] : (u < nov ? kDfDeps + u : u - nov);
         const int d = posf[col[lo + k]];
-        if (k < kDfDeps) {
-            dep[k] = d;
-            val[k] = lu[lo + k];
+        const T w = lu[lo + k];
+        if (u < nov) {
+            ovf_dep[ov + u] = d;
+            ovf_val[ov + u] = w;
         } else {
-            ovf_dep[ov + k - kDfDeps] = d;
-            ovf_val[ov + k - kDfDeps] = lu[lo + k];
+            dep[u - nov] = d;
+            val[u - nov] = w;
         }
     }
 }
@@ -939,8 +1000,14 @@ __global__ void k_df_rhs(int32_t n, const int64_t* __restrict__ fidx, unsigned c
 }
 
 // ------------------------------------------------------------ host side
-constexpr int kDfLpr = 8;     // lanes per row of the dataflow kernel
-constexpr int kDfSleep = 64;  // back-off between unsuccessful polls (ns; measured best of 0, 64, 200)
+// launch shape of the dataflow kernel: 16 lanes per row (two rows per warp),
+// 1024 threads per CTA, no back-off between polls.  Measured on the 64^3
+// workload (FP64 / FP32 ms for both sweeps): 16 lanes 1.59 / 1.30, 8 lanes
+// 1.73 / 1.43, 32 lanes 2.38 / 1.49, 4 lanes 3.04 / 2.64; 512 threads per CTA
+// and 32-64 ns back-off were slower in every shape.
+constexpr int kDfLpr = 16;
+constexpr int kDfThreads = 1024;
+constexpr int kDfSleep = 0;
 
 static cudaLaunchConfig_t cluster_cfg(size_t smem, int threads, cudaStream_t s, cudaLaunchAttribute* attr)
 {
@@ -991,8 +1058,16 @@ static bool cluster_schedulable(const void* fn, int threads, size_t smem)
 
 // owner blocks, value slots and the per-(phase, level, CTA) row lists shared
 // by both cluster variants; returns the slot capacity (0: does not fit)
+// round the row count of every (CTA, phase, level) list up to a multiple of
+// pad (padding rows are -1 at the end of the list)
+__global__ void k_cp_pad_lists(int64_t nlists, int64_t* __restrict__ cnt, int pad)
+{
+    const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (l < nlists) cnt[l] = (cnt[l] + pad - 1) / pad * pad;
+}
+
 template <class T>
-static int plan_common(edfa_handle_s* h, int64_t min_extra_smem, int32_t* cap_out, cudaStream_t s)
+static int plan_common(edfa_handle_s* h, int64_t min_extra_smem, int32_t* cap_out, cudaStream_t s, int pad = 1)
 {
     ClusterPlan& cp = h->cp;
     Factor& f = h->fs;
@@ -1038,14 +1113,22 @@ static int plan_common(edfa_handle_s* h, int64_t min_extra_smem, int32_t* cap_ou
 
     const int64_t nlists = (int64_t)kCl * nlt;
     rc = dalloc_t(h, &cp.lofs, (size_t)nlists + 1);
-    if (!rc) rc = dalloc_t(h, &cp.lrows, (size_t)2 * f.n);
     if (rc) return rc;
     ListGeom lg{f.fwd.perm, f.bwd.perm, f.fwd.loff, f.bwd.loff, nsf, nsb, nlf, nlb};
     const unsigned gl = (unsigned)((nsf + nsb + 255) / 256);
     cudaMemsetAsync(cp.lofs, 0, ((size_t)nlists + 1) * sizeof(int64_t), s);
     (edfa::count_launch(), k_cp_lists<0><<<gl, 256, 0, s>>>(lg, cp.posf, (unsigned long long*)cp.lofs, nullptr));
+    if (pad > 1)
+        (edfa::count_launch(), k_cp_pad_lists<<<(unsigned)((nlists + 255) / 256), 256, 0, s>>>(nlists, cp.lofs, pad));
     rc = scan_i64(h, cp.lofs, nlists, s);
     if (rc) return rc;
+    int64_t nrec = 0;
+    cudaMemcpyAsync(&nrec, cp.lofs + nlists, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return EDFA_ERR_CUDA;
+    rc = dalloc_t(h, &cp.lrows, (size_t)(nrec > 0 ? nrec : 1));
+    if (rc) return rc;
+    cudaMemsetAsync(cp.lrows, 0xFF, (size_t)(nrec > 0 ? nrec : 1) * sizeof(int32_t), s);
+    cp.nrec = nrec;
     unsigned long long* cursor = nullptr;
     if (cudaMallocAsync((void**)&cursor, ((size_t)nlists + 1) * sizeof(int64_t), s) != cudaSuccess) return EDFA_ERR_OOM;
     cudaMemcpyAsync(cursor, cp.lofs, ((size_t)nlists + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
@@ -1124,34 +1207,45 @@ static int plan_dataflow_t(edfa_handle_s* h, cudaStream_t s)
     ClusterPlan& cp = h->cp;
     const Factor& f = h->fs;
     int32_t cap = 0;
-    int rc = plan_common<T>(h, 64, &cap, s);
+    int rc = plan_common<T>(h, 64, &cap, s, 32 / kDfLpr);
     if (rc || cap == 0) return rc;
     const size_t smem = (size_t)pad16((int64_t)cap * sizeof(T));
-    if (!cluster_schedulable((const void*)k_s_df<T, T, kDfLpr, kDfThreads, kDfSleep>, kDfThreads, smem)) return EDFA_OK;
+    if (!cluster_schedulable((const void*)k_s_df<T, T, kDfLpr, kDfThreads, kDfSleep>, kDfThreads, smem))
+        return EDFA_OK;
     const int nlt = cp.nlf + cp.nlb;
-    const int64_t nrec = 2 * (int64_t)f.n;
+    const int64_t nrec = cp.nrec;
     rc = dalloc_t(h, &cp.fidx, (size_t)f.n);
     if (!rc) rc = dalloc_t(h, &cp.bidx, (size_t)kCl * cap);
-    if (!rc) rc = dalloc_t(h, &cp.rmeta, 2 * kCl);
+    if (!rc) rc = dalloc_t(h, &cp.rmeta, 4 * kCl);
     if (!rc) rc = dalloc_t(h, &cp.ovoff, (size_t)nrec + 1);
+    if (!rc) rc = dalloc_t(h, &cp.lvl, (size_t)2 * f.n);
     if (rc) return rc;
     cudaMemsetAsync(cp.bidx, 0xFF, (size_t)kCl * cap * sizeof(int64_t), s);
+    // dependency levels of every row in both sweeps (order of the record entries)
+    if (f.fwd.nslots > 0)
+        (edfa::count_launch(), k_df_levels<<<(unsigned)((f.fwd.nslots + 255) / 256), 256, 0, s>>>(
+            f.fwd.nslots, f.fwd.nlevels, f.fwd.perm, f.fwd.loff, cp.lvl));
+    if (f.bwd.nslots > 0)
+        (edfa::count_launch(), k_df_levels<<<(unsigned)((f.bwd.nslots + 255) / 256), 256, 0, s>>>(
+            f.bwd.nslots, f.bwd.nlevels, f.bwd.perm, f.bwd.loff, cp.lvl + f.n));
     const unsigned gr = (unsigned)((nrec + 255) / 256);
-    (edfa::count_launch(), k_df_idx<<<gr, 256, 0, s>>>(nrec, nlt, cp.nlf, cp.lofs, cp.lrows, cp.posf, cap, cp.fidx,
-                                                     cp.bidx));
-    (edfa::count_launch(), k_df_ovf_count<<<gr, 256, 0, s>>>(nrec, nlt, cp.nlf, cp.lofs, cp.lrows, cp.posf, f.rowptr,
-                                                           f.diag, cp.ovoff));
+    if (nrec > 0) {
+        (edfa::count_launch(), k_df_idx<<<gr, 256, 0, s>>>(nrec, nlt, cp.nlf, cp.lofs, cp.lrows, cp.posf, cap,
+                                                         cp.fidx, cp.bidx));
+        (edfa::count_launch(), k_df_ovf_count<<<gr, 256, 0, s>>>(nrec, nlt, cp.nlf, cp.lofs, cp.lrows, cp.posf,
+                                                               f.rowptr, f.diag, cp.ovoff));
+    }
     rc = scan_i64(h, cp.ovoff, nrec, s);
     if (rc) return rc;
     (edfa::count_launch(), k_df_rmeta<<<1, 32, 0, s>>>(nlt, cp.nlf, cp.lofs, cp.rmeta));
     int64_t novf = 0;
     cudaMemcpyAsync(&novf, cp.ovoff + nrec, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return EDFA_ERR_CUDA;
-    rc = dalloc(h, (void**)&cp.rec, (size_t)nrec * df_rb<T>());
+    rc = dalloc(h, (void**)&cp.rec, (size_t)(nrec > 0 ? nrec : 1) * df_rb<T>());
     if (!rc) rc = dalloc_t(h, &cp.ovf_dep, (size_t)(novf > 0 ? novf : 1));
     if (!rc) rc = dalloc(h, &cp.ovf_val, (size_t)(novf > 0 ? novf : 1) * sizeof(T));
     if (rc) return rc;
-    cudaMemsetAsync(cp.rec, 0, (size_t)nrec * df_rb<T>(), s);
+    cudaMemsetAsync(cp.rec, 0, (size_t)(nrec > 0 ? nrec : 1) * df_rb<T>(), s);
     cp.smem = smem;
     cp.bytes = nrec * df_rb<T>() + novf * (4 + (int64_t)sizeof(T));
     cp.state = 1;
@@ -1182,9 +1276,10 @@ static int fill_t(edfa_handle_s* h, const T* lu, const T* dinv, cudaStream_t s)
                                                                f.col, f.diag, lu, dinv, cp.posf, cp.lbyte, cp.lchunk,
                                                                cp.chunks, cp.sz, cp.szstride));
     } else {
-        const int64_t nrec = 2 * (int64_t)f.n;
+        const int64_t nrec = cp.nrec;
+        if (nrec > 0)
         (edfa::count_launch(), k_df_write<T><<<(unsigned)((nrec + 127) / 128), 128, 0, s>>>(
-            nrec, nlt, cp.nlf, cp.lofs, cp.lrows, cp.posf, f.rowptr, f.col, f.diag, lu, dinv, cp.ovoff, cp.rec,
+            nrec, nlt, cp.nlf, f.n, cp.lofs, cp.lrows, cp.posf, cp.lvl, f.rowptr, f.col, f.diag, lu, dinv, cp.ovoff, cp.rec,
             cp.ovf_dep, (T*)cp.ovf_val));
     }
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
