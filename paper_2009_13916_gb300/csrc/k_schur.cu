@@ -7,9 +7,15 @@
 //
 // Two passes, one warp per row of S~: a shared-memory hash set collects the
 // column candidates (cells m whose set Q^(m) meets the faces reached from row
-// E), pass 0 counts them, pass 1 sorts them and computes every entry as an
-// ordered merge of two ascending index lists (no atomics in the value path,
-// so the result is deterministic).
+// E) and pass 0 counts them.  The numeric pass (k_schur_num) sorts them, maps
+// every column to its position through the same hash, and forms the row as a
+// row-wise (Gustavson) product: for every face f of row E of C in ascending
+// order, the lanes take the cells m of row f of X~ (distinct within one f) and
+// add C[E,f] X~[f,m] into a shared-memory accumulator, with a warp barrier
+// between faces.  Every entry is thus summed over ascending f, the order of
+// the plain definition; no atomics touch values, so the result is
+// deterministic.  X~ is read through a row-major copy (cells and values of
+// every face row) made once per build.
 #include <climits>
 
 #include "internal.cuh"
@@ -34,6 +40,37 @@ __global__ void k_q_fill(int32_t Ne, const int64_t* qptr, const int32_t* qidx, u
     for (int64_t p = qptr[m]; p < qptr[m + 1]; ++p) {
         unsigned long long pos = atomicAdd(&cursor[qidx[p]], 1ull);
         xr_cell[pos] = (int32_t)m;
+    }
+}
+
+// row-major copy of X~ with its values: face row f lists (m, X~[f,m])
+template <class T>
+__global__ void k_q_fill_vals(int32_t Ne, const int64_t* qptr, const int32_t* qidx, const T* xv,
+                              unsigned long long* cursor, int32_t* xr_cell, T* xr_val)
+{
+    int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= Ne) return;
+    for (int64_t p = qptr[m]; p < qptr[m + 1]; ++p) {
+        unsigned long long pos = atomicAdd(&cursor[qidx[p]], 1ull);
+        xr_cell[pos] = (int32_t)m;
+        xr_val[pos] = xv[p];
+    }
+}
+
+// sort (col, val) pairs of every row by col (insertion sort, rows are short)
+template <class T>
+__global__ void k_row_sort_pairs(const int64_t* ptr, int32_t* col, T* val, int64_t n)
+{
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int64_t b = ptr[r], e = ptr[r + 1];
+    for (int64_t p = b + 1; p < e; ++p) {
+        int32_t v = col[p];
+        T w = val[p];
+        int64_t q = p - 1;
+        while (q >= b && col[q] > v) { col[q + 1] = col[q]; val[q + 1] = val[q]; --q; }
+        col[q + 1] = v;
+        val[q + 1] = w;
     }
 }
 
@@ -86,19 +123,6 @@ struct SchurArgs {
     DevErr* err;
 };
 
-// binary search of key in sorted a[0..n)
-__device__ __forceinline__ int bsearch_i(const int* a, int n, int key)
-{
-    int lo = 0, hi = n - 1;
-    while (lo <= hi) {
-        int mid = (lo + hi) >> 1;
-        int v = a[mid];
-        if (v == key) return mid;
-        if (v < key) lo = mid + 1; else hi = mid - 1;
-    }
-    return -1;
-}
-
 __device__ __forceinline__ void warp_bitonic(int* a, int n2, int lane)
 {
     for (int k = 2; k <= n2; k <<= 1)
@@ -139,8 +163,9 @@ __device__ int hs_compact_sort(const int* tab, int* out, int cap, int lane)
     return n;
 }
 
-template <class T, int PASS, int kSWarps>
-__global__ void __launch_bounds__(kSWarps * 32) k_schur(SchurArgs<T> a)
+// counting pass: the number of columns of every row of S~ (and the longest)
+template <class T, int kSWarps>
+__global__ void __launch_bounds__(kSWarps * 32) k_schur_count(SchurArgs<T> a)
 {
     __shared__ int s_tab[kSWarps][kHS];
     __shared__ int s_key[kSWarps][kHS];
@@ -210,44 +235,199 @@ __global__ void __launch_bounds__(kSWarps * 32) k_schur(SchurArgs<T> a)
         if (cnt > kHS * 3 / 4) overflow = true;
         if (overflow) {
             if (lane == 0) raise_err(a.err, EDFA_ERR_BOUNDS, E);
-            if (PASS == 0 && lane == 0) a.cnt[E] = 0;
+            if (lane == 0) a.cnt[E] = 0;
             __syncwarp();
             continue;
         }
-        if (PASS == 0) {
-            if (lane == 0) { a.cnt[E] = cnt; atomicMax(a.rowmax, cnt); }
-            __syncwarp();
-            continue;
-        }
-        int n = hs_compact_sort(tab, key, kHS, lane);
-        const int64_t sb = a.s_ptr[E];
-        for (int t = lane; t < n; t += 32) {
-            const int m = key[t];
-            a.s_col[sb + t] = m;
-            const int64_t qb = a.xptr[m], qe = a.xptr[m + 1];
-            T acc = T(0);
-            if (a.form == 0) {
-                // H~[E,m] = sum over f in C_E and Q^(m), ascending f
-                int64_t pc = a.C.rowptr[E], ec = a.C.rowptr[E + 1], pq = qb;
-                while (pc < ec && pq < qe) {
-                    int cc = a.C.col[pc], cq = a.xidx[pq];
-                    if (cc == cq) { acc = fma(a.C.val[pc], a.xval[pq], acc); ++pc; ++pq; }
-                    else if (cc < cq) ++pc;
-                    else ++pq;
-                }
-            } else {
-                // H~[E,m] = -sum_{g in Q^(m)} u_g X~[g,m]
-                for (int64_t pq = qb; pq < qe; ++pq) {
-                    int pos = bsearch_i(ul, nu, a.xidx[pq]);
-                    if (pos >= 0) acc = fma(-uv[pos], a.xval[pq], acc);
-                }
-            }
-            a.h_val[sb + t] = acc;
-        }
-        for (int64_t p = a.D.rowptr[E] + lane; p < a.D.rowptr[E + 1]; p += 32)
-            a.d_map[p] = sb + bsearch_i(key, n, a.D.col[p]);
+        if (lane == 0) { a.cnt[E] = cnt; atomicMax(a.rowmax, cnt); }
         __syncwarp();
     }
+}
+
+// ------------------------------------------------------------ numeric pass
+// hash of capacity cap (a power of two): insert / slot lookup
+__device__ __forceinline__ bool hsc_insert(int* tab, int cap, int key)
+{
+    unsigned h = ((unsigned)key * 2654435761u) & (unsigned)(cap - 1);
+    for (int probe = 0; probe < cap; ++probe) {
+        int prev = atomicCAS(&tab[h], -1, key);
+        if (prev == -1) return true;
+        if (prev == key) return false;
+        h = (h + 1) & (unsigned)(cap - 1);
+    }
+    return false;
+}
+
+__device__ __forceinline__ int hsc_slot(const int* tab, int cap, int key)
+{
+    unsigned h = ((unsigned)key * 2654435761u) & (unsigned)(cap - 1);
+    for (int probe = 0; probe < cap; ++probe) {
+        const int k = tab[h];
+        if (k == key) return (int)h;
+        if (k < 0) return -1;
+        h = (h + 1) & (unsigned)(cap - 1);
+    }
+    return -1;
+}
+
+// compact the keys of tab[0..cap) into out ascending (out holds cap entries)
+__device__ int hsc_compact_sort(const int* tab, int cap, int* out, int lane)
+{
+    int n = 0;
+    for (int base = 0; base < cap; base += 32) {
+        int v = tab[base + lane];
+        bool has = v >= 0;
+        unsigned b = __ballot_sync(0xffffffffu, has);
+        if (has) out[n + __popc(b & ((1u << lane) - 1u))] = v;
+        n += __popc(b);
+    }
+    __syncwarp();
+    int n2 = 32;
+    while (n2 < n) n2 <<= 1;
+    for (int i = n + lane; i < n2; i += 32) out[i] = INT_MAX;
+    __syncwarp();
+    warp_bitonic(out, n2, lane);
+    return n;
+}
+
+constexpr int kNumWarps = 8;  // rows (warps) per block of the numeric pass
+
+template <class T, int FORM>
+__host__ __device__ constexpr size_t num_warp_bytes(int hs)
+{
+    return ((size_t)hs * sizeof(T) + (size_t)hs * 12 + (size_t)(FORM ? (hs > kHS ? hs : kHS) : hs) * 4 +
+            (FORM ? (size_t)kUCap * (4 + sizeof(T)) : 0) + 15) & ~(size_t)15;
+}
+
+template <class T, int FORM>
+__global__ void __launch_bounds__(kNumWarps * 32, 2)
+k_schur_num(SchurArgs<T> a, const T* __restrict__ xr_val, int hs)
+{
+    extern __shared__ __align__(16) unsigned char nsm_raw[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* wb = nsm_raw + wid * num_warp_bytes<T, FORM>(hs);
+    T* acc = (T*)wb;              // [hs] accumulator by position
+    int* tab = (int*)(acc + hs);  // [hs] column hash
+    int* pos = tab + hs;          // [hs] position of the column in each slot
+    int* key = pos + hs;          // [hs] sorted columns (two-sided: [max(hs, kHS)], also the face hash)
+    const int kc = FORM ? (hs > kHS ? hs : kHS) : hs;
+    int* ul = key + kc;           // two-sided: faces g of G~_E A
+    T* uv = (T*)(ul + kUCap);     // and their values u_g
+    const int64_t nw = (int64_t)gridDim.x * kNumWarps;
+    for (int64_t E = (int64_t)blockIdx.x * kNumWarps + wid; E < a.Ne; E += nw) {
+        for (int i = lane; i < hs; i += 32) tab[i] = -1;
+        int nu = 0;
+        bool bad = false;
+        if (FORM == 1) {
+            for (int i = lane; i < kHS; i += 32) key[i] = -1;
+            __syncwarp();
+            for (int64_t p = a.gptr[E]; p < a.gptr[E + 1]; ++p) {
+                const int f = a.gidx[p];
+                for (int64_t q = a.A.rowptr[f] + lane; q < a.A.rowptr[f + 1]; q += 32) hs_insert(key, a.A.col[q]);
+            }
+            __syncwarp();
+            nu = hs_compact_sort(key, ul, kUCap, lane);
+            if (nu < 0) { bad = true; nu = 0; }
+            const int64_t qb = a.gptr[E], qe = a.gptr[E + 1];
+            for (int t = lane; t < nu; t += 32) {
+                const int g = ul[t];
+                int64_t pa = a.A.rowptr[g], ea = a.A.rowptr[g + 1], pq = qb;
+                T u = T(0);
+                while (pa < ea && pq < qe) {
+                    const int ca = a.A.col[pa], cq = a.gidx[pq];
+                    if (ca == cq) { u = fma(a.gval[pq], a.A.val[pa], u); ++pa; ++pq; }
+                    else if (ca < cq) ++pa;
+                    else ++pq;
+                }
+                uv[t] = u;
+            }
+        }
+        __syncwarp();
+        // columns: E, the row of D, every cell reached by a product term
+        if (lane == 0) hsc_insert(tab, hs, (int)E);
+        for (int64_t p = a.D.rowptr[E] + lane; p < a.D.rowptr[E + 1]; p += 32) hsc_insert(tab, hs, a.D.col[p]);
+        if (FORM == 0) {
+            for (int64_t p = a.C.rowptr[E]; p < a.C.rowptr[E + 1]; ++p) {
+                const int f = a.C.col[p];
+                for (int64_t t = a.xr_ptr[f] + lane; t < a.xr_ptr[f + 1]; t += 32) hsc_insert(tab, hs, a.xr_cell[t]);
+            }
+        } else {
+            for (int t0 = 0; t0 < nu; ++t0) {
+                const int g = ul[t0];
+                for (int64_t t = a.xr_ptr[g] + lane; t < a.xr_ptr[g + 1]; t += 32) hsc_insert(tab, hs, a.xr_cell[t]);
+            }
+        }
+        __syncwarp();
+        const int n = hsc_compact_sort(tab, hs, key, lane);
+        const int64_t sb = a.s_ptr[E];
+        if (bad || n != (int)(a.s_ptr[E + 1] - sb)) {
+            // the counting pass saw another set (or the face list overflowed)
+            if (lane == 0) raise_err(a.err, EDFA_ERR_BOUNDS, E);
+            __syncwarp();
+            continue;
+        }
+        for (int t = lane; t < n; t += 32) {
+            const int sl = hsc_slot(tab, hs, key[t]);
+            if (sl >= 0) pos[sl] = t;
+            acc[t] = T(0);
+        }
+        __syncwarp();
+        // Gustavson product, faces in ascending order
+        if (FORM == 0) {
+            for (int64_t p = a.C.rowptr[E]; p < a.C.rowptr[E + 1]; ++p) {
+                const int f = a.C.col[p];
+                const T c = a.C.val[p];
+                for (int64_t t = a.xr_ptr[f] + lane; t < a.xr_ptr[f + 1]; t += 32) {
+                    const int sl = hsc_slot(tab, hs, a.xr_cell[t]);
+                    if (sl < 0) continue;  // cannot happen: every cell was inserted above
+                    const int q = pos[sl];
+                    acc[q] = fma(c, xr_val[t], acc[q]);
+                }
+                __syncwarp();
+            }
+        } else {
+            for (int t0 = 0; t0 < nu; ++t0) {
+                const int g = ul[t0];
+                const T u = uv[t0];
+                for (int64_t t = a.xr_ptr[g] + lane; t < a.xr_ptr[g + 1]; t += 32) {
+                    const int sl = hsc_slot(tab, hs, a.xr_cell[t]);
+                    if (sl < 0) continue;
+                    const int q = pos[sl];
+                    acc[q] = fma(-u, xr_val[t], acc[q]);
+                }
+                __syncwarp();
+            }
+        }
+        for (int t = lane; t < n; t += 32) {
+            a.s_col[sb + t] = key[t];
+            a.h_val[sb + t] = acc[t];
+        }
+        for (int64_t p = a.D.rowptr[E] + lane; p < a.D.rowptr[E + 1]; p += 32) {
+            const int sl = hsc_slot(tab, hs, a.D.col[p]);
+            a.d_map[p] = sb + (sl >= 0 ? pos[sl] : 0);
+        }
+        __syncwarp();
+    }
+}
+
+template <class T, int FORM>
+static int launch_schur_num(edfa_handle_s* h, const SchurArgs<T>& a, const T* xr_val, int hs, cudaStream_t s)
+{
+    const size_t smem = num_warp_bytes<T, FORM>(hs) * kNumWarps;
+    auto fn = k_schur_num<T, FORM>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return EDFA_ERR_BOUNDS;
+    }
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kNumWarps * 32, smem);
+    if (per < 1) return EDFA_ERR_BOUNDS;
+    long long grid = (long long)per * h->nsm;
+    const long long need = (a.Ne + kNumWarps - 1) / kNumWarps;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    (edfa::count_launch(), fn<<<(unsigned)grid, kNumWarps * 32, smem, s>>>(a, xr_val, hs));
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
 template <class T>
@@ -278,10 +458,16 @@ static int schur_t(edfa_handle_s* h, const T* xval, const T* gval, T** h_val, cu
     rc = scan_i64(h, h->xr_ptr, Nf, s);
     if (rc) return rc;
     unsigned long long* cursor = nullptr;
+    T* xr_val = nullptr;  // X~ values in row-major order, for the numeric pass only
     if (cudaMallocAsync((void**)&cursor, ((size_t)Nf + 1) * sizeof(int64_t), s) != cudaSuccess) return EDFA_ERR_OOM;
+    if (cudaMallocAsync((void**)&xr_val, (size_t)(h->x_tot > 0 ? h->x_tot : 1) * sizeof(T), s) != cudaSuccess)
+        return EDFA_ERR_OOM;
     cudaMemcpyAsync(cursor, h->xr_ptr, ((size_t)Nf + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
-    if (Ne > 0) (edfa::count_launch(), k_q_fill<<<(Ne + 255) / 256, 256, 0, s>>>(Ne, h->x_ptr, h->x_idx, cursor, h->xr_cell));
-    if (Nf > 0) (edfa::count_launch(), k_row_sort2<<<(Nf + 255) / 256, 256, 0, s>>>(h->xr_ptr, h->xr_cell, Nf));
+    if (Ne > 0)
+        (edfa::count_launch(), k_q_fill_vals<T><<<(Ne + 255) / 256, 256, 0, s>>>(Ne, h->x_ptr, h->x_idx, xval, cursor,
+                                                                               h->xr_cell, xr_val));
+    if (Nf > 0)
+        (edfa::count_launch(), k_row_sort_pairs<T><<<(Nf + 255) / 256, 256, 0, s>>>(h->xr_ptr, h->xr_cell, xr_val, Nf));
     cudaFreeAsync(cursor, s);
 
     SchurArgs<T> a{};
@@ -326,8 +512,8 @@ static int schur_t(edfa_handle_s* h, const T* xval, const T* gval, T** h_val, cu
         for (int c : cands) {
             for (int rep = 0; rep < 2; ++rep) {
                 if (rep == 1) cudaEventRecord(e0, s);
-                if (c == 1) (edfa::count_launch(), k_schur<T, 0, 1><<<(unsigned)(h->nsm * 8), 32, 0, s>>>(sample));
-                else (edfa::count_launch(), k_schur<T, 0, 2><<<(unsigned)(h->nsm * 4), 64, 0, s>>>(sample));
+                if (c == 1) (edfa::count_launch(), k_schur_count<T, 1><<<(unsigned)(h->nsm * 8), 32, 0, s>>>(sample));
+                else (edfa::count_launch(), k_schur_count<T, 2><<<(unsigned)(h->nsm * 4), 64, 0, s>>>(sample));
             }
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
@@ -342,22 +528,24 @@ static int schur_t(edfa_handle_s* h, const T* xval, const T* gval, T** h_val, cu
     }
     h->stats.tuned_schur_warps = sw;
     int per = 0;
-    if (sw == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_schur<T, 0, 1>, 32, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_schur<T, 0, 2>, 64, 0);
+    if (sw == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_schur_count<T, 1>, 32, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_schur_count<T, 2>, 64, 0);
     if (per < 1) per = 1;
     long long grid = (long long)per * h->nsm;
     long long need = (Ne + sw - 1) / sw;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    if (sw == 1) (edfa::count_launch(), k_schur<T, 0, 1><<<(unsigned)grid, 32, 0, s>>>(a));
-    else (edfa::count_launch(), k_schur<T, 0, 2><<<(unsigned)grid, 64, 0, s>>>(a));
+    if (sw == 1) (edfa::count_launch(), k_schur_count<T, 1><<<(unsigned)grid, 32, 0, s>>>(a));
+    else (edfa::count_launch(), k_schur_count<T, 2><<<(unsigned)grid, 64, 0, s>>>(a));
     rc = scan_i64(h, h->s_ptr, Ne, s);
     if (rc) return rc;
     int64_t nnz = 0;
+    int rmax = 0;
     cudaMemcpyAsync(&nnz, h->s_ptr + Ne, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&rmax, rowmax, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(rowmax, s);
     rc = check_err(h, s);
-    if (rc) return rc;
+    if (rc) { cudaFreeAsync(xr_val, s); return rc; }
     h->s_nnz = nnz;
     rc = dalloc_t(h, &h->s_col, (size_t)(nnz > 0 ? nnz : 1));
     if (!rc) rc = dalloc_t(h, h_val, (size_t)(nnz > 0 ? nnz : 1));
@@ -367,9 +555,12 @@ static int schur_t(edfa_handle_s* h, const T* xval, const T* gval, T** h_val, cu
     a.s_col = h->s_col;
     a.h_val = *h_val;
     a.d_map = h->d_map;
-    if (sw == 1) (edfa::count_launch(), k_schur<T, 1, 1><<<(unsigned)grid, 32, 0, s>>>(a));
-    else (edfa::count_launch(), k_schur<T, 1, 2><<<(unsigned)grid, 64, 0, s>>>(a));
-    if (cudaGetLastError() != cudaSuccess) return EDFA_ERR_CUDA;
+    // numeric pass: hash capacity at least twice the longest row
+    int hs = 64;
+    while (hs < 2 * rmax) hs <<= 1;
+    rc = a.form == 1 ? launch_schur_num<T, 1>(h, a, xr_val, hs, s) : launch_schur_num<T, 0>(h, a, xr_val, hs, s);
+    cudaFreeAsync(xr_val, s);
+    if (rc) return rc;
     // post-filtration of H~ (Algorithm 1, Stage 1): compacts the S~ pattern
     if (h->opt.filtration == EDFA_FILT_POST_H) return postfilter_h<T>(h, *h_val, s);
     return EDFA_OK;
