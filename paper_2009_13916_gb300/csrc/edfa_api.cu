@@ -312,7 +312,8 @@ int edfa_matvec(edfa_handle h, const double* x, double* y, edfa_stream stream)
 }
 
 // Right-preconditioned flexible GMRES(m) (Saad, Alg. 9.6): Arnoldi with
-// classical Gram-Schmidt applied twice (CGS2) in FP64 on the device, the
+// classical Gram-Schmidt in FP64 on the device, repeated once when the first
+// pass removed more than half of the squared norm (DGKS criterion), the
 // (m+1) x m Hessenberg least-squares problem by Givens rotations on the host
 // (one (j+2)-value device->host read per inner iteration), x0 = 0, and the
 // true residual ||b - A x|| checked at the end of every cycle; the outer loop
@@ -329,7 +330,7 @@ int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol
         // (re)allocate workspace; previous buffers stay owned until edfa_free
         if (dalloc_t(h, &h->V, (size_t)(m + 1) * n) || dalloc_t(h, &h->Z, (size_t)m * n) ||
             dalloc_t(h, &h->w, (size_t)(n > 0 ? n : 1)) || dalloc_t(h, &h->part, (size_t)kry_part_size(n, m + 1)) ||
-            dalloc_t(h, &h->hbuf, (size_t)4 * (m + 2)))
+            dalloc_t(h, &h->hbuf, (size_t)4 * (m + 2)) || dalloc_t(h, &h->kgate, 1))
             return EDFA_ERR_OOM;
         if (h->hbuf_host) cudaFreeHost(h->hbuf_host);
         if (cudaMallocHost((void**)&h->hbuf_host, sizeof(double) * 4 * (m + 2)) != cudaSuccess) return EDFA_ERR_OOM;
@@ -373,11 +374,14 @@ int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol
             double* zj = h->Z + (int64_t)j * n;
             if ((rc = apply_prec(h, vj, zj, s))) return rc;
             if ((rc = matvec(h, zj, h->w, s))) return rc;
+            // classical Gram-Schmidt, repeated when the DGKS criterion asks for it
+            // (decided on the device: the second pass's kernels read the gate)
             const int nv = j + 1;
-            if ((rc = kry_multidot(h->V, n, nv, h->w, n, h->part, h1, nullptr, nullptr, 0, s))) return rc;
-            if ((rc = kry_update(h->V, n, nv, h1, h->w, n, h->part, nullptr, s))) return rc;
-            if ((rc = kry_multidot(h->V, n, nv, h->w, n, h->part, h2, h1, hf, 0, s))) return rc;
-            if ((rc = kry_update(h->V, n, nv, h2, h->w, n, h->part, misc, s))) return rc;
+            if ((rc = kry_multidot(h->V, n, nv, h->w, n, h->part, h1, nullptr, nullptr, 1, s))) return rc;
+            if ((rc = kry_update(h->V, n, nv, h1, h->w, n, h->part, misc, s))) return rc;
+            if ((rc = kry_dgks(misc, h1 + nv, h->kgate, s))) return rc;
+            if ((rc = kry_multidot(h->V, n, nv, h->w, n, h->part, h2, h1, hf, 0, s, h->kgate))) return rc;
+            if ((rc = kry_update(h->V, n, nv, h2, h->w, n, h->part, misc, s, h->kgate))) return rc;
             if ((rc = kry_scale_from(h->w, h->V + (int64_t)(j + 1) * n, n, misc, hf + nv, s))) return rc;
             cudaMemcpyAsync(hh, hf, sizeof(double) * (nv + 1), cudaMemcpyDeviceToHost, s);
             if ((rc = check_err(h, s))) return rc;

@@ -241,6 +241,7 @@ struct edfa_handle_s {
     int32_t kry_m = 0;
     double *V = nullptr, *Z = nullptr, *w = nullptr, *part = nullptr, *hbuf = nullptr;
     double* hbuf_host = nullptr;  // pinned
+    int* kgate = nullptr;         // device flag: second Gram-Schmidt pass needed
     // device error record and its pinned host mirror
     edfa::DevErr* err = nullptr;
     edfa::DevErr* err_host = nullptr;
@@ -318,9 +319,10 @@ int to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t s);
 
 // Krylov building blocks (k_krylov.cu)
 int kry_multidot(const double* V, int64_t ld, int nv, const double* w, int64_t n, double* part, double* out,
-                 const double* add, double* out_sum, int with_self, cudaStream_t s);
+                 const double* add, double* out_sum, int with_self, cudaStream_t s, const int* gate = nullptr);
 int kry_update(const double* V, int64_t ld, int nv, const double* hcoef, double* w, int64_t n, double* part,
-               double* nrm2_out, cudaStream_t s);
+               double* nrm2_out, cudaStream_t s, const int* gate = nullptr);
+int kry_dgks(const double* nrm2_after, const double* nrm2_before, int* gate, cudaStream_t s);
 int kry_scale_from(const double* w, double* v, int64_t n, const double* nrm2, double* out_norm, cudaStream_t s);
 int kry_scale_const(const double* w, double* v, int64_t n, double alpha, cudaStream_t s);
 int kry_combine(const double* Z, int64_t ld, int k, const double* y, double* x, int64_t n, cudaStream_t s);

@@ -1,11 +1,14 @@
 // Kernels of the outer flexible GMRES (FP64): the block-system SpMV, the
-// classical Gram-Schmidt multi-dot / update pair (applied twice per Arnoldi
-// step, CGS2) and small vector operations.  Reductions are two-level with a
+// classical Gram-Schmidt multi-dot / update pair (a second pass when the
+// DGKS criterion asks for it, decided on the device) and small vector
+// operations.  Reductions are two-level with a
 // fixed tree, so results do not depend on scheduling.
 //
-// FP64 on GB300 issues at ~2 FMA/clk/SM, so these kernels use one thread per
-// row / element and no shuffle reductions in the inner loops: every FP64
-// instruction does useful work on all 32 lanes.
+// FP64 on GB300 issues at ~2 FMA/clk/SM (a warp instruction occupies its SM
+// sub-partition for ~33 ns), so these kernels use one thread per row /
+// element, no shuffle reductions in the inner loops (every FP64 instruction
+// does useful work on all 32 lanes), and the dot kernels reduce across warps
+// once per block rather than once per vector.
 #include "internal.cuh"
 
 namespace edfa {
@@ -61,32 +64,69 @@ __device__ __forceinline__ double block_sum(double v)
 }
 
 // part[i * nchunks + chunk] = V_i[chunk] . w[chunk] for i < nv; when with_self,
-// part[nv * nchunks + chunk] = w[chunk] . w[chunk]
+// part[nv * nchunks + chunk] = w[chunk] . w[chunk].  Each thread keeps its
+// kPer elements of w in registers; per vector the warps reduce with shuffles
+// and park their partial sums in shared memory, and the cross-warp sums of
+// all vectors are formed once at the end (no block barrier per vector).
+// When gate is non-null and *gate == 0 the kernel does nothing (the second
+// Gram-Schmidt pass was found unnecessary on the device).
+constexpr int kPer = kChunk / kKT;
+constexpr int kMaxVec = 128;
+
 __global__ void __launch_bounds__(kKT)
 k_multidot(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ w, int64_t n,
-           double* part, int nchunks, int with_self)
+           double* part, int nchunks, int with_self, const int* gate)
 {
-    __shared__ double sw[kChunk];
+    __shared__ double wp[kMaxVec][kKT / 32];
+    if (gate && *gate == 0) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * kChunk;
-    for (int k = threadIdx.x; k < kChunk; k += kKT) sw[k] = (base + k < n) ? w[base + k] : 0.0;
-    __syncthreads();
-    for (int i = 0; i < nv + with_self; ++i) {
-        const double* vi = (i < nv) ? V + (int64_t)i * ld : nullptr;
+    double wr[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int64_t e = base + threadIdx.x + (int64_t)k * kKT;
+        wr[k] = e < n ? w[e] : 0.0;
+    }
+    const int nt = nv + with_self;
+    for (int i = 0; i < nt; ++i) {
         double acc = 0.0;
-        for (int k = threadIdx.x; k < kChunk; k += kKT) {
-            if (base + k < n) acc = fma(vi ? __ldg(vi + base + k) : sw[k], sw[k], acc);
+        if (i < nv) {
+            const double* vi = V + (int64_t)i * ld + base + threadIdx.x;
+#pragma unroll
+            for (int k = 0; k < kPer; ++k)
+                if (base + threadIdx.x + (int64_t)k * kKT < n) acc = fma(__ldg(vi + (int64_t)k * kKT), wr[k], acc);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) acc = fma(wr[k], wr[k], acc);
         }
-        double t = block_sum(acc);
-        if (threadIdx.x == 0) part[(int64_t)i * nchunks + blockIdx.x] = t;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) wp[i][wid] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt; i += kKT) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < kKT / 32; ++q) t += wp[i][q];
+        part[(int64_t)i * nchunks + blockIdx.x] = t;
     }
 }
 
 // out[i] = sum_c part[i * nchunks + c] in a fixed order; when add != null also
-// out_sum[i] = add[i] + out[i]
+// out_sum[i] = add[i] + out[i].  With a gate reading 0 the parts are not
+// summed: out[i] = 0 and out_sum[i] = add[i] (a skipped second pass), and a
+// norm request (add == null, out_sum == null) leaves out untouched.
 __global__ void __launch_bounds__(kKT)
-k_reduce_parts(const double* part, int nchunks, double* out, const double* add, double* out_sum)
+k_reduce_parts(const double* part, int nchunks, double* out, const double* add, double* out_sum, const int* gate)
 {
     const int i = blockIdx.x;
+    if (gate && *gate == 0) {
+        if (threadIdx.x == 0 && add) {
+            out[i] = 0.0;
+            out_sum[i] = add[i];
+        }
+        return;
+    }
     double acc = 0.0;
     for (int c = threadIdx.x; c < nchunks; c += kKT) acc += part[(int64_t)i * nchunks + c];
     double t = block_sum(acc);
@@ -94,6 +134,14 @@ k_reduce_parts(const double* part, int nchunks, double* out, const double* add, 
         out[i] = t;
         if (add) out_sum[i] = add[i] + t;
     }
+}
+
+// DGKS criterion (Daniel, Gragg, Kaufman & Stewart 1976): a second classical
+// Gram-Schmidt pass is needed when the first one removed more than half of
+// the squared norm, ||w1||^2 < ||w||^2 / 2
+__global__ void k_dgks(const double* nrm2_after, const double* nrm2_before, int* gate)
+{
+    if (threadIdx.x == 0) *gate = (*nrm2_after < 0.5 * *nrm2_before) ? 1 : 0;
 }
 
 // v = alpha * w
@@ -106,21 +154,32 @@ __global__ void k_scale_const(const double* w, double* v, int64_t n, double alph
 // w -= sum_i h_i V_i ; optional partial squared norm of the result
 __global__ void __launch_bounds__(kKT)
 k_update(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ hcoef, double* w, int64_t n,
-         double* part_norm)
+         double* part_norm, const int* gate)
 {
     __shared__ double sh[128];
+    if (gate && *gate == 0) return;
     for (int i = threadIdx.x; i < nv && i < 128; i += kKT) sh[i] = hcoef[i];
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kChunk;
-    double nacc = 0.0;
-    for (int k = threadIdx.x; k < kChunk; k += kKT) {
-        int64_t e = base + k;
-        if (e >= n) break;
-        double v = w[e];
-        for (int i = 0; i < nv; ++i) v = fma(-sh[i], __ldg(V + (int64_t)i * ld + e), v);
-        w[e] = v;
-        nacc = fma(v, v, nacc);
+    // kPer independent elements per thread: one coalesced load per element
+    // and vector, kPer independent FMA chains
+    const int64_t base = (int64_t)blockIdx.x * kChunk + threadIdx.x;
+    double v[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) v[k] = base + (int64_t)k * kKT < n ? w[base + (int64_t)k * kKT] : 0.0;
+    for (int i = 0; i < nv; ++i) {
+        const double hi = -sh[i];
+        const double* vi = V + (int64_t)i * ld + base;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k)
+            if (base + (int64_t)k * kKT < n) v[k] = fma(hi, __ldg(vi + (int64_t)k * kKT), v[k]);
     }
+    double nacc = 0.0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k)
+        if (base + (int64_t)k * kKT < n) {
+            w[base + (int64_t)k * kKT] = v[k];
+            nacc = fma(v[k], v[k], nacc);
+        }
     if (part_norm) {
         double t = block_sum(nacc);
         if (threadIdx.x == 0) part_norm[blockIdx.x] = t;
@@ -173,20 +232,27 @@ struct Kry {
 };
 
 int kry_multidot(const double* V, int64_t ld, int nv, const double* w, int64_t n, double* part, double* out,
-                 const double* add, double* out_sum, int with_self, cudaStream_t s)
+                 const double* add, double* out_sum, int with_self, cudaStream_t s, const int* gate)
 {
+    if (nv + with_self > kMaxVec) return EDFA_ERR_INVALID;
     int nc = Kry::nchunks(n);
-    (edfa::count_launch(), k_multidot<<<nc, kKT, 0, s>>>(V, ld, nv, w, n, part, nc, with_self));
-    (edfa::count_launch(), k_reduce_parts<<<nv + with_self, kKT, 0, s>>>(part, nc, out, add, out_sum));
+    (edfa::count_launch(), k_multidot<<<nc, kKT, 0, s>>>(V, ld, nv, w, n, part, nc, with_self, gate));
+    (edfa::count_launch(), k_reduce_parts<<<nv + with_self, kKT, 0, s>>>(part, nc, out, add, out_sum, gate));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
 int kry_update(const double* V, int64_t ld, int nv, const double* hcoef, double* w, int64_t n, double* part,
-               double* nrm2_out, cudaStream_t s)
+               double* nrm2_out, cudaStream_t s, const int* gate)
 {
     int nc = Kry::nchunks(n);
-    (edfa::count_launch(), k_update<<<nc, kKT, 0, s>>>(V, ld, nv, hcoef, w, n, nrm2_out ? part : nullptr));
-    if (nrm2_out) (edfa::count_launch(), k_reduce_parts<<<1, kKT, 0, s>>>(part, nc, nrm2_out, nullptr, nullptr));
+    (edfa::count_launch(), k_update<<<nc, kKT, 0, s>>>(V, ld, nv, hcoef, w, n, nrm2_out ? part : nullptr, gate));
+    if (nrm2_out) (edfa::count_launch(), k_reduce_parts<<<1, kKT, 0, s>>>(part, nc, nrm2_out, nullptr, nullptr, gate));
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
+int kry_dgks(const double* nrm2_after, const double* nrm2_before, int* gate, cudaStream_t s)
+{
+    (edfa::count_launch(), k_dgks<<<1, 32, 0, s>>>(nrm2_after, nrm2_before, gate));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
@@ -212,7 +278,7 @@ int kry_residual(const double* b, double* r, int64_t n, double* part, double* nr
 {
     int nc = Kry::nchunks(n);
     (edfa::count_launch(), k_residual<<<nc, kKT, 0, s>>>(b, r, n, part));
-    (edfa::count_launch(), k_reduce_parts<<<1, kKT, 0, s>>>(part, nc, nrm2_out, nullptr, nullptr));
+    (edfa::count_launch(), k_reduce_parts<<<1, kKT, 0, s>>>(part, nc, nrm2_out, nullptr, nullptr, nullptr));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
