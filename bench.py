@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=64, help="grid edge of the workload (default 64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the filtration, batched and adjoint variant measurements")
     return ap.parse_args()
 
 
@@ -220,6 +222,110 @@ def run_e2e(P, torch, sysd, precision, steps):
     return e0.elapsed_time(e1) / steps / 1e3, h2d, d2h
 
 
+def _elapsed(torch, fn, reps=1):
+    """Device time (s) of fn() per call, CUDA events on the current stream."""
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps, out
+
+
+def variant_filtration(P, torch, sysd, blocks, b, tau=1e-3):
+    """The paper's recommended post-filtration of H~ (tau 1e-3) on the bench workload."""
+    def step():
+        h = P.Edfa(*blocks, sysd.Nf, sysd.Ne, qmode="nbr", filtration="post_h", tau_filt=tau)
+        x, info = h.solve(b, restart=RESTART, rtol=RTOL, maxit=MAXIT)
+        return h, info
+    h, _ = step()
+    h.close()
+    t, (h, info) = _elapsed(torch, step)
+    st = h.stats()
+    h.close()
+    return {"value": t, "unit": "s", "filtration": f"post-filtration of H~, tau {tau:g}", "iterations": info.iterations,
+            "true_rel": info.true_rel, "converged": bool(info.converged), "s_nnz": int(st.s_nnz)}
+
+
+def variant_batched(P, torch, W, nsys=32):
+    """Batched form on the first nsys systems of the 256-system workload (n ~ U{16..48}):
+    one handle over the block-diagonal concatenation, lock-step FGMRES per system under a
+    CUDA graph, FP32-mixed and FP64, against the plain FP64 path one system at a time."""
+    import numpy as np
+    systems = W.config4(limit=nsys)
+    big, fo, co = W.concat(systems)
+    blocks = P.system_to_device(big)
+    bb = torch.as_tensor(big.b, device="cuda")
+    singles = [(P.system_to_device(sy), torch.as_tensor(sy.b, device="cuda"), sy) for sy in systems]
+
+    def batched(prec):
+        def run():
+            h = P.Edfa(*blocks, big.Nf, big.Ne, qmode="nbr", precision=prec)
+            x, it, tr, cyc, rc = h.solve_batched(fo, co, bb, restart=RESTART, rtol=RTOL, maxit=MAXIT)
+            h.close()
+            return it, tr, rc
+        run()
+        return _elapsed(torch, run)
+
+    def sequential():
+        its, trs = [], []
+        for blk, bi, sy in singles:
+            h = P.Edfa(*blk, sy.Nf, sy.Ne, qmode="nbr")
+            x, info = h.solve(bi, restart=RESTART, rtol=RTOL, maxit=MAXIT)
+            its.append(info.iterations)
+            trs.append(info.true_rel)
+            h.close()
+        return np.array(its), np.array(trs), 0
+    sequential()
+    t32, (it32, tr32, rc32) = batched(1)
+    t64, (it64, tr64, rc64) = batched(0)
+    tsq, (itsq, trsq, _) = _elapsed(torch, sequential)
+    return {"systems": nsys, "cells": int(big.Ne), "unknowns": int(big.n),
+            "batched_fp32_mixed_s": t32, "batched_fp64_s": t64, "plain_fp64_one_at_a_time_s": tsq,
+            "speedup_batched_fp32_vs_plain_fp64": tsq / t32, "speedup_batched_fp64_vs_plain_fp64": tsq / t64,
+            "max_true_rel": float(max(tr32.max(), tr64.max(), trsq.max())),
+            "all_converged": bool(rc32 == 0 and rc64 == 0),
+            "iterations_max": {"fp32_batched": int(it32.max()), "fp64_batched": int(it64.max()),
+                               "fp64_plain": int(itsq.max())}}
+
+
+def variant_adjoint(P, torch, W):
+    """Adjoint form on the 48^3 workload (C-row sets): forward EDFA solve, then the
+    preconditioner of the transposed system (edfa_build_adjoint), the adjoint solve and
+    dL/dlog k (edfa_grad_logk), all at rtol 1e-8, inputs resident on the device."""
+    sysd = W.config5()
+    dev = W.device_assembler(sysd)(torch.as_tensor(sysd.extra["logk"]))
+    obs = torch.as_tensor(sysd.Nf + sysd.extra["obs"], device="cuda")
+
+    def forward():
+        h = P.Edfa(*(dev[k] for k in "ABCD"), sysd.Nf, sysd.Ne, qmode="crow")
+        u, info = h.solve(dev["b"], restart=RESTART, rtol=RTOL, maxit=MAXIT)
+        return h, u, info
+
+    def backward(h, u):
+        g_u = torch.zeros_like(u)
+        g_u[obs] = 2 * u[obs]
+        adj = h.adjoint()
+        lam, info = adj.solve(g_u, restart=RESTART, rtol=RTOL, maxit=MAXIT)
+        g = P.grad_logk(dev, u, lam, sysd.Nf, sysd.Ne)
+        adj.close()
+        return g, info
+    h, u, _ = forward()
+    backward(h, u)
+    h.close()
+    tf, (h, u, fi) = _elapsed(torch, forward)
+    tb, (g, bi) = _elapsed(torch, lambda: backward(h, u))
+    h.close()
+    return {"workload": "48^3 isotropic strong-flux MHFE-FV, C-row sets, loss on 64 cells",
+            "forward_fp64_s": tf, "adjoint_build_solve_grad_s": tb, "adjoint_over_forward": tb / tf,
+            "forward_iterations": fi.iterations, "adjoint_iterations": bi.iterations,
+            "converged": bool(fi.converged and bi.converged)}
+
+
 def cpu_oracle_run(sysd):
     import oracle as O
     t = time.perf_counter()
@@ -321,6 +427,12 @@ def main():
     barrier()
     e2e_s, h2d, d2h = run_e2e(P, torch, sysd, 0, max(1, min(args.steps, 3)))
     barrier()
+    extra = {}
+    if not args.no_variants:
+        extra["fp64_post_h_filtration"] = variant_filtration(P, torch, sysd, blocks, b)
+        extra["batched_c4_subset"] = variant_batched(P, torch, W)
+        extra["adjoint_c5"] = variant_adjoint(P, torch, W)
+    barrier()
 
     t64 = max_over_ranks(statistics.mean(r64["step_ms"]) / 1e3)
     t32 = max_over_ranks(statistics.mean(r32["step_ms"]) / 1e3)
@@ -381,7 +493,7 @@ def main():
                                        "s_ilu0": st.ms_s_factor, "s_cluster_pack": st.ms_s_cluster}},
         "variants": {"fp32_mixed": {"value": t32, "unit": "s", "iterations": info32.iterations,
                                     "true_rel": info32.true_rel, "converged": bool(info32.converged),
-                                    "speedup_vs_fp64": t64 / t32 if t32 else None}},
+                                    "speedup_vs_fp64": t64 / t32 if t32 else None}, **extra},
         "systems_per_s": world / t64,
         "roofline": roofline,
         "gpu_launches": int(r64["launches"]),

@@ -657,7 +657,8 @@ k_s_cluster(const T* __restrict__ bslot, const unsigned char* __restrict__ chunk
 //
 // Row record (kDfDeps dependencies inline, older ones in an overflow array):
 //   0: int slot, int count, int64 overflow offset
-//  16: T aux (forward: right-hand side; backward: w_i), 24: T 1/U_ii
+//  16: T aux (forward: right-hand side; backward: w_i / U_ii), 24: T 1/U_ii
+//  (backward values are stored as U_ij / U_ii)
 //  32: int dep[kDfDeps] (slot * 16 + owner)
 // 160: T val[kDfDeps]
 // A padding record has slot -1 and no dependencies.
@@ -805,7 +806,10 @@ __device__ __forceinline__ void df_row(const unsigned char* __restrict__ rc, uin
     }
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o);
-    if (gl == 0) df_st(xs_s + (uint32_t)(slot * (int)sizeof(T)), bwd ? acc * dv : acc);
+    // backward rows: the record holds U_ij / U_ii and the scaled w_i / U_ii,
+    // so no product remains after the last dependency
+    (void)dv;
+    if (gl == 0) df_st(xs_s + (uint32_t)(slot * (int)sizeof(T)), acc);
 }
 
 template <class T, class TO, int LPR, int THREADS, int SLEEP>
@@ -847,7 +851,7 @@ k_s_df(unsigned char* __restrict__ rec, const int64_t* __restrict__ rmeta, int32
             // w_i into the backward records, then every slot back to the sentinel
             for (int sl = threadIdx.x; sl < cap; sl += blockDim.x) {
                 const int64_t p = bidx[(int64_t)rank * cap + sl];
-                if (p >= 0) *(T*)(rec + p * RB + 16) = xs[sl];
+                if (p >= 0) *(T*)(rec + p * RB + 16) = xs[sl] * *(const T*)(rec + p * RB + 24);
             }
             __syncthreads();
             for (int sl = threadIdx.x; sl < cap; sl += blockDim.x) xs[sl] = df_sentinel<T>();
@@ -967,7 +971,7 @@ __global__ void k_df_write(int64_t nrec, int nlt, int nlf, int32_t n, const int6
     for (int u = 0; u < cnt; ++u) {
         const int k = sorted ? ord[u] : (u < nov ? kDfDeps + u : u - nov);
         const int d = posf[col[lo + k]];
-        const T w = lu[lo + k];
+        const T w = bwd ? lu[lo + k] * dinv[i] : lu[lo + k];
         if (u < nov) {
             ovf_dep[ov + u] = d;
             ovf_val[ov + u] = w;
@@ -978,25 +982,22 @@ __global__ void k_df_write(int64_t nrec, int nlt, int nlf, int32_t n, const int6
     }
 }
 
-// forward right-hand side into the forward records: aux_i = base_i - (M v)_i
+// forward right-hand side into the forward records: aux_i = base_i - (M v)_i,
+// four consecutive lanes per row (coalesced runs of the row of M)
 template <class T, class TB>
 __global__ void k_df_rhs(int32_t n, const int64_t* __restrict__ fidx, unsigned char* __restrict__ rec,
                          const TB* __restrict__ base, const int64_t* __restrict__ mptr,
                          const int32_t* __restrict__ mcol, const T* __restrict__ mval, const T* __restrict__ mv)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T acc = T(0), a2 = T(0);
-    if (mptr) {
-        int64_t p = mptr[i];
-        const int64_t e = mptr[i + 1];
-        for (; p + 1 < e; p += 2) {
-            acc = fma(mval[p], mv[mcol[p]], acc);
-            a2 = fma(mval[p + 1], mv[mcol[p + 1]], a2);
-        }
-        if (p < e) acc = fma(mval[p], mv[mcol[p]], acc);
-    }
-    *(T*)(rec + fidx[i] * df_rb<T>() + 16) = (T)base[i] - (acc + a2);
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = t >> 2;
+    const int gl = (int)(t & 3);
+    T acc = T(0);
+    if (mptr && i < n)
+        for (int64_t p = mptr[i] + gl; p < mptr[i + 1]; p += 4) acc = fma(mval[p], mv[mcol[p]], acc);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (gl == 0 && i < n) *(T*)(rec + fidx[i] * df_rb<T>() + 16) = (T)base[i] - acc;
 }
 
 // ------------------------------------------------------------ host side
@@ -1312,7 +1313,7 @@ int s_cluster_solve(edfa_handle_s* h, const double* rp, const int64_t* mptr, con
                                (const uint16_t*)cp.sz, (const int64_t*)cp.meta, cp.szstride, cp.cap, cp.nlf, cp.nlb,
                                (const int32_t*)cp.rowof, out, h->err);
     } else {
-        (edfa::count_launch(), k_df_rhs<T, double><<<(unsigned)((f.n + 255) / 256), 256, 0, s>>>(
+        (edfa::count_launch(), k_df_rhs<T, double><<<(unsigned)((4 * (int64_t)f.n + 255) / 256), 256, 0, s>>>(
             f.n, cp.fidx, cp.rec, rp, mptr, mcol, mval, mv));
         cudaLaunchConfig_t cfg = cluster_cfg(cp.smem, kDfThreads, s, attr);
         if (pe) cudaEventRecord(pe[0], s);

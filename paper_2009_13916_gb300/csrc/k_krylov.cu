@@ -16,32 +16,46 @@ namespace edfa {
 constexpr int kKT = 256;           // threads per block
 constexpr int kChunk = kKT * 8;    // vector elements per block in the dot kernels
 
-// y = [A B; C D] x, one thread per row
+// y = [A B; C D] x, kSpLpr consecutive lanes per row: a warp load then
+// touches 32 / kSpLpr rows in kSpLpr * 8-byte runs (instead of 32 rows in
+// 8-byte pieces), each lane sums every kSpLpr-th entry and a 2-step shuffle
+// reduction closes the row
+constexpr int kSpLpr = 4;
+
 __global__ void __launch_bounds__(kKT)
 k_block_spmv(int32_t Nf, int32_t Ne, Csr<double> A, Csr<double> B, Csr<double> C, Csr<double> D,
              const double* __restrict__ x, double* __restrict__ y)
 {
-    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= (int64_t)Nf + Ne) return;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t r = t / kSpLpr;
+    const int gl = (int)(t % kSpLpr);
+    const int64_t nr = (int64_t)Nf + Ne;
     const double* xp = x + Nf;
     double acc = 0.0;
     if (r < Nf) {
-        for (int64_t p = A.rowptr[r]; p < A.rowptr[r + 1]; ++p) acc = fma(__ldg(A.val + p), x[__ldg(A.col + p)], acc);
-        for (int64_t p = B.rowptr[r]; p < B.rowptr[r + 1]; ++p) acc = fma(__ldg(B.val + p), xp[__ldg(B.col + p)], acc);
-    } else {
-        int64_t e = r - Nf;
-        for (int64_t p = C.rowptr[e]; p < C.rowptr[e + 1]; ++p) acc = fma(__ldg(C.val + p), x[__ldg(C.col + p)], acc);
-        for (int64_t p = D.rowptr[e]; p < D.rowptr[e + 1]; ++p) acc = fma(__ldg(D.val + p), xp[__ldg(D.col + p)], acc);
+        for (int64_t p = A.rowptr[r] + gl; p < A.rowptr[r + 1]; p += kSpLpr)
+            acc = fma(__ldg(A.val + p), x[__ldg(A.col + p)], acc);
+        for (int64_t p = B.rowptr[r] + gl; p < B.rowptr[r + 1]; p += kSpLpr)
+            acc = fma(__ldg(B.val + p), xp[__ldg(B.col + p)], acc);
+    } else if (r < nr) {
+        const int64_t e = r - Nf;
+        for (int64_t p = C.rowptr[e] + gl; p < C.rowptr[e + 1]; p += kSpLpr)
+            acc = fma(__ldg(C.val + p), x[__ldg(C.col + p)], acc);
+        for (int64_t p = D.rowptr[e] + gl; p < D.rowptr[e + 1]; p += kSpLpr)
+            acc = fma(__ldg(D.val + p), xp[__ldg(D.col + p)], acc);
     }
-    y[r] = acc;
+#pragma unroll
+    for (int o = kSpLpr / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (gl == 0 && r < nr) y[r] = acc;
 }
 
 int matvec(edfa_handle_s* h, const double* x, double* y, cudaStream_t s)
 {
     int64_t n = (int64_t)h->Nf + h->Ne;
     if (n == 0) return EDFA_OK;
-    (edfa::count_launch(), k_block_spmv<<<(unsigned)((n + kKT - 1) / kKT), kKT, 0, s>>>(h->Nf, h->Ne, csr_of(h->A), csr_of(h->B),
-                                                                  csr_of(h->C), csr_of(h->D), x, y));
+    const int64_t th = n * kSpLpr;
+    (edfa::count_launch(), k_block_spmv<<<(unsigned)((th + kKT - 1) / kKT), kKT, 0, s>>>(
+                               h->Nf, h->Ne, csr_of(h->A), csr_of(h->B), csr_of(h->C), csr_of(h->D), x, y));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
@@ -65,11 +79,12 @@ __device__ __forceinline__ double block_sum(double v)
 
 // part[i * nchunks + chunk] = V_i[chunk] . w[chunk] for i < nv; when with_self,
 // part[nv * nchunks + chunk] = w[chunk] . w[chunk].  Each thread keeps its
-// kPer elements of w in registers; per vector the warps reduce with shuffles
-// and park their partial sums in shared memory, and the cross-warp sums of
-// all vectors are formed once at the end (no block barrier per vector).
-// When gate is non-null and *gate == 0 the kernel does nothing (the second
-// Gram-Schmidt pass was found unnecessary on the device).
+// kPer elements of w in registers and takes four vectors at a time (4 kPer
+// independent loads in flight); a transposed butterfly reduces the four dot
+// products across the warp with 6 FP64 adds (instead of 4 x 5 for separate
+// reductions), and the cross-warp sums of all vectors are formed once at the
+// end.  When gate is non-null and *gate == 0 the kernel does nothing (the
+// second Gram-Schmidt pass was found unnecessary on the device).
 constexpr int kPer = kChunk / kKT;
 constexpr int kMaxVec = 128;
 
@@ -80,28 +95,38 @@ k_multidot(const double* __restrict__ V, int64_t ld, int nv, const double* __res
     __shared__ double wp[kMaxVec][kKT / 32];
     if (gate && *gate == 0) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t base = (int64_t)blockIdx.x * kChunk;
+    const int64_t base = (int64_t)blockIdx.x * kChunk + threadIdx.x;
     double wr[kPer];
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const int64_t e = base + threadIdx.x + (int64_t)k * kKT;
-        wr[k] = e < n ? w[e] : 0.0;
-    }
+    for (int k = 0; k < kPer; ++k) wr[k] = base + (int64_t)k * kKT < n ? w[base + (int64_t)k * kKT] : 0.0;
     const int nt = nv + with_self;
-    for (int i = 0; i < nt; ++i) {
-        double acc = 0.0;
-        if (i < nv) {
-            const double* vi = V + (int64_t)i * ld + base + threadIdx.x;
+    for (int i0 = 0; i0 < nt; i0 += 4) {
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-            for (int k = 0; k < kPer; ++k)
-                if (base + threadIdx.x + (int64_t)k * kKT < n) acc = fma(__ldg(vi + (int64_t)k * kKT), wr[k], acc);
-        } else {
+        for (int j = 0; j < 4; ++j) {
+            const int i = i0 + j;
+            if (i < nv) {
+                const double* vi = V + (int64_t)i * ld + base;
 #pragma unroll
-            for (int k = 0; k < kPer; ++k) acc = fma(wr[k], wr[k], acc);
+                for (int k = 0; k < kPer; ++k)
+                    if (base + (int64_t)k * kKT < n) a[j] = fma(__ldg(vi + (int64_t)k * kKT), wr[k], a[j]);
+            } else if (i < nt) {
+#pragma unroll
+                for (int k = 0; k < kPer; ++k) a[j] = fma(wr[k], wr[k], a[j]);
+            }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) wp[i][wid] = acc;
+        // transposed butterfly: the lower half of the warp keeps vectors 0, 1,
+        // the upper 2, 3; then lanes with bit 3 clear keep the first of the two
+        const bool up = lane >= 16;
+        const double b0 = (up ? a[2] : a[0]) + __shfl_xor_sync(0xffffffffu, up ? a[0] : a[2], 16);
+        const double b1 = (up ? a[3] : a[1]) + __shfl_xor_sync(0xffffffffu, up ? a[1] : a[3], 16);
+        const bool odd = (lane & 8) != 0;
+        double c = (odd ? b1 : b0) + __shfl_xor_sync(0xffffffffu, odd ? b0 : b1, 8);
+        c += __shfl_xor_sync(0xffffffffu, c, 4);
+        c += __shfl_xor_sync(0xffffffffu, c, 2);
+        c += __shfl_xor_sync(0xffffffffu, c, 1);
+        const int v = i0 + (up ? 2 : 0) + (odd ? 1 : 0);
+        if ((lane & 7) == 0 && v < nt) wp[v][wid] = c;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nt; i += kKT) {
@@ -151,23 +176,23 @@ __global__ void k_scale_const(const double* w, double* v, int64_t n, double alph
         v[e] = alpha * w[e];
 }
 
-// w -= sum_i h_i V_i ; optional partial squared norm of the result
+// w -= sum_i h_i V_i ; optional partial squared norm of the result.  kPer
+// independent elements per thread: one coalesced load per element and vector,
+// kPer independent FMA chains
 __global__ void __launch_bounds__(kKT)
 k_update(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ hcoef, double* w, int64_t n,
          double* part_norm, const int* gate)
 {
-    __shared__ double sh[128];
+    __shared__ double sh[kMaxVec];
     if (gate && *gate == 0) return;
-    for (int i = threadIdx.x; i < nv && i < 128; i += kKT) sh[i] = hcoef[i];
+    for (int i = threadIdx.x; i < nv && i < kMaxVec; i += kKT) sh[i] = -hcoef[i];
     __syncthreads();
-    // kPer independent elements per thread: one coalesced load per element
-    // and vector, kPer independent FMA chains
     const int64_t base = (int64_t)blockIdx.x * kChunk + threadIdx.x;
     double v[kPer];
 #pragma unroll
     for (int k = 0; k < kPer; ++k) v[k] = base + (int64_t)k * kKT < n ? w[base + (int64_t)k * kKT] : 0.0;
     for (int i = 0; i < nv; ++i) {
-        const double hi = -sh[i];
+        const double hi = sh[i];
         const double* vi = V + (int64_t)i * ld + base;
 #pragma unroll
         for (int k = 0; k < kPer; ++k)
@@ -186,12 +211,19 @@ k_update(const double* __restrict__ V, int64_t ld, int nv, const double* __restr
     }
 }
 
-// v = w / nrm  where nrm = sqrt(*nrm2) is also stored into *out_norm
+// v = w / nrm  where nrm = sqrt(*nrm2) is also stored into *out_norm; the
+// square root and the reciprocal (multi-instruction FP64 sequences) are taken
+// once per block, not once per thread
 __global__ void k_scale_from(const double* w, double* v, int64_t n, const double* nrm2, double* out_norm)
 {
-    double nr = sqrt(*nrm2);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && out_norm) *out_norm = nr;
-    double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+    __shared__ double s_inv;
+    if (threadIdx.x == 0) {
+        const double nr = sqrt(*nrm2);
+        if (blockIdx.x == 0 && out_norm) *out_norm = nr;
+        s_inv = nr > 0.0 ? 1.0 / nr : 0.0;
+    }
+    __syncthreads();
+    const double inv = s_inv;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
         v[e] = w[e] * inv;
 }
@@ -244,6 +276,7 @@ int kry_multidot(const double* V, int64_t ld, int nv, const double* w, int64_t n
 int kry_update(const double* V, int64_t ld, int nv, const double* hcoef, double* w, int64_t n, double* part,
                double* nrm2_out, cudaStream_t s, const int* gate)
 {
+    if (nv > kMaxVec) return EDFA_ERR_INVALID;
     int nc = Kry::nchunks(n);
     (edfa::count_launch(), k_update<<<nc, kKT, 0, s>>>(V, ld, nv, hcoef, w, n, nrm2_out ? part : nullptr, gate));
     if (nrm2_out) (edfa::count_launch(), k_reduce_parts<<<1, kKT, 0, s>>>(part, nc, nrm2_out, nullptr, nullptr, gate));
