@@ -244,3 +244,46 @@ def test_rng_moments_and_determinism():
     assert abs(a.mean()) < 0.01 and abs(a.std() - 1) < 0.01
     u = W.Stream(5).uniform(100000)
     assert u.min() >= 0 and u.max() < 1 and abs(u.mean() - 0.5) < 0.01
+
+
+# ------------------------------------------------------------ transient driver
+def test_transient_accumulation_term_and_dt_rule():
+    s = W.brick(4, seed=2)
+    tr = W.Transient(s, dt_mult=2.0, dp_target=0.05, dt_max=3.0)
+    np.testing.assert_allclose(tr.D_values(s.dt), s.D.val, rtol=1e-13, atol=0)
+    # an independent assembly with another time step puts Omega c / dt on the same diagonal
+    s2 = W.assemble(s.nx, s.ny, s.nz, s.K, h=s.h, dt=0.37, stor=s.stor)
+    assert np.array_equal(s2.D.col, s.D.col)
+    np.testing.assert_allclose(tr.D_values(0.37), s2.D.val, rtol=1e-13, atol=1e-300)
+    np.testing.assert_allclose(s2.f_phys, s.f_phys, rtol=1e-13, atol=0)
+    # Eq. delta_t_dyn: growth capped by dt_mult, by dp_T / dp_max and by dt_max
+    assert tr.next_dt(0.1, 0.001) == pytest.approx(0.2)
+    assert tr.next_dt(0.1, 0.5) == pytest.approx(0.01)
+    assert tr.next_dt(2.5, 0.0) == pytest.approx(3.0)
+
+
+def test_transient_reaches_the_steady_state():
+    # implicit Euler with growing steps converges to the steady solution
+    # [A B; C D - Omega c / dt I] u = f (dense solves on a small grid)
+    s = W.brick(4, seed=2)
+    tr = W.Transient(s, dt_mult=3.0, dp_target=0.5, dt_max=1e6)
+    import scipy.sparse as sp
+    Ab = sp.bmat([[s.A.to_scipy(), s.B.to_scipy()], [s.C.to_scipy(), None]]).tolil()
+    def full(dt):
+        D = W.CSR(s.D.nrows, s.D.ncols, s.D.rowptr, s.D.col, tr.D_values(dt)).to_scipy()
+        return sp.bmat([[s.A.to_scipy(), s.B.to_scipy()], [s.C.to_scipy(), D]]).toarray()
+    Dss = W.CSR(s.D.nrows, s.D.ncols, s.D.rowptr, s.D.col, tr.d_base).to_scipy()
+    full_ss = sp.bmat([[s.A.to_scipy(), s.B.to_scipy()], [s.C.to_scipy(), Dss]]).toarray()
+    p_ss = np.linalg.solve(full_ss, s.f_phys)[s.Nf:]
+    p = np.zeros(s.Ne)
+    dt = 0.1
+    errs = []
+    for _ in range(40):
+        u = np.linalg.solve(full(dt), tr.rhs(dt, p))
+        pn = u[s.Nf:]
+        dt = tr.next_dt(dt, float(np.max(pn - p)))
+        p = pn
+        errs.append(np.abs(p - p_ss).max())
+    assert errs[-1] <= 1e-8 * np.abs(p_ss).max()
+    floor = 1e-12 * np.abs(p_ss).max()  # monotone until round-off
+    assert all(b <= a * (1 + 1e-12) or b <= floor for a, b in zip(errs, errs[1:]))

@@ -507,3 +507,40 @@ def sub_vector(v, sysd_list, fo, co, i):
     """Unknowns of system i (faces then cells) out of a concatenated vector."""
     Nf = int(fo[-1])
     return np.concatenate([v[fo[i]:fo[i + 1]], v[Nf + co[i]:Nf + co[i + 1]]])
+
+
+class Transient:
+    """Implicit-Euler time stepping of the single-phase compressible MHFE-FV model on an
+    assembled system: between steps only the accumulation term of D (Omega c / dt on the
+    diagonal) and the cell right-hand side (Omega c / dt) p_n change, so a preconditioner
+    keeps its Stage 1 and redoes Stage 2 only.  The step size follows the adaptive rule of
+    Sec. 4 (Eq. delta_t_dyn): dt_{n+1} = min(dt_n min(dt_mult, dp_T / dp_max), dt_max)."""
+
+    def __init__(self, sysd: System, dt_mult=2.0, dp_target=0.05, dt_max=10.0):
+        self.s = sysd
+        self.dt_mult, self.dp_target, self.dt_max = dt_mult, dp_target, dt_max
+        self.acc = float(np.prod(sysd.h)) * sysd.stor  # Omega c, per cell (brick cells)
+        D = sysd.D
+        rows = np.repeat(np.arange(D.nrows), np.diff(D.rowptr))
+        self.diag_pos = np.nonzero(D.col == rows)[0]
+        assert len(self.diag_pos) == D.nrows
+        self.d_base = D.val.copy()
+        self.d_base[self.diag_pos] -= self.acc / sysd.dt
+
+    def D_values(self, dt: float) -> np.ndarray:
+        v = self.d_base.copy()
+        v[self.diag_pos] += self.acc / dt
+        return v
+
+    def D(self, dt: float) -> CSR:
+        D = self.s.D
+        return CSR(D.nrows, D.ncols, D.rowptr, D.col, self.D_values(dt))
+
+    def rhs(self, dt: float, p_cells: np.ndarray) -> np.ndarray:
+        b = self.s.f_phys.copy()
+        b[self.s.Nf:] += self.acc / dt * p_cells
+        return b
+
+    def next_dt(self, dt: float, dp_max: float) -> float:
+        f = self.dt_mult if dp_max <= 0 else min(self.dt_mult, self.dp_target / dp_max)
+        return min(dt * f, self.dt_max)
