@@ -12,6 +12,7 @@ Paper: Nardean, Ferronato, Abushaikha, arXiv 2009.13916.
   * approximate Schur complement: Eq. sparse_S
   * preconditioner application: Eq. EDFA_prec, Remark 1
   * outer Krylov stopping rule: Sec. 4 (||r_k||/||r_0|| <= tau, x0 = 0)
+  * outer Krylov methods: flexible GMRES(m) and Bi-CGStab (the paper's, Sec. 4)
 """
 from __future__ import annotations
 
@@ -83,6 +84,8 @@ def lib():
         L.orc_apply.restype = None
         L.orc_fgmres.argtypes = [P(_Prec), C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
                                  P(C.c_int), C.c_void_p, P(C.c_double)]
+        L.orc_bicgstab.argtypes = [P(_Prec), C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                                   P(C.c_int), C.c_void_p, P(C.c_double)]
         L.orc_prec_setup.argtypes = [P(_Prec), P(_CSR), P(_CSR), P(_CSR), P(_CSR), P(_CSR),
                                      P(_CSR), C.c_int, C.c_int, P(C.c_int32)]
         L.orc_prec_free.argtypes = [P(_Prec)]
@@ -367,6 +370,22 @@ def fgmres(prec: Prec, b, restart=50, rtol=1e-8, maxit=2000):
         raise RuntimeError(f"orc_fgmres failed ({rc})")
     return dict(x=x, iters=it.value, converged=(rc == 0), hist=hist[: it.value + 1],
                 true_rel=tr.value)
+
+
+def bicgstab(prec: Prec, b, rtol=1e-8, maxit=2000):
+    """Right-preconditioned Bi-CGStab, x0 = 0 (the paper's outer solver, Sec. 4).
+    Returns dict with x, iterations (two preconditioner applications each),
+    converged flag, residual history and true residual."""
+    b = np.ascontiguousarray(b, np.float64)
+    x = np.zeros_like(b)
+    hist = np.zeros(maxit + 1)
+    it = C.c_int(0)
+    tr = C.c_double(np.nan)
+    rc = lib().orc_bicgstab(C.byref(prec.p), _ptr(b), _ptr(x), float(rtol), int(maxit), C.byref(it),
+                            _ptr(hist), C.byref(tr))
+    if rc < 0:
+        raise RuntimeError(f"orc_bicgstab failed ({rc})")
+    return dict(x=x, iters=it.value, converged=(rc == 0), hist=hist[: it.value + 1], true_rel=tr.value)
 
 
 def adjoint_grad(sysd, u, lam, logk):

@@ -894,6 +894,84 @@ done:
 /* ---------------------------------------------- preconditioner setup */
 /* Assemble the preconditioner record: ILU(0) of Ma (stands for A~^{-1}) and
  * of S~.  Factor arrays are malloc'd and released with orc_prec_free. */
+/* Right-preconditioned Bi-CGStab (van der Vorst 1992), the outer solver of the
+ * paper's experiments (Sec. 4), x0 = 0, stopping rule ||r_k|| / ||r_0|| <= rtol
+ * with r_0 = b.  One iteration applies the preconditioner twice.  When the
+ * recursive residual meets the tolerance the true residual b - A x is formed; if
+ * it does not meet it too, or on a breakdown (rho = 0, (r^, v) = 0, omega = 0),
+ * the method restarts from the true residual.  Returns 0 converged, 1 not
+ * converged within maxit iterations. */
+ORC_EXPORT int orc_bicgstab(const orc_prec* P, const double* b, double* x, double rtol, int maxit, int* iters,
+                            double* hist, double* true_rel)
+{
+    const int64_t n = (int64_t)P->A.nrows + P->D.nrows;
+    double* r = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double* rh = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double* p = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double* v = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double* ph = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double* sv = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double* sh = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double* t = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+    if (!r || !rh || !p || !v || !ph || !sv || !sh || !t) return -1;
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    const double bnorm = sqrt(dot(b, b, n));
+    int it = 0, status = 1;
+    if (hist) hist[0] = 1.0;
+    if (true_rel) *true_rel = 0.0;
+    if (bnorm == 0.0) { *iters = 0; status = 0; goto done; }
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i];
+    for (;;) {
+        /* (re)start from the residual r */
+        for (int64_t i = 0; i < n; ++i) { rh[i] = r[i]; p[i] = 0.0; v[i] = 0.0; }
+        double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        int restart = 0;
+        while (it < maxit) {
+            const double rho = dot(rh, r, n);
+            if (rho == 0.0) { restart = 1; break; }
+            const double beta = (rho / rho_old) * (alpha / omega);
+            for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+            orc_apply(P, p, ph);
+            block_mv(P, ph, v);
+            const double rv = dot(rh, v, n);
+            if (rv == 0.0) { restart = 1; break; }
+            alpha = rho / rv;
+            for (int64_t i = 0; i < n; ++i) sv[i] = r[i] - alpha * v[i];
+            it++;
+            const double snorm = sqrt(dot(sv, sv, n));
+            if (snorm / bnorm <= rtol) {
+                for (int64_t i = 0; i < n; ++i) x[i] += alpha * ph[i];
+                for (int64_t i = 0; i < n; ++i) r[i] = sv[i];
+                if (hist) hist[it] = snorm / bnorm;
+                break;
+            }
+            orc_apply(P, sv, sh);
+            block_mv(P, sh, t);
+            const double tt = dot(t, t, n);
+            omega = tt != 0.0 ? dot(t, sv, n) / tt : 0.0;
+            for (int64_t i = 0; i < n; ++i) x[i] += alpha * ph[i] + omega * sh[i];
+            for (int64_t i = 0; i < n; ++i) r[i] = sv[i] - omega * t[i];
+            rho_old = rho;
+            const double rn = sqrt(dot(r, r, n));
+            if (hist) hist[it] = rn / bnorm;
+            if (rn / bnorm <= rtol) break;
+            if (omega == 0.0) { restart = 1; break; }
+        }
+        /* true residual */
+        block_mv(P, x, t);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+        const double tr = sqrt(dot(r, r, n)) / bnorm;
+        if (true_rel) *true_rel = tr;
+        if (tr <= rtol) { status = 0; break; }
+        if (it >= maxit) break;
+        (void)restart;
+    }
+    *iters = it;
+done:
+    free(r); free(rh); free(p); free(v); free(ph); free(sv); free(sh); free(t);
+    return status;
+}
+
 ORC_EXPORT int orc_prec_setup(orc_prec* P, const orc_csr* A, const orc_csr* B, const orc_csr* C,
                               const orc_csr* D, const orc_csr* Ma, const orc_csr* S, int variant,
                               int identity, int32_t* bad)
