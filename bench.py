@@ -383,6 +383,23 @@ def variant_transient(P, torch, W, sysd, blocks, nsteps=5):
             "iterations_rebuilding": rb_its}
 
 
+def variant_bicgstab(P, torch, sysd, blocks, b):
+    """The paper's outer solver (Sec. 4) with the same preconditioner on the bench workload:
+    edfa_build + edfa_solve_bicgstab to rtol 1e-8 (one iteration = two applications)."""
+    def step():
+        h = P.Edfa(*blocks, sysd.Nf, sysd.Ne, qmode="nbr")
+        x, info = h.solve_bicgstab(b, rtol=RTOL, maxit=MAXIT)
+        return h, info
+    h, _ = step()
+    h.close()
+    t, (h, info) = _elapsed(torch, step)
+    solve_ms = h.stats().ms_solve
+    h.close()
+    return {"value": t, "unit": "s", "solver": "Bi-CGStab", "iterations": info.iterations,
+            "preconditioner_applications": 2 * info.iterations, "solve_ms": solve_ms,
+            "true_rel": info.true_rel, "converged": bool(info.converged), "restarts": info.restarts}
+
+
 def cpu_oracle_run(sysd):
     import oracle as O
     t = time.perf_counter()
@@ -487,6 +504,7 @@ def main():
     extra = {}
     if not args.no_variants:
         extra["fp64_post_h_filtration"] = variant_filtration(P, torch, sysd, blocks, b)
+        extra["fp64_bicgstab"] = variant_bicgstab(P, torch, sysd, blocks, b)
         extra["batched_c4_subset"] = variant_batched(P, torch, W)
         extra["adjoint_c5"] = variant_adjoint(P, torch, W)
         extra["transient_stage2_reuse"] = variant_transient(P, torch, W, sysd, blocks)

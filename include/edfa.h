@@ -202,6 +202,20 @@ EDFA_API int edfa_matvec(edfa_handle h, const double* x, double* y, edfa_stream 
 EDFA_API int edfa_solve(edfa_handle h, const double* b, double* x, int32_t restart, double rtol,
                int32_t maxit, edfa_solve_info* info, edfa_stream stream);
 
+/* Right-preconditioned Bi-CGStab (van der Vorst 1992), the outer solver of the
+ * paper's experiments (Sec. 4), with the preconditioner of the handle; x0 = 0,
+ * stopping rule ||r_k||_2 / ||r_0||_2 <= rtol (r_0 = b), the true residual
+ * ||b - A x|| confirmed at the end (the method restarts from the true residual
+ * when the recursive one met rtol but the true one did not, or on a breakdown).
+ * One iteration applies the preconditioner twice.  x receives the solution
+ * (device, N_f + N_e); info->iterations counts iterations, info->restarts the
+ * restarts.  Returns EDFA_ERR_NOT_CONVERGED if maxit iterations do not reach
+ * rtol (x then holds the last iterate).  Synchronises `stream` four times per
+ * iteration to read the scalars.  Workspace (8 (N_f + N_e) doubles) is kept by
+ * the handle. */
+EDFA_API int edfa_solve_bicgstab(edfa_handle h, const double* b, double* x, double rtol, int32_t maxit,
+                                 edfa_solve_info* info, edfa_stream stream);
+
 /* Batched solve of many independent systems held block-diagonally in one
  * handle (the caller concatenates the systems: system i owns faces
  * [face_off[i], face_off[i+1]) and cells [cell_off[i], cell_off[i+1]), with no

@@ -76,7 +76,7 @@ _lib = None
 EXPORTS = ("edfa_default_options", "edfa_build", "edfa_setup", "edfa_apply", "edfa_matvec",
            "edfa_solve", "edfa_history", "edfa_get_view", "edfa_get_stats", "edfa_set_profiling",
            "edfa_launch_count", "edfa_qsets_noalloc", "edfa_build_adjoint", "edfa_grad_logk",
-           "edfa_solve_batched",
+           "edfa_solve_batched", "edfa_solve_bicgstab",
            "edfa_free", "edfa_strerror",
            "edfa_last_error_detail")
 
@@ -121,6 +121,8 @@ def lib(build_if_missing: bool = True):
         L.edfa_solve_batched.argtypes = [vp, C.c_int32, vp, vp, vp, vp, C.c_int32, C.c_double, C.c_int32,
                                          vp, vp, vp, vp]
         L.edfa_solve_batched.restype = C.c_int
+        L.edfa_solve_bicgstab.argtypes = [vp, vp, vp, C.c_double, C.c_int32, P(SolveInfo), vp]
+        L.edfa_solve_bicgstab.restype = C.c_int
         L.edfa_launch_count.argtypes = []
         L.edfa_launch_count.restype = C.c_int64
         L.edfa_strerror.argtypes = [C.c_int]
@@ -286,6 +288,18 @@ class Edfa:
         if x is None:
             x = torch.empty_like(b)
         info = edfa_solve(self.h, b.data_ptr(), x.data_ptr(), restart, rtol, maxit, _stream(stream))
+        return x, info
+
+    def solve_bicgstab(self, b, x=None, rtol=1e-8, maxit=2000, stream=None):
+        """Bi-CGStab with this preconditioner (edfa_solve_bicgstab)."""
+        import torch
+        if x is None:
+            x = torch.empty_like(b)
+        info = SolveInfo()
+        rc = lib().edfa_solve_bicgstab(self.h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), float(rtol),
+                                       int(maxit), C.byref(info), C.c_void_p(_stream(stream)))
+        if rc not in (EDFA_OK, EDFA_ERR_NOT_CONVERGED):
+            raise EdfaError(rc, "edfa_solve_bicgstab", lib().edfa_last_error_detail())
         return x, info
 
     def history(self):

@@ -437,6 +437,126 @@ int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol
     return status;
 }
 
+// Right-preconditioned Bi-CGStab (van der Vorst 1992), the outer solver of the
+// paper's experiments (Sec. 4): x0 = 0, stop at ||r_k|| / ||r_0|| <= rtol with
+// the true residual confirmed; restart from the true residual when it is not met
+// or on a breakdown.  Scalars are read back to the host four times per iteration.
+int edfa_solve_bicgstab(edfa_handle h, const double* b, double* x, double rtol, int32_t maxit,
+                        edfa_solve_info* info, edfa_stream stream)
+{
+    g_detail = -1;
+    if (!h || !(rtol >= 0.0) || maxit < 0) return EDFA_ERR_INVALID;
+    const int64_t n = (int64_t)h->Nf + h->Ne;
+    if (n > 0 && (!b || !x)) return EDFA_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!h->bcg) {
+        if (dalloc_t(h, &h->bcg, (size_t)8 * (n > 0 ? n : 1)) ||
+            dalloc_t(h, &h->bcg_part, (size_t)kry_part_size(n > 0 ? n : 1, 2)) || dalloc_t(h, &h->bcg_sc, 8))
+            return EDFA_ERR_OOM;
+        if (!h->hbuf_host) {
+            if (cudaMallocHost((void**)&h->hbuf_host, sizeof(double) * 16) != cudaSuccess) return EDFA_ERR_OOM;
+        }
+    }
+    double* r = h->bcg;
+    double* rh = r + n;
+    double* p = rh + n;
+    double* v = p + n;
+    double* ph = v + n;
+    double* sv = ph + n;
+    double* sh = sv + n;
+    double* t = sh + n;
+    double* sc = h->bcg_sc;  // device scalars
+    double* hh = h->hbuf_host;
+    edfa_solve_info loc{};
+    h->hist.assign(1, 1.0);
+    cudaEventRecord(h->ev[0], s);
+    int rc;
+    auto fetch = [&](int k) -> int {
+        cudaMemcpyAsync(hh, sc, sizeof(double) * k, cudaMemcpyDeviceToHost, s);
+        return check_err(h, s);
+    };
+    cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), s);
+    if ((rc = kry_multidot(nullptr, n, 0, b, n, h->bcg_part, sc, nullptr, nullptr, 1, s))) return rc;
+    if ((rc = fetch(1))) return rc;
+    const double bnorm = std::sqrt(hh[0]);
+    if (bnorm == 0.0 || n == 0) {
+        loc.converged = 1;
+        if (info) *info = loc;
+        return EDFA_OK;
+    }
+    cudaMemcpyAsync(r, b, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    int it = 0, status = EDFA_ERR_NOT_CONVERGED;
+    for (;;) {
+        cudaMemcpyAsync(rh, r, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaMemsetAsync(p, 0, (size_t)n * sizeof(double), s);
+        cudaMemsetAsync(v, 0, (size_t)n * sizeof(double), s);
+        double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        // rho = (r^, r)
+        if ((rc = kry_multidot(rh, n, 1, r, n, h->bcg_part, sc, nullptr, nullptr, 0, s))) return rc;
+        if ((rc = fetch(1))) return rc;
+        double rho = hh[0];
+        while (it < maxit) {
+            if (rho == 0.0) break;  // restart
+            const double beta = (rho / rho_old) * (alpha / omega);
+            if ((rc = kry_bcg_p(r, p, v, beta, omega, n, s))) return rc;
+            if ((rc = apply_prec(h, p, ph, s))) return rc;
+            if ((rc = matvec(h, ph, v, s))) return rc;
+            if ((rc = kry_multidot(rh, n, 1, v, n, h->bcg_part, sc, nullptr, nullptr, 0, s))) return rc;
+            if ((rc = fetch(1))) return rc;
+            const double rv = hh[0];
+            if (rv == 0.0) break;  // restart
+            alpha = rho / rv;
+            if ((rc = kry_bcg_s(r, v, alpha, sv, n, h->bcg_part, sc, s))) return rc;
+            if ((rc = fetch(1))) return rc;
+            ++it;
+            const double snorm = std::sqrt(hh[0]);
+            if (snorm / bnorm <= rtol) {
+                if ((rc = kry_axpy(x, ph, alpha, n, s))) return rc;
+                cudaMemcpyAsync(r, sv, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+                h->hist.push_back(snorm / bnorm);
+                loc.est_rel = snorm / bnorm;
+                break;
+            }
+            if ((rc = apply_prec(h, sv, sh, s))) return rc;
+            if ((rc = matvec(h, sh, t, s))) return rc;
+            // (s, t) and (t, t)
+            if ((rc = kry_multidot(sv, n, 1, t, n, h->bcg_part, sc, nullptr, nullptr, 1, s))) return rc;
+            if ((rc = fetch(2))) return rc;
+            omega = hh[1] != 0.0 ? hh[0] / hh[1] : 0.0;
+            if ((rc = kry_bcg_xr(x, ph, sh, sv, t, alpha, omega, r, n, s))) return rc;
+            rho_old = rho;
+            // next rho = (r^, r) and ||r||^2
+            if ((rc = kry_multidot(rh, n, 1, r, n, h->bcg_part, sc, nullptr, nullptr, 1, s))) return rc;
+            if ((rc = fetch(2))) return rc;
+            rho = hh[0];
+            const double rn = std::sqrt(hh[1]);
+            h->hist.push_back(rn / bnorm);
+            loc.est_rel = rn / bnorm;
+            if (rn / bnorm <= rtol) break;
+            if (omega == 0.0) break;  // restart
+        }
+        // true residual
+        if ((rc = matvec(h, x, t, s))) return rc;
+        if ((rc = kry_residual(b, t, n, h->bcg_part, sc, s))) return rc;
+        if ((rc = fetch(1))) return rc;
+        loc.true_rel = std::sqrt(hh[0]) / bnorm;
+        cudaMemcpyAsync(r, t, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        if (loc.true_rel <= rtol) { status = EDFA_OK; break; }
+        if (it >= maxit) break;
+        loc.restarts++;
+    }
+    cudaEventRecord(h->ev[1], s);
+    cudaEventSynchronize(h->ev[1]);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+    h->stats.ms_solve = ms;
+    prof_collect(h);
+    loc.iterations = it;
+    loc.converged = status == EDFA_OK;
+    if (info) *info = loc;
+    return status;
+}
+
 int32_t edfa_history(edfa_handle h, double* hist, int32_t cap)
 {
     if (!h || !hist || cap <= 0) return 0;

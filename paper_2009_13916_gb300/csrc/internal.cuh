@@ -242,6 +242,10 @@ struct edfa_handle_s {
     double *V = nullptr, *Z = nullptr, *w = nullptr, *part = nullptr, *hbuf = nullptr;
     double* hbuf_host = nullptr;  // pinned
     int* kgate = nullptr;         // device flag: second Gram-Schmidt pass needed
+    // Bi-CGStab workspace: r, r^, p, v, p^, s, s^, t (n each), partial sums, scalars
+    double* bcg = nullptr;
+    double* bcg_part = nullptr;
+    double* bcg_sc = nullptr;
     // device error record and its pinned host mirror
     edfa::DevErr* err = nullptr;
     edfa::DevErr* err_host = nullptr;
@@ -328,5 +332,12 @@ int kry_scale_const(const double* w, double* v, int64_t n, double alpha, cudaStr
 int kry_combine(const double* Z, int64_t ld, int k, const double* y, double* x, int64_t n, cudaStream_t s);
 int kry_residual(const double* b, double* r, int64_t n, double* part, double* nrm2_out, cudaStream_t s);
 int64_t kry_part_size(int64_t n, int nvmax);
+// Bi-CGStab vector updates (k_krylov.cu)
+int kry_bcg_p(const double* r, double* p, const double* v, double beta, double omega, int64_t n, cudaStream_t s);
+int kry_bcg_s(const double* r, const double* v, double alpha, double* sv, int64_t n, double* part, double* nrm2_out,
+              cudaStream_t s);
+int kry_bcg_xr(double* x, const double* ph, const double* sh, const double* sv, const double* t, double alpha,
+               double omega, double* r, int64_t n, cudaStream_t s);
+int kry_axpy(double* x, const double* y, double a, int64_t n, cudaStream_t s);
 
 }  // namespace edfa

@@ -258,6 +258,51 @@ __global__ void __launch_bounds__(kKT) k_residual(const double* b, double* r, in
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
+// ------------------------------------------------------------ Bi-CGStab vectors
+// p = r + beta (p - omega v)
+__global__ void k_bcg_p(const double* __restrict__ r, double* __restrict__ p, const double* __restrict__ v,
+                        double beta, double omega, int64_t n)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        p[e] = r[e] + beta * (p[e] - omega * v[e]);
+}
+
+// s = r - alpha v, partial ||s||^2 per chunk
+__global__ void __launch_bounds__(kKT)
+k_bcg_s(const double* __restrict__ r, const double* __restrict__ v, double alpha, double* __restrict__ sv, int64_t n,
+        double* part)
+{
+    const int64_t base = (int64_t)blockIdx.x * kChunk;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < kChunk; k += kKT) {
+        const int64_t e = base + k;
+        if (e >= n) break;
+        const double x = r[e] - alpha * v[e];
+        sv[e] = x;
+        acc = fma(x, x, acc);
+    }
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// x += alpha ph + omega sh ; r = s - omega t
+__global__ void k_bcg_xr(double* __restrict__ x, const double* __restrict__ ph, const double* __restrict__ sh,
+                         const double* __restrict__ sv, const double* __restrict__ t, double alpha, double omega,
+                         double* __restrict__ r, int64_t n)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        x[e] += alpha * ph[e] + omega * sh[e];
+        r[e] = sv[e] - omega * t[e];
+    }
+}
+
+// x += a y
+__global__ void k_axpy(double* __restrict__ x, const double* __restrict__ y, double a, int64_t n)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        x[e] += a * y[e];
+}
+
 // ------------------------------------------------------------ launchers
 struct Kry {
     static int nchunks(int64_t n) { return (int)((n + kChunk - 1) / kChunk); }
@@ -325,5 +370,45 @@ int kry_scale_const(const double* w, double* v, int64_t n, double alpha, cudaStr
 }
 
 int64_t kry_part_size(int64_t n, int nvmax) { return (int64_t)Kry::nchunks(n) * (nvmax + 2); }
+
+}  // namespace edfa
+
+namespace edfa {
+
+static unsigned flat_blocks(int64_t n)
+{
+    int64_t g = (n + kKT - 1) / kKT;
+    if (g > 4096) g = 4096;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+int kry_bcg_p(const double* r, double* p, const double* v, double beta, double omega, int64_t n, cudaStream_t s)
+{
+    (edfa::count_launch(), k_bcg_p<<<flat_blocks(n), kKT, 0, s>>>(r, p, v, beta, omega, n));
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
+int kry_bcg_s(const double* r, const double* v, double alpha, double* sv, int64_t n, double* part, double* nrm2_out,
+              cudaStream_t s)
+{
+    const int nc = Kry::nchunks(n);
+    (edfa::count_launch(), k_bcg_s<<<nc, kKT, 0, s>>>(r, v, alpha, sv, n, part));
+    (edfa::count_launch(), k_reduce_parts<<<1, kKT, 0, s>>>(part, nc, nrm2_out, nullptr, nullptr, nullptr));
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
+int kry_bcg_xr(double* x, const double* ph, const double* sh, const double* sv, const double* t, double alpha,
+               double omega, double* r, int64_t n, cudaStream_t s)
+{
+    (edfa::count_launch(), k_bcg_xr<<<flat_blocks(n), kKT, 0, s>>>(x, ph, sh, sv, t, alpha, omega, r, n));
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
+int kry_axpy(double* x, const double* y, double a, int64_t n, cudaStream_t s)
+{
+    (edfa::count_launch(), k_axpy<<<flat_blocks(n), kKT, 0, s>>>(x, y, a, n));
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
 
 }  // namespace edfa
