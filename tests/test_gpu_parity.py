@@ -37,6 +37,7 @@ CASES = {
     "ragged_full_7x5x3": lambda: full_tensor((7, 5, 3)),
     "c3_small": lambda: W.config3(24, 20, 6),
     "c5_small": lambda: W.config5(10),
+    "dome8": lambda: W.dome(8),
 }
 
 
@@ -66,14 +67,15 @@ def compare_setup(sysd, mode, form=0):
 
 @pytest.mark.parametrize("case,mode", [("c1", "own"), ("brick6_paper", "own"), ("brick6_paper", "nbr"),
                                        ("brick6_paper", "crow"), ("ragged_full_7x5x3", "nbr"),
-                                       ("c3_small", "thresh"), ("c5_small", "crow")])
+                                       ("c3_small", "thresh"), ("c5_small", "crow"), ("dome8", "nbr"),
+                                       ("dome8", "crow")])
 def test_setup_parity(case, mode):
     sysd = CASES[case]()
     h, _ = compare_setup(sysd, mode)
     h.close()
 
 
-@pytest.mark.parametrize("case,mode", [("brick6_paper", "nbr"), ("ragged_full_7x5x3", "crow")])
+@pytest.mark.parametrize("case,mode", [("brick6_paper", "nbr"), ("ragged_full_7x5x3", "crow"), ("dome8", "nbr")])
 def test_two_sided_schur_parity(case, mode):
     sysd = CASES[case]()
     h, _ = compare_setup(sysd, mode, form=1)
@@ -81,7 +83,8 @@ def test_two_sided_schur_parity(case, mode):
 
 
 @pytest.mark.parametrize("case,mode,variant", [("brick6_paper", "nbr", 0), ("ragged_full_7x5x3", "nbr", 0),
-                                               ("c3_small", "thresh", 0), ("brick6_paper", "own", 1)])
+                                               ("c3_small", "thresh", 0), ("brick6_paper", "own", 1),
+                                               ("dome8", "nbr", 0), ("dome8", "crow", 0)])
 def test_apply_and_fgmres_parity(case, mode, variant):
     torch = _torch()
     sysd = CASES[case]()

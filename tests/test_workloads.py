@@ -287,3 +287,61 @@ def test_transient_reaches_the_steady_state():
     assert errs[-1] <= 1e-8 * np.abs(p_ss).max()
     floor = 1e-12 * np.abs(p_ss).max()  # monotone until round-off
     assert all(b <= a * (1 + 1e-12) or b <= floor for a, b in zip(errs, errs[1:]))
+
+
+# ------------------------------------------------------------ general hexahedra
+def test_hex_elemental_matrix_reduces_to_brick():
+    # Piola-mapped RT0 with Gauss quadrature on a brick-shaped hexahedron equals the
+    # closed-form brick matrix (Eq. B_ij), for full-tensor K and unequal edges
+    s = W.Stream(17)
+    for _ in range(4):
+        K = W.rotated_K(np.exp(s.normal(1)), 0.1, s.normal(4).reshape(1, 4))[0]
+        h = tuple(0.1 + s.uniform(3))
+        X = np.array([[i * h[0], j * h[1], k * h[2]] for k in (0, 1) for j in (0, 1) for i in (0, 1)])
+        X += s.normal(3)  # translation does not matter
+        Bh, vol = W.elem_B_hex(K, X)
+        Bb = W.elem_B(K, h)
+        np.testing.assert_allclose(Bh, Bb, rtol=1e-12, atol=1e-12 * np.abs(Bb).max())
+        assert vol == pytest.approx(np.prod(h), rel=1e-13)
+
+
+def test_sheared_parallelepiped_linear_pressure_patch():
+    # RT0 on parallelepipeds (an affine shear mixing y and z only, so that the flux
+    # of p = 1 - x is tangential to every lateral face) reproduces linear pressure
+    n = (5, 3, 4)
+    X = W.grid_nodes(*n)
+    X = np.stack([X[:, 0], X[:, 1] + 0.3 * X[:, 2], X[:, 2] + 0.2 * X[:, 1]], axis=1)
+    K = np.tile([2.5, 0.3, 0.07, 0, 0, 0], (int(np.prod(n)), 1))
+    sysd = W.assemble(*n, K, stor=0.0, xyz=X)
+    import scipy.sparse.linalg as spl
+    u = spl.spsolve(sysd.full_scipy().tocsc(), sysd.f_phys)
+    xf, xc = _centres(sysd)
+    np.testing.assert_allclose(u[: sysd.Nf], 1 - xf, atol=1e-11)
+    np.testing.assert_allclose(u[sysd.Nf:], 1 - xc, atol=1e-11)
+
+
+def test_dome_grid_blocks():
+    # general (non-parallelepiped) cells: SPD elemental matrices, positive volumes,
+    # face block symmetric negative definite, constant pressure balanced with the
+    # accumulation term of each cell's own volume
+    sysd = W.dome(5)
+    A = sysd.A.dense()
+    assert np.array_equal(A, A.T)
+    np.linalg.cholesky(-A)
+    X = W.dome_nodes(5, 5, 5)
+    vols = []
+    for e in range(sysd.Ne):
+        ix, iy, iz = e % 5, (e // 5) % 5, e // 25
+        nodes = [ix + di + 6 * (iy + dj + 6 * (iz + dk)) for dk in (0, 1) for dj in (0, 1) for di in (0, 1)]
+        Bh, vol = W.elem_B_hex(sysd.K[e], X[nodes])
+        np.linalg.cholesky(Bh)
+        np.testing.assert_allclose(np.linalg.inv(Bh), sysd.W[e], rtol=1e-9, atol=1e-9 * np.abs(sysd.W[e]).max())
+        vols.append(vol)
+    vols = np.array(vols)
+    assert (vols > 0).all()
+    # volume under the dome: 1 - 0.25 * (1 - E[r^2]) with E[r^2] = 1/3 (trilinear cells: O(h^2))
+    assert abs(vols.sum() - (1 - 0.25 * 2 / 3)) < 0.02
+    s2 = W.assemble(5, 5, 5, sysd.K, xyz=X, p_left=1.0, p_right=1.0, dt=0.1, stor=0.01)
+    res = s2.full_scipy() @ np.ones(s2.n) - s2.f_phys
+    np.testing.assert_allclose(res[: s2.Nf], 0.0, atol=1e-11)
+    np.testing.assert_allclose(res[s2.Nf:], vols * 0.01 / 0.1, rtol=1e-9)

@@ -50,7 +50,8 @@ class _Problem(C.Structure):
                 ("dt", C.c_double), ("stor", C.c_double),
                 ("fv_kind", C.c_int32), ("dirichlet", C.c_int32),
                 ("p_left", C.c_double), ("p_right", C.c_double),
-                ("K", C.POINTER(C.c_double)), ("lam_face", C.POINTER(C.c_double))]
+                ("K", C.POINTER(C.c_double)), ("lam_face", C.POINTER(C.c_double)),
+                ("xyz", C.POINTER(C.c_double))]
 
 
 class _System(C.Structure):
@@ -182,14 +183,19 @@ def _csr_from(c: _CSR) -> CSR:
 
 
 def assemble(nx, ny, nz, K, *, h=None, dt=0.1, stor=1e-2, fv_kind=0, lam_face=None,
-             dirichlet=True, p_left=1.0, p_right=0.0, name="custom", b=None) -> System:
-    """Assemble the MHFE-FV block system for a brick grid with per-cell K[Ne,6]."""
+             dirichlet=True, p_left=1.0, p_right=0.0, name="custom", b=None, xyz=None) -> System:
+    """Assemble the MHFE-FV block system for a structured grid with per-cell K[Ne,6]:
+    brick cells h[0] x h[1] x h[2], or general hexahedra with node coordinates
+    xyz[(nx+1)(ny+1)(nz+1), 3] (node (i,j,k) lexicographic, i fastest)."""
     if h is None:
         h = (1.0 / nx, 1.0 / nx, 1.0 / nx)
     Ne = nx * ny * nz
     K = np.ascontiguousarray(K, dtype=np.float64).reshape(Ne, 6)
     P = _Problem(nx, ny, nz, h[0], h[1], h[2], dt, stor, fv_kind, 1 if dirichlet else 0,
-                 p_left, p_right, _dp(K), None)
+                 p_left, p_right, _dp(K), None, None)
+    if xyz is not None:
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape((nx + 1) * (ny + 1) * (nz + 1), 3)
+        P.xyz = _dp(xyz)
     if fv_kind == 1:
         lam_face = np.ascontiguousarray(lam_face, dtype=np.float64)
         P.lam_face = _dp(lam_face)
@@ -228,6 +234,50 @@ def elem_B(K6, h):
     out = np.empty(36)
     lib().wl_elem_B(_dp(K6), h[0], h[1], h[2], _dp(out))
     return out.reshape(6, 6)
+
+
+def elem_B_hex(K6, X):
+    """B^E of a general hexahedron with nodes X[8,3] (Piola-mapped RT0, Gauss
+    quadrature) and its volume."""
+    K6 = np.ascontiguousarray(K6, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(24)
+    out = np.empty(36)
+    vol = C.c_double(0.0)
+    if lib().wl_elem_B_hex(_dp(K6), _dp(X), _dp(out), C.byref(vol)) != 0:
+        raise ValueError("inverted cell")
+    return out.reshape(6, 6), vol.value
+
+
+def grid_nodes(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0):
+    """Node coordinates of a uniform brick grid, [(nx+1)(ny+1)(nz+1), 3]."""
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    return np.stack([i.ravel() * lx / nx, j.ravel() * ly / ny, k.ravel() * lz / nz], axis=1).astype(np.float64)
+
+
+def dome_nodes(nx, ny, nz, height=0.25, wobble=0.02):
+    """A dome-shaped layered grid on the unit cube: every layer is lifted by a smooth
+    bump height * (1 - z) * (1 - r^2) (r the distance from the centre of the x-y square,
+    scaled to 1 at the corners), and the lateral node positions get a smooth wobble, so
+    that cells are general (non-parallelepiped) hexahedra.  The x = 0 and x = 1 planes
+    stay planar (the prescribed-pressure boundaries)."""
+    X = grid_nodes(nx, ny, nz)
+    x, y, z = X[:, 0].copy(), X[:, 1].copy(), X[:, 2].copy()
+    r2 = ((x - 0.5) ** 2 + (y - 0.5) ** 2) / 0.5
+    zn = z + height * (1.0 - z) * (1.0 - r2)  # the layers lifted into a dome
+    yn = y + wobble * np.sin(2 * np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z + 0.3)
+    return np.stack([x, yn, zn], axis=1)
+
+
+def dome(n: int = 12, seed: int = 7, sigma: float = 1.0, name=None) -> System:
+    """Dome-shaped structured grid of general hexahedra (a stand-in for the paper's
+    dome grids, whose data are not available): n x n x n cells, isotropic lognormal K,
+    prescribed pressures on x = 0 and x = 1, own + neighbour-face sets."""
+    s = Stream(7000 + seed)
+    Ne = n ** 3
+    K = iso_K(np.exp(sigma * s.normal(Ne)))
+    sysd = assemble(n, n, n, K, xyz=dome_nodes(n, n, n), name=name or f"dome {n}^3")
+    sysd.extra.update(qmode="nbr")
+    return sysd
 
 
 def iso_K(k: np.ndarray) -> np.ndarray:

@@ -71,6 +71,9 @@ typedef struct {
     double p_left, p_right;
     const double* K;     /* [Ne*6] Kxx Kyy Kzz Kxy Kxz Kyz per cell */
     const double* lam_face; /* [Nf] face mobility (fv_kind 1 only) */
+    const double* xyz;   /* optional [(nx+1)(ny+1)(nz+1)*3] node coordinates (node (i,j,k)
+                            lexicographic, i fastest): general hexahedra with trilinear
+                            maps; NULL = brick cells hx x hy x hz */
 } wl_problem;
 
 typedef struct {
@@ -178,6 +181,82 @@ static int spd_inverse6(const double Bm[36], double Wm[36])
             Wm[j * 6 + i] = s;
         }
     return 0;
+}
+
+/* General hexahedron (Sec. 2.2, Eq. B_ij with the Piola transformation of the
+ * RT0 fields): cell = image of the unit cube by the trilinear map F through its
+ * 8 nodes X[8][3] (node a = (a&1, (a>>1)&1, (a>>2)&1) in reference coordinates).
+ * Reference fields with unit outward flux through their face (local order
+ * x-, x+, y-, y+, z-, z+): w_{x-} = (x^-1, 0, 0), w_{x+} = (x^, 0, 0), and
+ * cyclic; physical fields w = DF w^ / J (flux preserving), so
+ *     B_ij = int_cube (DF w^_i)^T K^{-1} (DF w^_j) / J  dx^,
+ * by 3 x 3 x 3 Gauss-Legendre quadrature; vol = int_cube J dx^. */
+static void hex_jac(const double X[24], double u, double v, double w, double DF[9])
+{
+    /* DF[r*3+c] = d x_r / d xhat_c */
+    memset(DF, 0, 9 * sizeof(double));
+    for (int a = 0; a < 8; ++a) {
+        const int ia = a & 1, ja = (a >> 1) & 1, ka = (a >> 2) & 1;
+        const double fu = ia ? u : 1.0 - u, fv = ja ? v : 1.0 - v, fw = ka ? w : 1.0 - w;
+        const double du = ia ? 1.0 : -1.0, dv = ja ? 1.0 : -1.0, dw = ka ? 1.0 : -1.0;
+        const double g[3] = {du * fv * fw, fu * dv * fw, fu * fv * dw};
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) DF[r * 3 + c] += X[3 * a + r] * g[c];
+    }
+}
+
+static int elem_B_hex(const double K6[6], const double X[24], double Bm[36], double* vol)
+{
+    const double kxx = K6[0], kyy = K6[1], kzz = K6[2], kxy = K6[3], kxz = K6[4], kyz = K6[5];
+    const double c00 = kyy * kzz - kyz * kyz, c01 = -(kxy * kzz - kyz * kxz), c02 = kxy * kyz - kyy * kxz;
+    const double c11 = kxx * kzz - kxz * kxz, c12 = -(kxx * kyz - kxy * kxz), c22 = kxx * kyy - kxy * kxy;
+    const double det = kxx * c00 + kxy * c01 + kxz * c02;
+    const double M[9] = {c00 / det, c01 / det, c02 / det, c01 / det, c11 / det, c12 / det,
+                         c02 / det, c12 / det, c22 / det};
+    /* 3-point Gauss-Legendre on [0,1] */
+    const double gx[3] = {0.5 - 0.5 * sqrt(0.6), 0.5, 0.5 + 0.5 * sqrt(0.6)};
+    const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+    memset(Bm, 0, 36 * sizeof(double));
+    double V = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int c = 0; c < 3; ++c) {
+                const double u = gx[a], v = gx[b], w = gx[c], wt = gw[a] * gw[b] * gw[c];
+                double DF[9];
+                hex_jac(X, u, v, w, DF);
+                const double J = DF[0] * (DF[4] * DF[8] - DF[5] * DF[7]) - DF[1] * (DF[3] * DF[8] - DF[5] * DF[6]) +
+                                 DF[2] * (DF[3] * DF[7] - DF[4] * DF[6]);
+                if (!(J > 0.0)) return -1;
+                V += wt * J;
+                /* DF w^_l for the six fields: column a of DF times the scalar */
+                const double sc[6] = {u - 1.0, u, v - 1.0, v, w - 1.0, w};
+                double Y[6][3];
+                for (int l = 0; l < 6; ++l)
+                    for (int r = 0; r < 3; ++r) Y[l][r] = DF[r * 3 + l / 2] * sc[l];
+                for (int i = 0; i < 6; ++i) {
+                    double MY[3];
+                    for (int r = 0; r < 3; ++r) MY[r] = M[r * 3] * Y[i][0] + M[r * 3 + 1] * Y[i][1] + M[r * 3 + 2] * Y[i][2];
+                    for (int j = 0; j < 6; ++j)
+                        Bm[i * 6 + j] += wt / J * (MY[0] * Y[j][0] + MY[1] * Y[j][1] + MY[2] * Y[j][2]);
+                }
+            }
+    *vol = V;
+    return 0;
+}
+
+WL_EXPORT int wl_elem_B_hex(const double K6[6], const double X[24], double Bm[36], double* vol)
+{
+    return elem_B_hex(K6, X, Bm, vol);
+}
+
+/* the 8 nodes of cell (ix, iy, iz) of a structured hexahedral grid */
+static void cell_nodes(const wl_problem* P, int ix, int iy, int iz, double X[24])
+{
+    for (int a = 0; a < 8; ++a) {
+        const int i = ix + (a & 1), j = iy + ((a >> 1) & 1), k = iz + ((a >> 2) & 1);
+        const int64_t nd = i + (int64_t)(P->nx + 1) * (j + (int64_t)(P->ny + 1) * k);
+        for (int r = 0; r < 3; ++r) X[3 * a + r] = P->xyz[3 * nd + r];
+    }
 }
 
 WL_EXPORT int wl_elem_W(const double K6[6], double hx, double hy, double hz, double Wm[36])
@@ -360,6 +439,8 @@ WL_EXPORT int wl_assemble(const wl_problem* P, wl_system* S)
         return -2;
     }
     for (int64_t i = 0; i < 2 * (int64_t)Nf; ++i) S->face_cells[i] = -1;
+    double* vol = (double*)malloc((size_t)Ne * sizeof(double));  /* cell volumes Omega_E */
+    if (!vol) { wl_free_system(S); return -2; }
 
     for (int iz = 0; iz < nz; ++iz)
         for (int iy = 0; iy < ny; ++iy)
@@ -377,9 +458,22 @@ WL_EXPORT int wl_assemble(const wl_problem* P, wl_system* S)
                     int side = (l & 1) ? 0 : 1;
                     S->face_cells[2 * (int64_t)cf[l] + side] = e;
                 }
-                if (wl_elem_W(P->K + 6 * (int64_t)e, P->hx, P->hy, P->hz, S->W + 36 * (int64_t)e)) {
-                    wl_free_system(S);
-                    return -3;
+                if (P->xyz) {
+                    double X[24], Bm[36];
+                    cell_nodes(P, ix, iy, iz, X);
+                    if (elem_B_hex(P->K + 6 * (int64_t)e, X, Bm, vol + e) ||
+                        spd_inverse6(Bm, S->W + 36 * (int64_t)e)) {
+                        free(vol);
+                        wl_free_system(S);
+                        return -3;
+                    }
+                } else {
+                    vol[e] = P->hx * P->hy * P->hz;
+                    if (wl_elem_W(P->K + 6 * (int64_t)e, P->hx, P->hy, P->hz, S->W + 36 * (int64_t)e)) {
+                        free(vol);
+                        wl_free_system(S);
+                        return -3;
+                    }
                 }
             }
     if (P->dirichlet)
@@ -412,8 +506,8 @@ WL_EXPORT int wl_assemble(const wl_problem* P, wl_system* S)
             err |= trip_push(&tB, i, e, L);
         }
     /* cell rows */
-    const double acc = P->hx * P->hy * P->hz * P->stor / P->dt;
     for (int32_t e = 0; e < Ne && !err; ++e) {
+        const double acc = vol[e] * P->stor / P->dt;
         const int32_t* cf = S->cell_faces + (int64_t)e * 6;
         const double* W = S->W + 36 * (int64_t)e;
         double Lrow[6];
@@ -461,6 +555,7 @@ WL_EXPORT int wl_assemble(const wl_problem* P, wl_system* S)
             /* no-flow face: q_i = 0 */
         }
     }
+    free(vol);
     if (err) { trip_free(&tA); trip_free(&tB); trip_free(&tC); trip_free(&tD); wl_free_system(S); return -2; }
     err |= trip_to_csr(&tA, Nf, Nf, &S->A);
     err |= trip_to_csr(&tB, Nf, Ne, &S->B);
