@@ -141,6 +141,7 @@ struct Factor {
     float* dinv32 = nullptr;
     SweepPlan fwd, bwd;
     ChainPlan chf, chb;  // chain decomposition of the sweeps (k_chain.cu), used when ok
+    int fac_R = 0;  // longest row (picks the shared-memory layout of the numeric factorisation)
 };
 
 // Packed per-CTA level chunks of both S~ sweeps for the single-cluster solve

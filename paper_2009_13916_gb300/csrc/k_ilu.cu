@@ -301,6 +301,13 @@ __global__ void k_find_diag(int32_t n, const int64_t* rowptr, const int32_t* col
     diag[i] = d;
 }
 
+// longest row of a pattern (picks the layout of the numeric factorisation)
+__global__ void k_row_maxlen(int32_t n, const int64_t* __restrict__ rowptr, int* out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(out, (int)(rowptr[i + 1] - rowptr[i]));
+}
+
 int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
                 cudaStream_t s)
 {
@@ -315,6 +322,18 @@ int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64
     if (rc) return rc;
     rc = make_plan(h, f.bwd, n, rowptr, col, 0, 32, s);
     if (rc) return rc;
+    {
+        // longest row: picks the shared-memory layout of the numeric factorisation
+        int* d = nullptr;
+        if (cudaMallocAsync((void**)&d, sizeof(int), s) != cudaSuccess) return EDFA_ERR_OOM;
+        cudaMemsetAsync(d, 0, sizeof(int), s);
+        if (n > 0) (edfa::count_launch(), k_row_maxlen<<<(n + 255) / 256, 256, 0, s>>>(n, rowptr, d));
+        int r = 0;
+        cudaMemcpyAsync(&r, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaFreeAsync(d, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return EDFA_ERR_CUDA;
+        f.fac_R = r;
+    }
     const bool f32 = h->opt.precision == 1;
     if (f32) {
         rc = dalloc_t(h, &f.lu32, (size_t)(nnz > 0 ? nnz : 1));
@@ -340,41 +359,51 @@ int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64
 // The critical path through the level DAG is one row latency per level, so
 // every step above is a single round trip.  Rows whose U data exceed the
 // shared buffers read the U parts from global memory in step 4 instead.
-constexpr int kFRow = 256;    // row entries held in shared memory
-constexpr int kFU = 1280;     // U-part entries of all dependencies (incl. 16-byte alignment padding)
-constexpr int kFHash = 512;   // column -> position hash slots
+// Two shared-memory layouts per warp: rows of up to 256 entries with up to
+// 1280 gathered U entries and a 512-slot hash (S~), and a narrow one for
+// factors whose rows have at most 32 entries (the face block: <= 11), ~5 KB
+// instead of ~30 KB per warp, so that many more rows are in flight.
+template <int R_, int U_, int HB_>
+struct FacLayout {
+    static constexpr int R = R_, U = U_, HB = HB_, H = 1 << HB_;
+};
+using FacWide = FacLayout<256, 1280, 9>;
+using FacNarrow = FacLayout<32, 256, 7>;
 
-template <class T>
+template <class T, class L>
 struct alignas(16) FacSmem {
-    T rv[kFRow];       // the row being factored
-    T dk[kFRow];       // 1 / u_kk of every dependency
-    T uv[kFU];         // U values of the dependencies
-    int uc[kFU];       // U columns of the dependencies
-    long long ub[kFRow];  // first U entry of every dependency
-    int rc[kFRow];     // row columns
-    int oc[kFRow + 1]; // dependency u's columns start at uc[oc[u] + sc[u]]
-    int ov[kFRow + 1]; // ... and its values at uv[ov[u] + sv[u]]
-    int sc[kFRow];
-    int sv[kFRow];
-    int ul[kFRow];     // U length of every dependency
-    int hk[kFHash];    // hash keys (column, -1 empty)
-    int hp[kFHash];    // hash values (position in the row)
+    T rv[L::R];        // the row being factored
+    T dk[L::R];        // 1 / u_kk of every dependency
+    T uv[L::U];        // U values of the dependencies
+    int uc[L::U];      // U columns of the dependencies
+    long long ub[L::R];  // first U entry of every dependency
+    int rc[L::R];      // row columns
+    int oc[L::R + 1];  // dependency u's columns start at uc[oc[u] + sc[u]]
+    int ov[L::R + 1];  // ... and its values at uv[ov[u] + sv[u]]
+    int sc[L::R];
+    int sv[L::R];
+    int ul[L::R];      // U length of every dependency
+    int hk[L::H];      // hash keys (column, -1 empty)
+    int hp[L::H];      // hash values (position in the row)
 };
 
-__device__ __forceinline__ int fac_hslot(int j) { return (int)(((unsigned)j * 2654435769u) >> 23); }  // 512 slots
+template <class L>
+__device__ __forceinline__ int fac_hslot(int j) { return (int)(((unsigned)j * 2654435769u) >> (32 - L::HB)); }
 
-template <class T>
-__device__ __forceinline__ int fac_lookup(const FacSmem<T>& S, int j)
+template <class T, class L>
+__device__ __forceinline__ int fac_lookup(const FacSmem<T, L>& S, int j)
 {
-    int sl = fac_hslot(j);
-    for (int it = 0; it < kFHash; ++it) {
+    int sl = fac_hslot<L>(j);
+    for (int it = 0; it < L::H; ++it) {
         const int k = S.hk[sl];
         if (k == j) return S.hp[sl];
         if (k < 0) return -1;
-        sl = (sl + 1) & (kFHash - 1);
+        sl = (sl + 1) & (L::H - 1);
     }
     return -1;
 }
+
+
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
 {
@@ -402,7 +431,7 @@ __device__ __forceinline__ void gather_blocks(V* dst, const V* src, long long fi
     }
 }
 
-template <class T>
+template <class T, class L>
 __global__ void __launch_bounds__(kFacWarps * 32)
 k_ilu0(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
        const int64_t* __restrict__ diag, const T* __restrict__ vals, T* lu, T* dinv, const int32_t* perm,
@@ -410,7 +439,7 @@ k_ilu0(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr, const int32_t
 {
     extern __shared__ __align__(16) unsigned char fsm_raw[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    FacSmem<T>& S = reinterpret_cast<FacSmem<T>*>(fsm_raw)[wid];
+    FacSmem<T, L>& S = reinterpret_cast<FacSmem<T, L>*>(fsm_raw)[wid];
     constexpr int VPB = 16 / (int)sizeof(T);
     for (;;) {
         long long t = claim(ticket, 1);
@@ -420,21 +449,21 @@ k_ilu0(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr, const int32_t
         const int64_t b = rowptr[i], e = rowptr[i + 1];
         const int len = (int)(e - b);
         const int dpos = (int)(diag[i] - b);
-        if (len > kFRow) {
+        if (len > L::R) {
             if (lane == 0) { raise_err(err, EDFA_ERR_BOUNDS, i); st_release(flags + i, epoch); }
             continue;
         }
         // 1. the row and its column hash
-        for (int k = lane; k < kFHash; k += 32) S.hk[k] = -1;
+        for (int k = lane; k < L::H; k += 32) S.hk[k] = -1;
         __syncwarp();
         for (int u = lane; u < len; u += 32) {
             const int j = col[b + u];
             S.rv[u] = vals[b + u];
             S.rc[u] = j;
-            int sl = fac_hslot(j);
-            for (int it = 0; it < kFHash; ++it) {
+            int sl = fac_hslot<L>(j);
+            for (int it = 0; it < L::H; ++it) {
                 if (atomicCAS(&S.hk[sl], -1, j) == -1) { S.hp[sl] = u; break; }
-                sl = (sl + 1) & (kFHash - 1);
+                sl = (sl + 1) & (L::H - 1);
             }
         }
         __syncwarp();
@@ -485,7 +514,7 @@ k_ilu0(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr, const int32_t
         if (lane == 0) { S.oc[dpos] = totc; S.ov[dpos] = totv; }
         __syncwarp();
         // 3. gather every dependency's U part in one burst
-        const bool in_smem = totc <= kFU && totv <= kFU;
+        const bool in_smem = totc <= L::U && totv <= L::U;
         if (in_smem) {
             // one lane per dependency issues all of its copies
             for (int u = lane; u < dpos; u += 32) {
@@ -548,20 +577,35 @@ int factor_numeric(edfa_handle_s* h, Factor& f, const double* vals64, const floa
     // 16-byte copies need 16-byte aligned column and value arrays
     const bool f32 = h->opt.precision == 1;
     const int async_ok = ((uintptr_t)f.col % 16 == 0) && ((uintptr_t)(f32 ? (void*)f.lu32 : (void*)f.lu64) % 16 == 0);
+    // resident warps: about two and a half dependency levels of rows in flight
+    // (a wide DAG such as the face block fills the SMs; more rows only add
+    // polling traffic on a narrow one such as S~)
+    const double per_level = f.fwd.nlevels > 0 ? (double)f.n / f.fwd.nlevels : (double)f.n;
+    int wps = (int)(2.5 * per_level / h->nsm);
+    if (wps < 6) wps = 6;
+    if (wps > 32) wps = 32;
+    auto launch = [&](auto tag, auto lay) -> void {
+        using TT = decltype(tag);
+        using LL = decltype(lay);
+        auto fn = k_ilu0<TT, LL>;
+        const size_t smem = sizeof(FacSmem<TT, LL>) * kFacWarps;
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int grid = resident_grid(h, (const void*)fn, kFacWarps * 32, smem, wps);
+        const TT* vals;
+        TT *lu, *dinv;
+        if constexpr (sizeof(TT) == 8) { vals = (const TT*)vals64; lu = (TT*)f.lu64; dinv = (TT*)f.dinv64; }
+        else { vals = (const TT*)vals32; lu = (TT*)f.lu32; dinv = (TT*)f.dinv32; }
+        (edfa::count_launch(), fn<<<grid, kFacWarps * 32, smem, s>>>(f.n, f.nnz, f.rowptr, f.col, f.diag, vals, lu, dinv,
+                                                                     f.fwd.perm, f.fwd.nslots, h->flags, h->epoch,
+                                                                     h->ticket, async_ok, h->err));
+    };
+    const bool narrow = f.fac_R <= FacNarrow::R;
     if (f32) {
-        size_t smem = sizeof(FacSmem<float>) * kFacWarps;
-        cudaFuncSetAttribute(k_ilu0<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int grid = resident_grid(h, (const void*)k_ilu0<float>, kFacWarps * 32, smem, 32);
-        (edfa::count_launch(), k_ilu0<float><<<grid, kFacWarps * 32, smem, s>>>(f.n, f.nnz, f.rowptr, f.col, f.diag, vals32,
-                                                          f.lu32, f.dinv32, f.fwd.perm, f.fwd.nslots, h->flags,
-                                                          h->epoch, h->ticket, async_ok, h->err));
+        if (narrow) launch(float(0), FacNarrow{});
+        else launch(float(0), FacWide{});
     } else {
-        size_t smem = sizeof(FacSmem<double>) * kFacWarps;
-        cudaFuncSetAttribute(k_ilu0<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int grid = resident_grid(h, (const void*)k_ilu0<double>, kFacWarps * 32, smem, 32);
-        (edfa::count_launch(), k_ilu0<double><<<grid, kFacWarps * 32, smem, s>>>(f.n, f.nnz, f.rowptr, f.col, f.diag, vals64,
-                                                           f.lu64, f.dinv64, f.fwd.perm, f.fwd.nslots, h->flags,
-                                                           h->epoch, h->ticket, async_ok, h->err));
+        if (narrow) launch(double(0), FacNarrow{});
+        else launch(double(0), FacWide{});
     }
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }

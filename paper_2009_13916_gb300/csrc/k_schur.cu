@@ -17,6 +17,9 @@
 // deterministic.  X~ is read through a row-major copy (cells and values of
 // every face row) made once per build.
 #include <climits>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -499,9 +502,19 @@ static int schur_t(edfa_handle_s* h, const T* xval, const T* gval, T** h_val, cu
     a.cnt = h->s_ptr;
     a.rowmax = rowmax;
     // autotuned tile: warps (rows) per block of the Schur kernel, timed on a
-    // prefix sample of the rows with the counting pass
+    // prefix sample of the rows with the counting pass (once per process for a
+    // given precision, form and longest X~ set)
     int sw = 2;
-    if (Ne >= 32768) {
+    static std::mutex tune_mu;
+    static std::vector<std::pair<long long, int>> tuned;
+    const long long tkey = ((long long)sizeof(T) << 40) | ((long long)a.form << 32) | (long long)h->qmax;
+    bool have = false;
+    {
+        std::lock_guard<std::mutex> lock(tune_mu);
+        for (auto& kv : tuned)
+            if (kv.first == tkey) { sw = kv.second; have = true; }
+    }
+    if (Ne >= 32768 && !have) {
         SchurArgs<T> sample = a;
         sample.Ne = 8192;
         cudaEvent_t e0, e1;
@@ -525,6 +538,8 @@ static int schur_t(edfa_handle_s* h, const T* xval, const T* gval, T** h_val, cu
         cudaEventDestroy(e1);
         cudaMemsetAsync(rowmax, 0, sizeof(int), s);
         cudaMemsetAsync(h->s_ptr, 0, ((size_t)Ne + 1) * sizeof(int64_t), s);
+        std::lock_guard<std::mutex> lock(tune_mu);
+        tuned.push_back({tkey, sw});
     }
     h->stats.tuned_schur_warps = sw;
     int per = 0;
