@@ -351,23 +351,30 @@ int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64
 // j > k present in row k.  One warp per row, rows taken in level order.
 // Per row the warp
 //   1. stages the row in shared memory with a column -> position hash,
-//   2. waits for every row it depends on (lanes poll in parallel, no sleep),
-//   3. gathers the U parts of all those rows into shared memory with one burst
-//      of 16-byte cp.async.cg copies (L2, never a stale L1 line),
-//   4. eliminates: a sequential loop over k whose inner updates are one
-//      lane per U entry with an O(1) hash lookup of the target position.
-// The critical path through the level DAG is one row latency per level, so
-// every step above is a single round trip.  Rows whose U data exceed the
+//   2. before any wait, gathers the U columns of every row it depends on (the
+//      pattern is fixed) with one burst of 16-byte cp.async.cg copies (L2,
+//      never a stale L1 line) and maps them to positions in row i,
+//   3. polls its dependencies (lanes in parallel, no sleep) and gathers 1/u_kk
+//      and the U values of each one as soon as it has finished,
+//   4. eliminates every finished dependency that has no unfinished one before
+//      it in column order: a sequential loop over k whose inner updates are
+//      one lane per U entry; then back to 3.
+// The operations and their order are those of the IKJ loop; only the waits
+// move.  The critical path through the level DAG is one row latency per
+// level, and after the last dependency finishes only one poll, one gather
+// and the elimination of the last few k remain.  Rows whose U data exceed the
 // shared buffers read the U parts from global memory in step 4 instead.
-// Two shared-memory layouts per warp: rows of up to 256 entries with up to
-// 1280 gathered U entries and a 512-slot hash (S~), and a narrow one for
-// factors whose rows have at most 32 entries (the face block: <= 11), ~5 KB
-// instead of ~30 KB per warp, so that many more rows are in flight.
+// Three shared-memory layouts per warp, picked by the longest row: up to 256
+// entries with up to 1280 gathered U entries and a 512-slot hash (~35 KB per
+// warp); up to 64 entries (S~ of the face-neighbour sets: <= 63), ~20 KB; and
+// up to 32 entries (the face block: <= 11), ~5 KB; the smaller the layout, the
+// more rows are in flight.
 template <int R_, int U_, int HB_>
 struct FacLayout {
     static constexpr int R = R_, U = U_, HB = HB_, H = 1 << HB_;
 };
 using FacWide = FacLayout<256, 1280, 9>;
+using FacMedium = FacLayout<64, 1280, 7>;
 using FacNarrow = FacLayout<32, 256, 7>;
 
 template <class T, class L>
@@ -383,6 +390,7 @@ struct alignas(16) FacSmem {
     int sc[L::R];
     int sv[L::R];
     int ul[L::R];      // U length of every dependency
+    int rd[L::R];      // dependency state: 0 pending, 1 finished, 2 U values gathered
     int hk[L::H];      // hash keys (column, -1 empty)
     int hp[L::H];      // hash values (position in the row)
 };
@@ -432,7 +440,7 @@ __device__ __forceinline__ void gather_blocks(V* dst, const V* src, long long fi
 }
 
 template <class T, class L>
-__global__ void __launch_bounds__(kFacWarps * 32)
+__global__ void __launch_bounds__(kFacWarps * 32, 16)
 k_ilu0(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
        const int64_t* __restrict__ diag, const T* __restrict__ vals, T* lu, T* dinv, const int32_t* perm,
        int64_t nslots, int* flags, int epoch, unsigned long long* ticket, int async_ok, DevErr* err)
@@ -467,22 +475,10 @@ k_ilu0(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr, const int32_t
             }
         }
         __syncwarp();
-        // 2. wait for the dependencies (bounded; no sleep: one row latency per
-        // level).  Relaxed polls, then one acquire fence: acquire loads in a
-        // spin loop would keep invalidating the L1 of every warp on the SM.
-        {
-            bool done = false;
-            for (unsigned it = 0; it < (kSpinLimit << 2); ++it) {
-                bool ok = true;
-                for (int u = lane; u < dpos; u += 32) ok &= ld_relaxed_i32(flags + S.rc[u]) == epoch;
-                if (__all_sync(0xffffffffu, ok)) { done = true; break; }
-                if ((it & 255u) == 255u && err_set(err)) break;
-            }
-            if (!done && lane == 0) raise_err(err, EDFA_ERR_TIMEOUT, i);
-            asm volatile("fence.acq_rel.gpu;" ::: "memory");
-            __syncwarp();
-        }
-        // dependency metadata: U ranges, their aligned blocks, 1/u_kk
+        // 2. what does not change while the rows above are factored: the U
+        // ranges of the dependencies, their aligned blocks, their U columns
+        // (gathered in one burst) and the target position of every U entry in
+        // row i, all before any wait
         int totc = 0, totv = 0;
         for (int base0 = 0; base0 < dpos; base0 += 32) {
             const int u = base0 + lane;
@@ -491,9 +487,9 @@ k_ilu0(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr, const int32_t
                 const int k = S.rc[u];
                 const long long ubk = diag[k] + 1;
                 const int ulen = (int)(rowptr[k + 1] - ubk);
-                S.dk[u] = ld_cg(dinv + k);
                 S.ub[u] = ubk;
                 S.ul[u] = ulen;
+                S.rd[u] = 0;
                 const int sc = (int)(ubk & 3), sv = (int)(ubk % VPB);
                 S.sc[u] = sc;
                 S.sv[u] = sv;
@@ -513,43 +509,79 @@ k_ilu0(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr, const int32_t
         }
         if (lane == 0) { S.oc[dpos] = totc; S.ov[dpos] = totv; }
         __syncwarp();
-        // 3. gather every dependency's U part in one burst
         const bool in_smem = totc <= L::U && totv <= L::U;
         if (in_smem) {
-            // one lane per dependency issues all of its copies
-            for (int u = lane; u < dpos; u += 32) {
-                const long long ubk = S.ub[u];
-                gather_blocks(S.uc + S.oc[u], col, ubk - S.sc[u], (S.oc[u + 1] - S.oc[u]) / 4, nnz, async_ok != 0);
-                gather_blocks(S.uv + S.ov[u], (const T*)lu, ubk - S.sv[u], (S.ov[u + 1] - S.ov[u]) / VPB, nnz,
-                              async_ok != 0);
-            }
+            for (int u = lane; u < dpos; u += 32)
+                gather_blocks(S.uc + S.oc[u], col, S.ub[u] - S.sc[u], (S.oc[u + 1] - S.oc[u]) / 4, nnz, async_ok != 0);
             asm volatile("cp.async.wait_all;" ::: "memory");
             __syncwarp();
-            // target position in row i of every gathered U entry (padding
-            // entries get a position too, never used), off the sequential path
+            // padding entries get a position too, never used
             for (int q = lane; q < totc; q += 32) S.uc[q] = fac_lookup(S, S.uc[q]);
         }
         __syncwarp();
-        // 4. eliminate
-        for (int tt = 0; tt < dpos; ++tt) {
-            const T lik = S.rv[tt] * S.dk[tt];
-            const int n_u = S.ul[tt];
-            __syncwarp();
-            if (lane == 0) S.rv[tt] = lik;
-            if (in_smem) {
-                const int c0 = S.oc[tt] + S.sc[tt], v0 = S.ov[tt] + S.sv[tt];
-                for (int q = lane; q < n_u; q += 32) {
-                    const int pos = S.uc[c0 + q];
-                    if (pos >= 0) S.rv[pos] -= lik * S.uv[v0 + q];
+        // 3. progressive elimination: poll the pending dependencies (relaxed,
+        // then one acquire fence per round: acquire loads in a spin loop would
+        // keep invalidating the L1 of every warp on the SM), gather 1/u_kk and
+        // the U values of those that finished, and eliminate the longest
+        // finished prefix in ascending column order, the order of the IKJ loop.
+        // Bounded: no sleep between polls (one row latency per level).
+        int done = 0;
+        unsigned spins = 0;
+        while (done < dpos) {
+            bool fresh = false;
+            for (int u = done + lane; u < dpos; u += 32)
+                if (S.rd[u] == 0 && ld_relaxed_i32(flags + S.rc[u]) == epoch) {
+                    S.rd[u] = 1;
+                    fresh = true;
                 }
-            } else {
-                const long long ubk = S.ub[tt];
-                for (int q = lane; q < n_u; q += 32) {
-                    const int pos = fac_lookup(S, __ldcg(col + ubk + q));
-                    if (pos >= 0) S.rv[pos] -= lik * ld_cg(lu + ubk + q);
+            if (!__any_sync(0xffffffffu, fresh)) {
+                ++spins;  // warp-uniform
+                if (__any_sync(0xffffffffu, spins >= (kSpinLimit << 2) || ((spins & 255u) == 255u && err_set(err)))) {
+                    if (lane == 0 && spins >= (kSpinLimit << 2)) raise_err(err, EDFA_ERR_TIMEOUT, i);
+                    break;
                 }
+                continue;
             }
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
             __syncwarp();
+            for (int u = done + lane; u < dpos; u += 32) {
+                if (S.rd[u] != 1) continue;
+                // the copies first, so that the load of 1/u_kk overlaps them
+                if (in_smem)
+                    gather_blocks(S.uv + S.ov[u], (const T*)lu, S.ub[u] - S.sv[u], (S.ov[u + 1] - S.ov[u]) / VPB, nnz,
+                                  async_ok != 0);
+                S.dk[u] = ld_cg(dinv + S.rc[u]);
+                S.rd[u] = 2;
+            }
+            if (in_smem) asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncwarp();
+            // 4. eliminate the finished prefix: l_ik on lane 0 (no other lane
+            // touches a_ik in this step), the updates a_ij -= l_ik u_kj one
+            // lane per U entry
+            for (; done < dpos && S.rd[done] == 2; ++done) {
+                const int tt = done;
+                T lik = T(0);
+                if (lane == 0) {
+                    lik = S.rv[tt] * S.dk[tt];
+                    S.rv[tt] = lik;
+                }
+                lik = __shfl_sync(0xffffffffu, lik, 0);
+                const int n_u = S.ul[tt];
+                if (in_smem) {
+                    const int c0 = S.oc[tt] + S.sc[tt], v0 = S.ov[tt] + S.sv[tt];
+                    for (int q = lane; q < n_u; q += 32) {
+                        const int pos = S.uc[c0 + q];
+                        if (pos >= 0) S.rv[pos] -= lik * S.uv[v0 + q];
+                    }
+                } else {
+                    const long long ubk = S.ub[tt];
+                    for (int q = lane; q < n_u; q += 32) {
+                        const int pos = fac_lookup(S, __ldcg(col + ubk + q));
+                        if (pos >= 0) S.rv[pos] -= lik * ld_cg(lu + ubk + q);
+                    }
+                }
+                __syncwarp();
+            }
         }
         const T piv = S.rv[dpos];
         for (int u = lane; u < len; u += 32) lu[b + u] = S.rv[u];
@@ -577,11 +609,13 @@ int factor_numeric(edfa_handle_s* h, Factor& f, const double* vals64, const floa
     // 16-byte copies need 16-byte aligned column and value arrays
     const bool f32 = h->opt.precision == 1;
     const int async_ok = ((uintptr_t)f.col % 16 == 0) && ((uintptr_t)(f32 ? (void*)f.lu32 : (void*)f.lu64) % 16 == 0);
-    // resident warps: about two and a half dependency levels of rows in flight
-    // (a wide DAG such as the face block fills the SMs; more rows only add
-    // polling traffic on a narrow one such as S~)
+    // resident warps: about six dependency levels of rows in flight, so that
+    // the preparation of a row (step 2) is done before its dependencies are;
+    // a wide DAG such as the face block fills the SMs, a narrow one such as
+    // S~ is capped by the shared memory per warp (64^3, FP64: 6 levels 9.0 ms,
+    // 4 levels 9.5 ms, 2.5 levels 12.2 ms)
     const double per_level = f.fwd.nlevels > 0 ? (double)f.n / f.fwd.nlevels : (double)f.n;
-    int wps = (int)(2.5 * per_level / h->nsm);
+    int wps = (int)(6.0 * per_level / h->nsm);
     if (wps < 6) wps = 6;
     if (wps > 32) wps = 32;
     auto launch = [&](auto tag, auto lay) -> void {
@@ -600,11 +634,14 @@ int factor_numeric(edfa_handle_s* h, Factor& f, const double* vals64, const floa
                                                                      h->ticket, async_ok, h->err));
     };
     const bool narrow = f.fac_R <= FacNarrow::R;
+    const bool medium = !narrow && f.fac_R <= FacMedium::R;
     if (f32) {
         if (narrow) launch(float(0), FacNarrow{});
+        else if (medium) launch(float(0), FacMedium{});
         else launch(float(0), FacWide{});
     } else {
         if (narrow) launch(double(0), FacNarrow{});
+        else if (medium) launch(double(0), FacMedium{});
         else launch(double(0), FacWide{});
     }
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
