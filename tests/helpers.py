@@ -6,7 +6,7 @@ import oracle as O
 
 QCODE = {"own": 0, "nbr": 1, "crow": 2, "thresh": 3, "dynamic": 4}
 
-# Tolerances (derived in the design doc):
+# Tolerances:
 #  FP64 local solves and S~: |gpu - oracle| <= TOL_FP64 * max |oracle| over the
 #  column of X~ / row of S~ (the bar of 1e-10 relative, applied normwise).
 TOL_FP64 = 1e-10
