@@ -282,7 +282,9 @@ EDFA_API int edfa_grad_logk(int32_t Nf, int32_t Ne, const int32_t* cell_faces, c
  * modes EDFA_Q_OWN, EDFA_Q_NBR, EDFA_Q_CROW and EDFA_Q_THRESH (thresh used by
  * the last one); the paper has no counterpart of this entry point.
  *
- * A, B, C: the blocks as for edfa_build (device CSR, validated here).
+ * A, B, C: the blocks as for edfa_build (device CSR, validated here with
+ *          the checks edfa_build makes; invalid blocks return
+ *          EDFA_ERR_INVALID before any kernel reads through their indices).
  * qptr:    caller-owned device array of N_e + 1 int64, receives the offsets.
  * qidx:    caller-owned device array of qidx_capacity int32, receives the
  *          sets, ascending per cell.
@@ -296,14 +298,20 @@ EDFA_API int edfa_grad_logk(int32_t Nf, int32_t Ne, const int32_t* cell_faces, c
  * the sets do not fit in qidx_capacity the call returns EDFA_ERR_BOUNDS with
  * the needed capacity in *qtot and edfa_last_error_detail (qidx untouched).
  *
- * The first call on a device looks up the device address of the fixed array
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call reuses the same array and leaves
- * its contents behind (the parts that must start at zero are cleared on each
- * call), so calls whose work overlaps on the GPU (different streams or host
- * threads at the same time) race and must not be issued.  The call
- * synchronises `stream` once, to read the total size; the fill of qidx is
- * then enqueued on `stream`.  Calls no allocating CUDA or library routine. */
+ * The library's kernels load lazily (CUDA's default module loading), and the
+ * fixed array is reserved on a device when the module holding it is first
+ * used there: by the first edfa_qsets_noalloc or edfa_build call on that
+ * device.  Make one such call at start-up, before the caller's pool takes the
+ * device memory (or run with CUDA_MODULE_LOADING=EAGER, which reserves it
+ * when the library is loaded).  The first call on a device also looks up the
+ * device address of the fixed array (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  Every call
+ * reuses the same array and leaves its contents behind (the parts that must
+ * start at zero are cleared on each call), so calls whose work overlaps on
+ * the GPU (different streams or host threads at the same time) race and must
+ * not be issued.  The call synchronises `stream` twice: after validating the
+ * blocks, and to read the total size; the fill of qidx is then enqueued on
+ * `stream`.  Calls no allocating CUDA or library routine. */
 #define EDFA_NOALLOC_SCRATCH_BYTES (64ull << 20)
 EDFA_API int edfa_qsets_noalloc(const edfa_csr* A, const edfa_csr* B, const edfa_csr* C, int32_t qmode,
                                 double thresh, int64_t* qptr, int32_t* qidx, int64_t qidx_capacity,

@@ -457,11 +457,23 @@ extern "C" int edfa_qsets_noalloc(const edfa_csr* A, const edfa_csr* B, const ed
     cudaMemsetAsync(base + off_misc, 0, sizeof(DevErr) + sizeof(int), s);
     cudaMemsetAsync(bt_ptr, 0, ((size_t)Ne + 1) * sizeof(int64_t), s);
     cudaMemsetAsync(qptr, 0, ((size_t)Ne + 1) * sizeof(int64_t), s);
-    // input validation (same checks as edfa_build)
+    // input validation (the checks edfa_build makes: A must store its
+    // diagonal), read back before any kernel uses the blocks' indices as
+    // addresses
     const edfa_csr* mats[3] = {A, B, C};
     for (int k = 0; k < 3; ++k) {
         int64_t n = (int64_t)mats[k]->nrows + 1;
-        (edfa::count_launch(), k_validate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(csr_of(*mats[k]), 0, err));
+        (edfa::count_launch(),
+         k_validate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(csr_of(*mats[k]), k == 0 ? 1 : 0, err));
+    }
+    {
+        DevErr ve{};
+        cudaMemcpyAsync(&ve, err, sizeof(DevErr), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return EDFA_ERR_CUDA;
+        if (ve.code != 0) {
+            set_detail(ve.detail);
+            return ve.code;
+        }
     }
     // B^T pattern: the faces of each cell
     Csr<double> Bc = csr_of(*B);

@@ -17,6 +17,7 @@ from helpers import gpu_handle
 
 pytestmark = pytest.mark.gpu
 
+EDFA_ERR_INVALID = 1
 EDFA_ERR_BOUNDS = 7
 
 
@@ -84,3 +85,60 @@ def test_noalloc_rejects_small_output_and_oversized_problem():
                                     qptr.data_ptr(), qidx.data_ptr(), 10, ctypes.byref(t), None)
     assert rc == EDFA_ERR_BOUNDS
     assert P.lib().edfa_last_error_detail() > (64 << 20)
+
+
+def test_noalloc_rejects_invalid_blocks_then_recovers():
+    """Blocks whose indices are in range but invalid (columns out of order in a
+    row, a row pointer not starting at 0, A without a stored diagonal) are
+    rejected with EDFA_ERR_INVALID before any kernel reads through them; the
+    next valid call still gives the allocating path's sets."""
+    torch = _torch()
+    import paper_2009_13916_gb300 as P
+    sysd = _full_tensor((7, 6, 5), 43)
+    h = gpu_handle(sysd, mode="nbr")
+    ref = h.tensors()
+    ref_ptr = ref["qptr"].cpu().numpy()
+    ref_idx = ref["qidx"].cpu().numpy()
+    h.close()
+    A, B, C, D = P.system_to_device(sysd)
+    qptr = torch.empty(sysd.Ne + 1, dtype=torch.int64, device="cuda")
+    qidx = torch.full((int(ref_ptr[-1]),), -9, dtype=torch.int32, device="cuda")
+
+    def call(Ab, Bb, Cb):
+        rc, tot = P.qsets_noalloc(Ab, Bb, Cb, sysd.Nf, sysd.Ne, qmode="nbr", qptr=qptr, qidx=qidx)
+        torch.cuda.synchronize()
+        return rc
+
+    # columns of one row of C swapped (both still inside [0, N_f))
+    row = 3
+    c_col = C[1].clone()
+    a, b = int(sysd.C.rowptr[row]), int(sysd.C.rowptr[row]) + 1
+    c_col[a], c_col[b] = C[1][b].item(), C[1][a].item()
+    assert call(A, B, (C[0], c_col, C[2])) == EDFA_ERR_INVALID
+    assert P.lib().edfa_last_error_detail() == row
+    # row pointer of B not starting at 0 (every entry still a valid offset)
+    b_ptr = B[0].clone()
+    b_ptr[0] = 1
+    assert call(A, (b_ptr, B[1], B[2]), C) == EDFA_ERR_INVALID
+    # A without a stored diagonal in one row: its diagonal column replaced by a
+    # free column between its neighbours, so the row stays ascending and in range
+    a_col = None
+    for r in range(sysd.Nf):
+        p0, p1 = int(sysd.A.rowptr[r]), int(sysd.A.rowptr[r + 1])
+        cols = [int(c) for c in sysd.A.col[p0:p1]]
+        d = cols.index(r)
+        lo = cols[d - 1] if d > 0 else -1
+        hi = cols[d + 1] if d + 1 < len(cols) else sysd.Nf
+        free = [c for c in range(lo + 1, hi) if c != r]
+        if free:
+            a_col = A[1].clone()
+            a_col[p0 + d] = free[0]
+            break
+    assert a_col is not None
+    assert call((A[0], a_col, A[2]), B, C) == EDFA_ERR_INVALID
+    assert P.lib().edfa_last_error_detail() == r
+    assert np.all(qidx.cpu().numpy() == -9)
+    # a valid call afterwards
+    assert call(A, B, C) == 0
+    assert np.array_equal(qptr.cpu().numpy(), ref_ptr)
+    assert np.array_equal(qidx.cpu().numpy(), ref_idx)
