@@ -1,9 +1,11 @@
 """The 128x128x64 channelised workload at full size (1,048,576 local systems,
 4,227,072 unknowns, thresh-0.05 sets): sets and S~ pattern bit-exact and X~,
 S~ within 1e-10 against the oracle; FP64 and FP32-mixed FGMRES(50) to 1e-8,
-FP64 iteration count within 2 of the oracle's (golden file written by
-tests/golden/make_c3_fgmres.py from the oracle; the inputs are regenerated
-on each host, so a count off by rounding is allowed one extra iteration)."""
+FP64 iteration count within 1 of the oracle's.  The oracle's count is stored
+in tests/golden/c3_oracle_fgmres.txt (written by make_c3_fgmres.py from the
+oracle) together with the digest of the inputs it belongs to; the generator
+uses no host math library, so the inputs are the same on every host, and if
+the digest ever differs the oracle's FGMRES is run here instead."""
 import os
 
 import numpy as np
@@ -17,11 +19,23 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "c3_oracle_fgmres.txt")
 
 
-def golden_iterations():
+def golden():
+    vals = {}
     for line in open(GOLDEN):
-        if line.startswith("iterations"):
-            return int(line.split()[1])
-    raise RuntimeError("no iteration count in golden file")
+        if not line.startswith("#") and line.strip():
+            k, v = line.split(None, 1)
+            vals[k] = v.strip()
+    return vals
+
+
+def oracle_iterations(sysd):
+    """The oracle's FGMRES(50) count on these inputs: the stored one when the
+    input digest matches, else computed now (several minutes of CPU time)."""
+    g = golden()
+    if g.get("inputs_sha256") == W.digest(sysd):
+        return int(g["iterations"])
+    r = O.edfa_pipeline(sysd, mode="thresh", restart=50, rtol=1e-8, maxit=3000)
+    return int(r["iters"])
 
 
 def test_config3_full_size():
@@ -44,7 +58,8 @@ def test_config3_full_size():
     xg, info = h.solve(b, restart=50, rtol=1e-8, maxit=3000)
     res = np.linalg.norm(sysd.full_scipy() @ xg.cpu().numpy() - sysd.b) / np.linalg.norm(sysd.b)
     assert info.converged and res <= 1.05e-8
-    assert abs(info.iterations - golden_iterations()) <= 2, (info.iterations, golden_iterations())
+    it_orc = oracle_iterations(sysd)
+    assert abs(info.iterations - it_orc) <= 1, (info.iterations, it_orc)
     h.close()
     h32 = gpu_handle(sysd, mode="thresh", thresh=0.05, precision=1)
     x32, info32 = h32.solve(b, restart=50, rtol=1e-8, maxit=3000)
@@ -52,3 +67,12 @@ def test_config3_full_size():
     assert info32.converged and res32 <= 1.05e-8
     assert info32.iterations <= info.iterations * 1.25 + 2
     h32.close()
+
+
+def test_inputs_identical_on_this_host():
+    """Runs with the GPU tests so that it runs on the GPU host (aarch64): the
+    generated inputs equal, bit for bit, those recorded on the x86-64 host."""
+    from test_workloads import DIGEST_C1, DIGEST_C2_8, DIGEST_C3_SMALL
+    assert W.digest(W.config1()) == DIGEST_C1
+    assert W.digest(W.config2(8)) == DIGEST_C2_8
+    assert W.digest(W.config3(16, 12, 6)) == DIGEST_C3_SMALL

@@ -85,6 +85,8 @@ def lib():
         L.wl_elem_W.restype = C.c_int
         L.wl_elem_W.argtypes = [C.POINTER(C.c_double), C.c_double, C.c_double, C.c_double,
                                 C.POINTER(C.c_double)]
+        L.wl_vmath.restype = None
+        L.wl_vmath.argtypes = [C.c_int, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.wl_elem_B.restype = None
         L.wl_elem_B.argtypes = [C.POINTER(C.c_double), C.c_double, C.c_double, C.c_double,
                                 C.POINTER(C.c_double)]
@@ -94,6 +96,31 @@ def lib():
 
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _vmath(f: int, x) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    lib().wl_vmath(int(f), int(x.size), _dp(x), _dp(out))
+    return out
+
+
+# exp, log and sin of the generator (gen.c): IEEE arithmetic only, so that a seed
+# gives the same inputs bit for bit on every host (host math libraries differ in
+# the last bit between machines)
+def wexp(x) -> np.ndarray:
+    return _vmath(0, x)
+
+
+def wlog(x) -> np.ndarray:
+    return _vmath(1, x)
+
+
+def wsin(x) -> np.ndarray:
+    return _vmath(2, x)
+
+
+LN10 = 2.302585092994046
 
 
 class Stream:
@@ -264,7 +291,7 @@ def dome_nodes(nx, ny, nz, height=0.25, wobble=0.02):
     x, y, z = X[:, 0].copy(), X[:, 1].copy(), X[:, 2].copy()
     r2 = ((x - 0.5) ** 2 + (y - 0.5) ** 2) / 0.5
     zn = z + height * (1.0 - z) * (1.0 - r2)  # the layers lifted into a dome
-    yn = y + wobble * np.sin(2 * np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z + 0.3)
+    yn = y + wobble * wsin(2 * np.pi * x) * wsin(np.pi * y) * wsin(np.pi * z + 0.3)
     return np.stack([x, yn, zn], axis=1)
 
 
@@ -274,7 +301,7 @@ def dome(n: int = 12, seed: int = 7, sigma: float = 1.0, name=None) -> System:
     prescribed pressures on x = 0 and x = 1, own + neighbour-face sets."""
     s = Stream(7000 + seed)
     Ne = n ** 3
-    K = iso_K(np.exp(sigma * s.normal(Ne)))
+    K = iso_K(wexp(sigma * s.normal(Ne)))
     sysd = assemble(n, n, n, K, xyz=dome_nodes(n, n, n), name=name or f"dome {n}^3")
     sysd.extra.update(qmode="nbr")
     return sysd
@@ -307,7 +334,13 @@ def rotated_K(m: np.ndarray, aniso: float, q: np.ndarray) -> np.ndarray:
     """K = R diag(m, m, m*aniso) R^T per cell, stored as xx yy zz xy xz yz."""
     R = _quat_rot(q)
     d = np.stack([m, m, m * aniso], axis=1)
-    Kf = np.einsum("nij,nj,nkj->nik", R, d, R)
+    # sum over j written out in a fixed order (no library contraction whose
+    # summation order could depend on the host's vector unit)
+    Kf = np.empty_like(R)
+    for i in range(3):
+        for k in range(3):
+            Kf[:, i, k] = ((R[:, i, 0] * d[:, 0]) * R[:, k, 0] + (R[:, i, 1] * d[:, 1]) * R[:, k, 1]) \
+                + (R[:, i, 2] * d[:, 2]) * R[:, k, 2]
     Kf = 0.5 * (Kf + np.transpose(Kf, (0, 2, 1)))
     return np.stack([Kf[:, 0, 0], Kf[:, 1, 1], Kf[:, 2, 2], Kf[:, 0, 1], Kf[:, 0, 2], Kf[:, 1, 2]], axis=1)
 
@@ -335,11 +368,11 @@ def brick(nx, ny=None, nz=None, *, seed=1, sigma=1.0, kind="paper", rhs="phys", 
     nz = nx if nz is None else nz
     s = Stream(seed)
     Ne = nx * ny * nz
-    k = np.exp(sigma * s.normal(Ne))
+    k = wexp(sigma * s.normal(Ne))
     K = iso_K(k)
     kw = {}
     if kind == "upwind":
-        lam = np.exp(0.5 * s.normal(Ne))
+        lam = wexp(0.5 * s.normal(Ne))
         tmp = assemble(nx, ny, nz, K, dt=dt, stor=stor)  # for the face-cell map only
         signs = s.uniform(tmp.Nf)
         kw = dict(fv_kind=1, lam_face=_face_upwind_mobility(nx, ny, nz, lam, signs, tmp.face_cells))
@@ -355,8 +388,8 @@ def config1() -> System:
     s = Stream(1)
     nx = 10
     Ne = nx ** 3
-    K = iso_K(np.exp(s.normal(Ne)))
-    lam = np.exp(0.5 * s.normal(Ne))
+    K = iso_K(wexp(s.normal(Ne)))
+    lam = wexp(0.5 * s.normal(Ne))
     tmp = assemble(nx, nx, nx, K)
     signs = s.uniform(tmp.Nf)
     lam_f = _face_upwind_mobility(nx, nx, nx, lam, signs, tmp.face_cells)
@@ -372,7 +405,7 @@ def config2(n: int = 64) -> System:
     prescribed-pressure RHS; Q = own faces + faces of face-neighbours."""
     s = Stream(2)
     Ne = n ** 3
-    m = np.exp(2.0 * s.normal(Ne))
+    m = wexp(2.0 * s.normal(Ne))
     q = s.normal(4 * Ne).reshape(Ne, 4)
     K = rotated_K(m, 0.1, q)
     sysd = assemble(n, n, n, K, name=f"C2 {n}^3 full-tensor")
@@ -403,9 +436,9 @@ def channel_K(nx, ny, nz, h, s: Stream) -> np.ndarray:
             fr = 0.5 + 1.5 * p[c, 2]
             ph = 2 * np.pi * p[c, 3]
             hw = 0.02 + 0.03 * p[c, 4]
-            inside |= np.abs(Y - (y0 + a * np.sin(2 * np.pi * fr * X + ph))) < hw
+            inside |= np.abs(Y - (y0 + a * wsin(2 * np.pi * fr * X + ph))) < hw
         lg[iz][inside] = lg_ch[iz][inside]
-    kh = 10.0 ** lg.reshape(Ne)
+    kh = wexp(LN10 * lg.reshape(Ne))
     K = np.zeros((Ne, 6))
     K[:, 0] = kh
     K[:, 1] = kh
@@ -435,7 +468,7 @@ def config4_system(i: int, n: int) -> System:
     strong-flux FV, random N(0,1) RHS, Q = own + neighbour faces."""
     s = Stream((4 << 32) + 1 + i)
     Ne = n ** 3
-    K = iso_K(np.exp(1.5 * s.normal(Ne)))
+    K = iso_K(wexp(1.5 * s.normal(Ne)))
     sysd = assemble(n, n, n, K, name=f"C4[{i}] {n}^3")
     sysd.b = s.normal(sysd.n)
     sysd.extra.update(qmode="nbr")
@@ -455,7 +488,8 @@ def config5(n: int = 48, nobs: int = 64, nfd: int = 20) -> System:
     finite-difference checks."""
     s = Stream(5)
     Ne = n ** 3
-    k = np.exp(s.normal(Ne))
+    logk = s.normal(Ne)
+    k = wexp(logk)
     K = iso_K(k)
     sysd = assemble(n, n, n, K, name=f"C5 {n}^3 adjoint")
     perm = np.arange(Ne)
@@ -470,13 +504,13 @@ def config5(n: int = 48, nobs: int = 64, nfd: int = 20) -> System:
         r = j + int(u[j] * (Ne - j))
         perm[j], perm[r] = perm[r], perm[j]
     fd = np.sort(perm[:nfd]).astype(np.int64)
-    sysd.extra.update(qmode="crow", obs=obs, fd_cells=fd, logk=np.log(k))
+    sysd.extra.update(qmode="crow", obs=obs, fd_cells=fd, logk=logk)
     return sysd
 
 
 def config5_reassemble(sysd: System, logk: np.ndarray) -> System:
     """Re-assemble workload 5 with a modified per-cell log-conductivity."""
-    out = assemble(sysd.nx, sysd.ny, sysd.nz, iso_K(np.exp(logk)), h=sysd.h, dt=sysd.dt,
+    out = assemble(sysd.nx, sysd.ny, sysd.nz, iso_K(wexp(logk)), h=sysd.h, dt=sysd.dt,
                    stor=sysd.stor, name=sysd.name + " (perturbed)")
     out.extra.update(sysd.extra)
     out.extra["logk"] = logk.copy()
@@ -496,7 +530,7 @@ def device_assembler(template: System, device="cuda"):
 
     def assemble_theta(theta):
         lk = theta.detach().double().cpu().numpy()
-        s = assemble(template.nx, template.ny, template.nz, iso_K(np.exp(lk)), h=template.h, dt=template.dt,
+        s = assemble(template.nx, template.ny, template.nz, iso_K(wexp(lk)), h=template.h, dt=template.dt,
                      stor=template.stor, name=template.name + " (theta)")
         return dict(
             A=t(s.A), B=t(s.B), C=t(s.C), D=t(s.D), Nf=s.Nf, Ne=s.Ne,
@@ -509,6 +543,18 @@ def device_assembler(template: System, device="cuda"):
             host=s)
 
     return assemble_theta
+
+
+def digest(sysd: System) -> str:
+    """SHA-256 (hex, first 16 digits) of a system's CSR blocks and right-hand
+    side: identifies the exact inputs a stored expected value belongs to."""
+    import hashlib
+    h = hashlib.sha256()
+    for M in (sysd.A, sysd.B, sysd.C, sysd.D):
+        for a, dt in ((M.rowptr, "<i8"), (M.col, "<i4"), (M.val, "<f8")):
+            h.update(np.ascontiguousarray(a, dtype=dt).tobytes())
+    h.update(np.ascontiguousarray(sysd.b, dtype="<f8").tobytes())
+    return h.hexdigest()[:16]
 
 
 def concat(systems, name="batch"):

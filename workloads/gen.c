@@ -42,12 +42,125 @@ WL_EXPORT double wl_uniform(uint64_t* s)
     return (double)(wl_splitmix64(s) >> 11) * (1.0 / 9007199254740992.0);
 }
 
+/* ---------------------------------------------------------------------
+ * exp, log, sin and cos of the generator, written with IEEE +, -, *, / and
+ * exact scalings by powers of two only.  Host math libraries differ in the
+ * last bit between machines (x86-64 and aarch64 builds of the same library
+ * included), which made the generated matrices, and with them iteration
+ * counts, depend on the host; with these a seed gives the same bits on every
+ * IEEE-754 host (the library is compiled with floating-point contraction off).
+ * Accuracy is a few ulp, which is all a synthetic input needs.
+ *
+ * exp:  x = k ln2 + r with |r| <= ln2/2, ln2 split as LN2_HI + LN2_LO where
+ *       LN2_HI has 32 significant bits (k LN2_HI is exact); e^r by its Taylor
+ *       polynomial of degree 16 in Horner form; times 2^k.
+ * log:  x = m 2^e with m in [sqrt(1/2), sqrt(2)); log m = 2 atanh(s) with
+ *       s = (m - 1)/(m + 1), |s| <= 0.172, odd series to s^25; plus e ln2.
+ * sin, cos: x = k pi/2 + r with |r| <= pi/4, pi/2 split in three parts of 33,
+ *       33 and 53 significant bits (Cody-Waite reduction, exact products for
+ *       |k| < 2^20); Taylor polynomials of sin r (to r^21) and cos r (to
+ *       r^22); the quadrant k mod 4 picks the sign and the function.
+ * The split constants are pi/2 and ln 2 computed to 60 digits and cut after
+ * the stated numbers of bits.
+ * --------------------------------------------------------------------- */
+static const double WL_LN2_HI = 0.6931471803691238;
+static const double WL_LN2_LO = 1.9082149292705877e-10;
+static const double WL_INV_LN2 = 1.4426950408889634;
+static const double WL_PIO2_1 = 1.5707963267341256;
+static const double WL_PIO2_2 = 6.077100506303966e-11;
+static const double WL_PIO2_3 = 2.0222662487959506e-21;
+static const double WL_TWO_OVER_PI = 0.6366197723675814;
+
+WL_EXPORT double wl_exp(double x)
+{
+    if (x != x) return x;
+    if (x > 709.0) return HUGE_VAL;
+    if (x < -745.0) return 0.0;
+    double k = floor(x * WL_INV_LN2 + 0.5);
+    double r = (x - k * WL_LN2_HI) - k * WL_LN2_LO;
+    double p = 1.0;
+    for (int n = 16; n >= 1; --n) p = 1.0 + p * r / (double)n;
+    return ldexp(p, (int)k);
+}
+
+WL_EXPORT double wl_log(double x)
+{
+    if (!(x > 0.0)) return x == 0.0 ? -HUGE_VAL : (x - x) / (x - x);
+    if (x == HUGE_VAL) return x;
+    int e = 0;
+    double m = frexp(x, &e); /* m in [1/2, 1) */
+    if (m < 0.7071067811865476) { m *= 2.0; e -= 1; }
+    double s = (m - 1.0) / (m + 1.0);
+    double s2 = s * s;
+    double t = 1.0 / 25.0;
+    for (int k = 23; k >= 1; k -= 2) t = 1.0 / (double)k + s2 * t;
+    return (2.0 * s * t + (double)e * WL_LN2_LO) + (double)e * WL_LN2_HI;
+}
+
+static double wl_sin_poly(double r)
+{
+    double r2 = r * r, t = 1.0;
+    for (int n = 21; n >= 3; n -= 2) t = 1.0 - t * r2 / ((double)n * (double)(n - 1));
+    return r * t;
+}
+
+static double wl_cos_poly(double r)
+{
+    double r2 = r * r, t = 1.0;
+    for (int n = 22; n >= 2; n -= 2) t = 1.0 - t * r2 / ((double)n * (double)(n - 1));
+    return t;
+}
+
+/* quadrant q = k mod 4 and reduced argument r of x */
+static double wl_reduce(double x, int* q)
+{
+    double k = floor(x * WL_TWO_OVER_PI + 0.5);
+    double r = ((x - k * WL_PIO2_1) - k * WL_PIO2_2) - k * WL_PIO2_3;
+    long long kk = (long long)k;
+    *q = (int)(((kk % 4) + 4) % 4);
+    return r;
+}
+
+WL_EXPORT double wl_sin(double x)
+{
+    int q;
+    double r = wl_reduce(x, &q);
+    switch (q) {
+    case 0: return wl_sin_poly(r);
+    case 1: return wl_cos_poly(r);
+    case 2: return -wl_sin_poly(r);
+    default: return -wl_cos_poly(r);
+    }
+}
+
+WL_EXPORT double wl_cos(double x)
+{
+    int q;
+    double r = wl_reduce(x, &q);
+    switch (q) {
+    case 0: return wl_cos_poly(r);
+    case 1: return -wl_sin_poly(r);
+    case 2: return -wl_cos_poly(r);
+    default: return wl_sin_poly(r);
+    }
+}
+
+/* elementwise forms for the Python side: out[i] = f(in[i]), f = 0 exp, 1 log,
+ * 2 sin, 3 cos */
+WL_EXPORT void wl_vmath(int f, int64_t n, const double* in, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double x = in[i];
+        out[i] = f == 0 ? wl_exp(x) : f == 1 ? wl_log(x) : f == 2 ? wl_sin(x) : wl_cos(x);
+    }
+}
+
 /* standard normal by the Box-Muller transform (cosine branch only) */
 WL_EXPORT double wl_normal(uint64_t* s)
 {
     double u1 = 1.0 - wl_uniform(s); /* (0,1] */
     double u2 = wl_uniform(s);
-    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+    return sqrt(-2.0 * wl_log(u1)) * wl_cos(6.283185307179586 * u2);
 }
 
 WL_EXPORT void wl_fill_uniform(uint64_t* s, int64_t n, double* out)
