@@ -201,3 +201,24 @@ def test_dynamic_sets_parity(dyn):
     x, info = h.solve(torch.as_tensor(sysd.b, device="cuda"), restart=50, rtol=1e-8, maxit=2000)
     assert info.converged and abs(info.iterations - ref["iters"]) <= 1
     h.close()
+
+
+@pytest.mark.parametrize("case,dyn", [("full", (4, 12, 100)), ("full", (1, 6, 100)), ("dome", (4, 12, 100))])
+def test_dynamic_sets_parity_24(case, dyn):
+    # Algorithm 1 (dynamic branch) on 24^3 grids with the paper's (n_add, n_ent)
+    # settings of Tests 2 and 4: sets grow from up to 36 to up to 48 faces and up
+    # to ~130 candidates per sweep pass through the kernel's hash table
+    torch = _torch()
+    sysd = full_tensor((24, 24, 24), seed=29) if case == "full" else W.dome(24)
+    ref = O.edfa_pipeline(sysd, mode="dynamic", dyn=dyn, solve=True)
+    h = gpu_handle(sysd, mode="dynamic", dyn=dyn)
+    g = gpu_results(h)
+    assert np.array_equal(g["qptr"], ref["qptr"])
+    assert np.array_equal(g["qidx"], ref["qidx"])
+    assert np.diff(ref["qptr"]).max() == 36 + dyn[1]
+    assert normwise_cols_fast(g["xval"], ref["xval"], ref["qptr"]) <= TOL_FP64
+    assert np.array_equal(g["s_col"], ref["S"].col)
+    assert normwise_cols_fast(g["s_val"], ref["S"].val, ref["S"].rowptr) <= TOL_FP64
+    x, info = h.solve(torch.as_tensor(sysd.b, device="cuda"), restart=50, rtol=1e-8, maxit=2000)
+    assert info.converged and abs(info.iterations - ref["iters"]) <= 1
+    h.close()
