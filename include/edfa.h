@@ -317,6 +317,21 @@ EDFA_API int edfa_qsets_noalloc(const edfa_csr* A, const edfa_csr* B, const edfa
                                 double thresh, int64_t* qptr, int32_t* qidx, int64_t qidx_capacity,
                                 int64_t* qtot, edfa_stream stream);
 
+/* Diagnostic of the library's failure detection (no counterpart in the paper).
+ * Every device-side wait of the library (a row waiting for a value another
+ * warp computes, a warp waiting on a flag or an mbarrier) is bounded: when its
+ * poll budget runs out it records EDFA_ERR_TIMEOUT with the waiting row in the
+ * detail, every other wait of that kernel gives up, and the kernel returns, so
+ * a lost dependency never hangs the GPU and the CUDA context stays usable.
+ * This call makes such a wait run out on purpose: it runs the sync-free
+ * forward-sweep kernel on a 2 x 2 unit lower-triangular system with a level
+ * plan that omits row 0, so row 1 waits for a value nothing writes.  Returns
+ * EDFA_ERR_TIMEOUT (edfa_last_error_detail() = 1) when the budget ran out as
+ * designed; *ms (may be NULL) receives the kernel's duration.  Synchronises
+ * `stream`; allocates and frees a few hundred bytes of device memory; must not
+ * run concurrently with other work of this library on the device. */
+EDFA_API int edfa_selftest_wait_timeout(float* ms, edfa_stream stream);
+
 /* Number of CUDA kernels this library has launched in this process. */
 EDFA_API int64_t edfa_launch_count(void);
 

@@ -76,7 +76,7 @@ _lib = None
 EXPORTS = ("edfa_default_options", "edfa_build", "edfa_setup", "edfa_apply", "edfa_matvec",
            "edfa_solve", "edfa_history", "edfa_get_view", "edfa_get_stats", "edfa_set_profiling",
            "edfa_launch_count", "edfa_qsets_noalloc", "edfa_build_adjoint", "edfa_grad_logk",
-           "edfa_solve_batched", "edfa_solve_bicgstab",
+           "edfa_solve_batched", "edfa_solve_bicgstab", "edfa_selftest_wait_timeout",
            "edfa_free", "edfa_strerror",
            "edfa_last_error_detail")
 
@@ -114,6 +114,8 @@ def lib(build_if_missing: bool = True):
         L.edfa_qsets_noalloc.argtypes = [P(Csr), P(Csr), P(Csr), C.c_int32, C.c_double, vp, vp, C.c_int64,
                                          P(C.c_int64), vp]
         L.edfa_qsets_noalloc.restype = C.c_int
+        L.edfa_selftest_wait_timeout.argtypes = [P(C.c_float), vp]
+        L.edfa_selftest_wait_timeout.restype = C.c_int
         L.edfa_build_adjoint.argtypes = [P(vp), vp, vp]
         L.edfa_build_adjoint.restype = C.c_int
         L.edfa_grad_logk.argtypes = [C.c_int32, C.c_int32] + [vp] * 8 + [vp]
@@ -197,6 +199,13 @@ def grad_logk(geom, u, lam, Nf: int, Ne: int, stream=None):
     if rc != EDFA_OK:
         raise EdfaError(rc, "edfa_grad_logk")
     return g
+
+
+def selftest_wait_timeout(stream=None):
+    """edfa_selftest_wait_timeout: returns (rc, detail, kernel ms)."""
+    ms = C.c_float(0)
+    rc = lib().edfa_selftest_wait_timeout(C.byref(ms), C.c_void_p(_stream(stream)))
+    return rc, int(lib().edfa_last_error_detail()), float(ms.value)
 
 
 def launch_count() -> int:

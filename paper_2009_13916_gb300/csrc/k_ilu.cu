@@ -16,6 +16,8 @@
 
 #include <cooperative_groups.h>
 
+#include <cstring>
+
 #include "internal.cuh"
 
 // lanes per row of the sweeps over A~ and S~ (1 = thread per row) and the
@@ -1035,6 +1037,58 @@ int to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t s)
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
+// ------------------------------------------------------------ wait self-test
+// The forward sync-free sweep kernel of the S~ factor run on a 2 x 2 unit lower
+// triangular system (row 1 depends on row 0) with a level plan that leaves out
+// row 0: row 1's bounded wait for x_0 can never end, so it runs to its poll
+// budget, records EDFA_ERR_TIMEOUT with detail 1 and the kernel finishes.
+static int wait_selftest(cudaStream_t s, long long* detail, float* ms)
+{
+    constexpr int LPR = EDFA_LPR_S, RPW = 32 / LPR;
+    auto fn = k_sweep<double, double, double, 1, LPR, (LPR >= 32 ? 1 : (LPR >= 16 ? 2 : 4))>;
+    struct Buf {
+        int64_t rowptr[3], diag[2];
+        int32_t col[3], perm[RPW];
+        double lu[3], base[2], out[2];
+        unsigned long long ticket;
+        DevErr err;
+    } hb{};
+    hb.rowptr[0] = 0; hb.rowptr[1] = 1; hb.rowptr[2] = 3;
+    hb.col[0] = 0; hb.col[1] = 0; hb.col[2] = 1;
+    hb.diag[0] = 0; hb.diag[1] = 2;
+    hb.lu[0] = 1.0; hb.lu[1] = 0.5; hb.lu[2] = 1.0;
+    hb.base[0] = 1.0; hb.base[1] = 1.0;
+    hb.perm[0] = 1;  // the only planned row; row 0 is never computed
+    for (int k = 1; k < RPW; ++k) hb.perm[k] = -1;
+    memset(hb.out, 0xFF, sizeof hb.out);  // the "not yet computed" pattern
+    Buf* db = nullptr;
+    if (cudaMalloc((void**)&db, sizeof(Buf)) != cudaSuccess) { cudaGetLastError(); return EDFA_ERR_OOM; }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = EDFA_OK;
+    if (cudaMemcpyAsync(db, &hb, sizeof(Buf), cudaMemcpyHostToDevice, s) != cudaSuccess) rc = EDFA_ERR_CUDA;
+    if (!rc) {
+        cudaEventRecord(e0, s);
+        (edfa::count_launch(), fn<<<1, kSweepThreads, 0, s>>>(db->perm, RPW, db->rowptr, db->col, db->lu, db->diag,
+                                                                nullptr, db->base, nullptr, nullptr, nullptr,
+                                                                nullptr, db->out, &db->ticket, &db->err));
+        cudaEventRecord(e1, s);
+        DevErr e{};
+        cudaMemcpyAsync(&e, &db->err, sizeof(DevErr), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) rc = EDFA_ERR_CUDA;
+        else {
+            rc = e.code;
+            *detail = e.detail;
+            cudaEventElapsedTime(ms, e0, e1);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(db);
+    return rc;
+}
+
 int apply_prec(edfa_handle_s* h, const double* r, double* z, cudaStream_t s)
 {
     if (h->opt.precision == 1) return apply_impl<float>(h, r, z, s);
@@ -1042,3 +1096,13 @@ int apply_prec(edfa_handle_s* h, const double* r, double* z, cudaStream_t s)
 }
 
 }  // namespace edfa
+
+extern "C" int edfa_selftest_wait_timeout(float* ms, edfa_stream stream)
+{
+    long long detail = -1;
+    float t = 0.f;
+    int rc = edfa::wait_selftest((cudaStream_t)stream, &detail, &t);
+    edfa::set_detail(detail);
+    if (ms) *ms = t;
+    return rc;
+}
