@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=os.path.dirname(_SO))
     os.close(fd)
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fvisibility=hidden",
-                           "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+                           "-ffp-contract=off", "-fopenmp", _SRC, "-o", tmp, "-lm"])
     os.replace(tmp, _SO)
     return _SO
 
@@ -62,6 +62,8 @@ def lib():
         L = C.CDLL(build())
         P = C.POINTER
         L.orc_free.argtypes = [C.c_void_p]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_set_threads.restype = None
         L.orc_free_csr.argtypes = [P(_CSR)]
         L.orc_qsets.argtypes = [C.c_int, C.c_double, P(_CSR), P(_CSR), P(_CSR),
                                 P(C.c_void_p), P(C.c_void_p)]
@@ -98,6 +100,12 @@ def lib():
         assert L.orc_prec_sizeof() == C.sizeof(_Prec)
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the per-cell local-solve loop (1 by default; results do not
+    depend on it)."""
+    lib().orc_set_threads(int(n))
 
 
 def _ptr(a):

@@ -217,6 +217,13 @@ static void lu_solve(const double* M, int s, double* x)
  *   -A^(m) f~ = R b_m        (b_m = column m of B)  -> xval: X~ = -F~ on Q^(m)
  * -A^(m) is factorised by LU without pivoting (it is SPD).  Either output may
  * be NULL.  A zero or non-finite pivot returns -2 with the cell in *bad. */
+/* Thread count of the per-cell loop below (1 by default).  The local systems
+ * are independent (Sec. 3, Remark 5) and the paper solves them under a
+ * parallel loop over cells; with n > 1 the loop runs on n OpenMP threads.
+ * Every cell's arithmetic is the same whatever n is, so the results are too. */
+static int g_threads = 1;
+ORC_EXPORT void orc_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+
 ORC_EXPORT int orc_local_solves(const orc_csr* A, const orc_csr* B, const orc_csr* C,
                                 const int64_t* qptr, const int32_t* qidx,
                                 double* xval, double* gval, int32_t* bad)
@@ -225,29 +232,47 @@ ORC_EXPORT int orc_local_solves(const orc_csr* A, const orc_csr* B, const orc_cs
     int smax = 0;
     for (int32_t m = 0; m < Ne; ++m)
         if (qptr[m + 1] - qptr[m] > smax) smax = (int)(qptr[m + 1] - qptr[m]);
-    double* M = (double*)malloc((size_t)(smax ? smax : 1) * (smax ? smax : 1) * sizeof(double));
-    double* x = (double*)malloc((size_t)(smax ? smax : 1) * sizeof(double));
-    if (!M || !x) { free(M); free(x); return -1; }
-    for (int32_t m = 0; m < Ne; ++m) {
-        const int32_t* q = qidx + qptr[m];
-        int s = (int)(qptr[m + 1] - qptr[m]);
-        if (s == 0) continue;
-        gather_local(A, q, s, M);
-        for (int i = 0; i < s * s; ++i) M[i] = -M[i];
-        if (lu_nopivot(M, s)) { if (bad) *bad = m; free(M); free(x); return -2; }
-        if (xval) {
-            for (int i = 0; i < s; ++i) x[i] = csr_get(B, q[i], m, NULL);
-            lu_solve(M, s, x);              /* x = f~ */
-            for (int i = 0; i < s; ++i) xval[qptr[m] + i] = -x[i];
+    int rc = 0;
+    int32_t first_bad = -1;
+#pragma omp parallel num_threads(g_threads)
+    {
+        double* M = (double*)malloc((size_t)(smax ? smax : 1) * (smax ? smax : 1) * sizeof(double));
+        double* x = (double*)malloc((size_t)(smax ? smax : 1) * sizeof(double));
+        if (!M || !x) {
+#pragma omp critical
+            rc = -1;
         }
-        if (gval) {
-            for (int i = 0; i < s; ++i) x[i] = csr_get(C, m, q[i], NULL);
-            lu_solve(M, s, x);              /* x = g~ */
-            for (int i = 0; i < s; ++i) gval[qptr[m] + i] = x[i];
+#pragma omp for schedule(dynamic, 256)
+        for (int32_t m = 0; m < Ne; ++m) {
+            const int32_t* q = qidx + qptr[m];
+            int s = (int)(qptr[m + 1] - qptr[m]);
+            if (s == 0 || !M || !x) continue;
+            gather_local(A, q, s, M);
+            for (int i = 0; i < s * s; ++i) M[i] = -M[i];
+            if (lu_nopivot(M, s)) {
+#pragma omp critical
+                if (first_bad < 0 || m < first_bad) first_bad = m;
+                continue;
+            }
+            if (xval) {
+                for (int i = 0; i < s; ++i) x[i] = csr_get(B, q[i], m, NULL);
+                lu_solve(M, s, x);              /* x = f~ */
+                for (int i = 0; i < s; ++i) xval[qptr[m] + i] = -x[i];
+            }
+            if (gval) {
+                for (int i = 0; i < s; ++i) x[i] = csr_get(C, m, q[i], NULL);
+                lu_solve(M, s, x);              /* x = g~ */
+                for (int i = 0; i < s; ++i) gval[qptr[m] + i] = x[i];
+            }
         }
+        free(M);
+        free(x);
     }
-    free(M);
-    free(x);
+    if (rc) return rc;
+    if (first_bad >= 0) {
+        if (bad) *bad = first_bad;
+        return -2;
+    }
     return 0;
 }
 

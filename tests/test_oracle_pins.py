@@ -532,3 +532,18 @@ def test_bicgstab_edfa_workload_converges():
     assert r["converged"] and r["true_rel"] <= 1e-8
     res = np.linalg.norm(sysd.full_scipy() @ r["x"] - sysd.b) / np.linalg.norm(sysd.b)
     assert res <= 1.05e-8
+
+
+def test_local_solves_do_not_depend_on_thread_count():
+    """The per-cell loop may run on several threads (the paper's parallel loop
+    over cells); every cell's arithmetic is unchanged, so X~ and G~ are equal
+    bit for bit."""
+    s = W.config2(10)
+    q = O.qsets("nbr", s.A, s.B, s.C)
+    x1, g1 = O.local_solves(s.A, s.B, s.C, *q, want_g=True)
+    try:
+        O.set_threads(4)
+        x4, g4 = O.local_solves(s.A, s.B, s.C, *q, want_g=True)
+    finally:
+        O.set_threads(1)
+    assert np.array_equal(x1, x4) and np.array_equal(g1, g4)
