@@ -50,7 +50,8 @@ class _CSR(C.Structure):
 class _Prec(C.Structure):
     _fields_ = [("A", _CSR), ("B", _CSR), ("C", _CSR), ("D", _CSR), ("Ma", _CSR),
                 ("lua", C.c_void_p), ("Ms", _CSR), ("lus", C.c_void_p),
-                ("variant", C.c_int), ("identity", C.c_int)]
+                ("variant", C.c_int), ("identity", C.c_int),
+                ("aperm", C.c_void_p), ("sperm", C.c_void_p), ("own_a", _CSR), ("own_s", _CSR)]
 
 
 _lib = None
@@ -90,12 +91,17 @@ def lib():
                                    P(C.c_int), C.c_void_p, P(C.c_double)]
         L.orc_prec_setup.argtypes = [P(_Prec), P(_CSR), P(_CSR), P(_CSR), P(_CSR), P(_CSR),
                                      P(_CSR), C.c_int, C.c_int, P(C.c_int32)]
+        L.orc_prec_setup_ordered.argtypes = [P(_Prec), P(_CSR), P(_CSR), P(_CSR), P(_CSR), P(_CSR),
+                                             P(_CSR), C.c_int, C.c_int, C.c_void_p, C.c_void_p, P(C.c_int32)]
+        L.orc_colour_order.argtypes = [P(_CSR), C.c_void_p, C.c_void_p, P(C.c_int32)]
+        L.orc_permute.argtypes = [P(_CSR), C.c_void_p, P(_CSR)]
         L.orc_prec_free.argtypes = [P(_Prec)]
         L.orc_prec_free.restype = None
         L.orc_prec_sizeof.restype = C.c_int
         L.orc_adjoint_grad.argtypes = [C.c_int32, C.c_int32] + [C.c_void_p] * 9
         for name in ("orc_qsets", "orc_qsets_dynamic", "orc_local_solves", "orc_schur",
-                     "orc_ilu0", "orc_fgmres", "orc_prec_setup", "orc_adjoint_grad"):
+                     "orc_ilu0", "orc_fgmres", "orc_prec_setup", "orc_adjoint_grad",
+                     "orc_prec_setup_ordered", "orc_colour_order", "orc_permute"):
             getattr(L, name).restype = C.c_int
         assert L.orc_prec_sizeof() == C.sizeof(_Prec)
         _lib = L
@@ -326,16 +332,19 @@ def ilu0_solve(M, lu, r):
 class Prec:
     """Preconditioner record: the system blocks, ILU(0) of Ma (for A~^{-1}) and of S~."""
 
-    def __init__(self, A, B, C_, D, S=None, Ma=None, variant=0, identity=False):
+    def __init__(self, A, B, C_, D, S=None, Ma=None, variant=0, identity=False, aperm=None, sperm=None):
         self.A, self.B, self.C, self.D = Mat.of(A), Mat.of(B), Mat.of(C_), Mat.of(D)
         self.Ma = self.A if Ma is None else Mat.of(Ma)
         self.S = None if S is None else Mat.of(S)
+        self.aperm = None if aperm is None else np.ascontiguousarray(aperm, dtype=np.int32)
+        self.sperm = None if sperm is None else np.ascontiguousarray(sperm, dtype=np.int32)
         self.p = _Prec()
         bad = C.c_int32(-1)
         Sc = self.S.c if self.S is not None else _CSR()
-        rc = lib().orc_prec_setup(C.byref(self.p), C.byref(self.A.c), C.byref(self.B.c),
-                                  C.byref(self.C.c), C.byref(self.D.c), C.byref(self.Ma.c),
-                                  C.byref(Sc), int(variant), 1 if identity else 0, C.byref(bad))
+        rc = lib().orc_prec_setup_ordered(C.byref(self.p), C.byref(self.A.c), C.byref(self.B.c),
+                                          C.byref(self.C.c), C.byref(self.D.c), C.byref(self.Ma.c),
+                                          C.byref(Sc), int(variant), 1 if identity else 0,
+                                          _ptr(self.aperm), _ptr(self.sperm), C.byref(bad))
         if rc:
             raise RuntimeError(f"orc_prec_setup failed ({rc}) at row {bad.value}")
         self._owned = not identity
@@ -360,8 +369,44 @@ class Prec:
     def lua(self):
         return np.ctypeslib.as_array(C.cast(self.p.lua, C.POINTER(C.c_double)), shape=(self.Ma.nnz,)).copy()
 
+    def ordered_factor(self, which="s"):
+        """(pattern, ILU(0) values) of the factorised matrix (ordered when an
+        ordering was given): which = "a" (A~) or "s" (S~)."""
+        M = self.p.Ma if which == "a" else self.p.Ms
+        lu = self.p.lua if which == "a" else self.p.lus
+        nnz = int(M.nnz)
+        g = lambda ptr, n, t: np.ctypeslib.as_array(C.cast(ptr, C.POINTER(t)), shape=(n,)).copy()
+        pat = Mat(M.nrows, M.ncols, g(M.rowptr, M.nrows + 1, C.c_int64), g(M.col, nnz, C.c_int32),
+                  g(M.val, nnz, C.c_double))
+        return pat, g(lu, nnz, C.c_double)
+
     def lus(self):
         return np.ctypeslib.as_array(C.cast(self.p.lus, C.POINTER(C.c_double)), shape=(self.S.nnz,)).copy()
+
+
+def colour_order(M):
+    """Multicolour ordering of the graph of M + M^T (the oracle's colouring):
+    returns (colour per row, perm with rows sorted by (colour, index), number
+    of colours)."""
+    M = Mat.of(M)
+    colour = np.empty(M.nrows, np.int32)
+    perm = np.empty(M.nrows, np.int32)
+    nc = C.c_int32(0)
+    rc = lib().orc_colour_order(C.byref(M.c), _ptr(colour), _ptr(perm), C.byref(nc))
+    if rc:
+        raise RuntimeError("orc_colour_order failed")
+    return colour, perm, int(nc.value)
+
+
+def permute(M, perm) -> Mat:
+    """P M P^T (row k = row perm[k] of M, columns renamed and sorted)."""
+    M = Mat.of(M)
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    out = _CSR()
+    rc = lib().orc_permute(C.byref(M.c), _ptr(perm), C.byref(out))
+    if rc:
+        raise RuntimeError("orc_permute failed")
+    return _take_csr(out)
 
 
 def fgmres(prec: Prec, b, restart=50, rtol=1e-8, maxit=2000):
@@ -425,17 +470,20 @@ def qsets_for(sysd, mode=None, thresh=None, dyn=None):
 
 
 def edfa_pipeline(sysd, mode=None, form=0, variant=0, restart=50, rtol=1e-8, maxit=2000, b=None,
-                  dyn=None, solve=True, filt="none", tau=0.0):
+                  dyn=None, solve=True, filt="none", tau=0.0, ordering=0):
     """The whole hot path on the CPU: Q sets, local solves, S~ (optionally
-    filtered), ILU(0)s, FGMRES."""
+    filtered), ILU(0)s (ordering 0: natural; 1: multicolour ordering of S~;
+    2: multicolour orderings of A and S~), FGMRES."""
     qptr, qidx = qsets_for(sysd, mode, dyn=dyn)
     xval, gval = local_solves(sysd.A, sysd.B, sysd.C, qptr, qidx, True, form == 1)
     if filt == "none":
         S = schur(form, sysd.A, sysd.C, sysd.D, qptr, qidx, xval, gval)
     else:
         S, _ = schur_filtered(form, sysd.A, sysd.C, sysd.D, qptr, qidx, xval, gval, filt, tau)
-    P = Prec(sysd.A, sysd.B, sysd.C, sysd.D, S=S, variant=variant)
-    out = dict(qptr=qptr, qidx=qidx, xval=xval, gval=gval, S=S, prec=P)
+    aperm = colour_order(sysd.A)[1] if ordering == 2 else None
+    sperm = colour_order(S)[1] if ordering >= 1 else None
+    P = Prec(sysd.A, sysd.B, sysd.C, sysd.D, S=S, variant=variant, aperm=aperm, sperm=sperm)
+    out = dict(qptr=qptr, qidx=qidx, xval=xval, gval=gval, S=S, prec=P, aperm=aperm, sperm=sperm)
     if solve:
         out.update(fgmres(P, sysd.b if b is None else b, restart, rtol, maxit))
     return out

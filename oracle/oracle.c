@@ -768,6 +768,12 @@ typedef struct {
     const double* lus;       /* ILU(0) factor values of S~ */
     int variant;             /* 0: full block LDU (Eq. EDFA_prec); 1: upper block triangular */
     int identity;            /* 1: no preconditioning */
+    /* optional orderings of the inner factorisations (NULL: natural order):
+     * with aperm the factorised matrix is P_a Ma P_a^T, with sperm P_s S~ P_s^T,
+     * row k of the ordered matrix being row perm[k] of the original */
+    const int32_t* aperm;
+    const int32_t* sperm;
+    orc_ocsr own_a, own_s;   /* the ordered copies, owned by the record */
 } orc_prec;
 
 /* z = P^{-1} r, Eq. (EDFA_prec) applied right to left:
@@ -778,6 +784,23 @@ typedef struct {
  * (the second application uses linearity: y - A~^{-1} B z_p).  The triangular
  * factors use the exact B and C (Remark 1).  variant 1: z_p = S~^{-1} r_p,
  * z_pi = A~^{-1}(r_pi - B z_p). */
+/* z = M~^{-1} r with the ILU(0) factors of the (possibly reordered) matrix:
+ * with an ordering, r is gathered into the ordered numbering, solved there and
+ * z scattered back (z[perm[k]] = solution[k]). */
+static void inner_solve(const orc_csr* M, const double* lu, const int32_t* perm, const double* r, double* z)
+{
+    if (!perm) {
+        orc_ilu0_solve(M, lu, r, z);
+        return;
+    }
+    const int32_t n = M->nrows;
+    double* w = (double*)malloc((size_t)(n ? n : 1) * 2 * sizeof(double));
+    for (int32_t k = 0; k < n; ++k) w[k] = r[perm[k]];
+    orc_ilu0_solve(M, lu, w, w + n);
+    for (int32_t k = 0; k < n; ++k) z[perm[k]] = w[n + k];
+    free(w);
+}
+
 ORC_EXPORT void orc_apply(const orc_prec* P, const double* r, double* z)
 {
     const int32_t Nf = P->A.nrows, Ne = P->D.nrows;
@@ -789,23 +812,23 @@ ORC_EXPORT void orc_apply(const orc_prec* P, const double* r, double* z)
     double* zpi = z;
     double* zp = z + Nf;
     if (P->variant == 0) {
-        orc_ilu0_solve(&P->Ma, P->lua, rpi, y);
+        inner_solve(&P->Ma, P->lua, P->aperm, rpi, y);
         for (int32_t e = 0; e < Ne; ++e) t[e] = rp[e];
         for (int32_t e = 0; e < Ne; ++e) {
             double v = 0.0;
             for (int64_t p = P->C.rowptr[e]; p < P->C.rowptr[e + 1]; ++p) v += P->C.val[p] * y[P->C.col[p]];
             t[e] -= v;
         }
-        orc_ilu0_solve(&P->Ms, P->lus, t, zp);
+        inner_solve(&P->Ms, P->lus, P->sperm, t, zp);
     } else {
-        orc_ilu0_solve(&P->Ms, P->lus, rp, zp);
+        inner_solve(&P->Ms, P->lus, P->sperm, rp, zp);
     }
     for (int32_t f = 0; f < Nf; ++f) {
         double v = 0.0;
         for (int64_t p = P->B.rowptr[f]; p < P->B.rowptr[f + 1]; ++p) v += P->B.val[p] * zp[P->B.col[p]];
         t[f] = rpi[f] - v;
     }
-    orc_ilu0_solve(&P->Ma, P->lua, t, zpi);
+    inner_solve(&P->Ma, P->lua, P->aperm, t, zpi);
     free(y);
     free(t);
 }
@@ -997,9 +1020,20 @@ done:
     return status;
 }
 
-ORC_EXPORT int orc_prec_setup(orc_prec* P, const orc_csr* A, const orc_csr* B, const orc_csr* C,
-                              const orc_csr* D, const orc_csr* Ma, const orc_csr* S, int variant,
-                              int identity, int32_t* bad)
+ORC_EXPORT int orc_permute(const orc_csr* M, const int32_t* perm, orc_ocsr* out);
+
+static orc_csr as_csr(const orc_ocsr* M)
+{
+    orc_csr c = {M->nrows, M->ncols, M->nnz, M->rowptr, M->col, M->val};
+    return c;
+}
+
+/* Preconditioner record; aperm / sperm (may be NULL) order the inner ILU(0)
+ * factorisations of Ma and S~ (the record keeps the pointers: they must stay
+ * valid while it is used). */
+ORC_EXPORT int orc_prec_setup_ordered(orc_prec* P, const orc_csr* A, const orc_csr* B, const orc_csr* C,
+                                      const orc_csr* D, const orc_csr* Ma, const orc_csr* S, int variant,
+                                      int identity, const int32_t* aperm, const int32_t* sperm, int32_t* bad)
 {
     memset(P, 0, sizeof *P);
     P->A = *A; P->B = *B; P->C = *C; P->D = *D;
@@ -1008,16 +1042,33 @@ ORC_EXPORT int orc_prec_setup(orc_prec* P, const orc_csr* A, const orc_csr* B, c
     if (identity) return 0;
     P->Ma = *Ma;
     P->Ms = *S;
-    double* la = (double*)malloc((size_t)(Ma->rowptr[Ma->nrows] ? Ma->rowptr[Ma->nrows] : 1) * sizeof(double));
-    double* ls = (double*)malloc((size_t)(S->rowptr[S->nrows] ? S->rowptr[S->nrows] : 1) * sizeof(double));
+    if (aperm) {
+        if (orc_permute(Ma, aperm, &P->own_a)) return -1;
+        P->Ma = as_csr(&P->own_a);
+        P->aperm = aperm;
+    }
+    if (sperm) {
+        if (orc_permute(S, sperm, &P->own_s)) return -1;
+        P->Ms = as_csr(&P->own_s);
+        P->sperm = sperm;
+    }
+    double* la = (double*)malloc((size_t)(P->Ma.nnz ? P->Ma.nnz : 1) * sizeof(double));
+    double* ls = (double*)malloc((size_t)(P->Ms.nnz ? P->Ms.nnz : 1) * sizeof(double));
     if (!la || !ls) return -1;
-    int rc = orc_ilu0(Ma, la, bad);
+    int rc = orc_ilu0(&P->Ma, la, bad);
     if (rc) { free(la); free(ls); return rc; }
-    rc = orc_ilu0(S, ls, bad);
+    rc = orc_ilu0(&P->Ms, ls, bad);
     if (rc) { free(la); free(ls); return rc - 10; }
     P->lua = la;
     P->lus = ls;
     return 0;
+}
+
+ORC_EXPORT int orc_prec_setup(orc_prec* P, const orc_csr* A, const orc_csr* B, const orc_csr* C,
+                              const orc_csr* D, const orc_csr* Ma, const orc_csr* S, int variant,
+                              int identity, int32_t* bad)
+{
+    return orc_prec_setup_ordered(P, A, B, C, D, Ma, S, variant, identity, NULL, NULL, bad);
 }
 
 ORC_EXPORT void orc_prec_free(orc_prec* P)
@@ -1025,6 +1076,122 @@ ORC_EXPORT void orc_prec_free(orc_prec* P)
     free((void*)P->lua);
     free((void*)P->lus);
     P->lua = P->lus = NULL;
+    if (P->aperm) orc_free_csr(&P->own_a);
+    if (P->sperm) orc_free_csr(&P->own_s);
+    P->aperm = P->sperm = NULL;
+}
+
+/* ------------------------------------------------- multicolour ordering
+ * An optional ordering of the inner ILU(0) factorisations.  The paper leaves
+ * the inner preconditioners and their ordering open (Sec. 3, inner
+ * preconditioners; Sec. 4 uses incomplete factorisations with partial
+ * fill-in); in the natural order the triangular solves of ILU(0) form long
+ * dependency chains, while after a multicolour ordering the rows of one colour
+ * depend only on rows of earlier colours.
+ *
+ * Graph: vertices = rows of M, an edge {i, j} (i != j) wherever M_ij or M_ji
+ * is stored.  Priority of vertex v: the SplitMix64 finaliser (Steele, Lea &
+ * Flood 2014) of v + 1, a bijection on 64-bit integers, so no two vertices
+ * tie.  Colouring (Jones & Plassmann 1993): every vertex takes the smallest
+ * colour not used by its neighbours of higher priority; computed here by
+ * visiting the vertices in decreasing priority and giving each the smallest
+ * colour its already coloured neighbours do not use, which is the same
+ * colouring.  Ordering: rows sorted by (colour, row index). */
+static uint64_t orc_priority(int32_t v)
+{
+    uint64_t z = ((uint64_t)v + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+typedef struct { uint64_t pri; int32_t v; } orc_pv;
+
+static int cmp_pri_desc(const void* a, const void* b)
+{
+    const orc_pv* x = (const orc_pv*)a;
+    const orc_pv* y = (const orc_pv*)b;
+    return x->pri < y->pri ? 1 : (x->pri > y->pri ? -1 : 0);
+}
+
+ORC_EXPORT int orc_colour_order(const orc_csr* M, int32_t* colour, int32_t* perm, int32_t* ncolours)
+{
+    const int32_t n = M->nrows;
+    orc_ocsr T = {0};
+    if (csr_transpose(M, &T)) { orc_free_csr(&T); return -1; }
+    orc_pv* order = (orc_pv*)malloc((size_t)(n ? n : 1) * sizeof(orc_pv));
+    int32_t* stamp = (int32_t*)malloc((size_t)(n + 2) * sizeof(int32_t));
+    if (!order || !stamp) { free(order); free(stamp); orc_free_csr(&T); return -1; }
+    for (int32_t v = 0; v < n; ++v) { order[v].pri = orc_priority(v); order[v].v = v; colour[v] = -1; }
+    qsort(order, (size_t)n, sizeof(orc_pv), cmp_pri_desc);
+    for (int32_t c = 0; c < n + 2; ++c) stamp[c] = -1;
+    int32_t ncol = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        const int32_t v = order[k].v;
+        /* colours of the neighbours coloured so far (those of higher priority) */
+        for (int64_t p = M->rowptr[v]; p < M->rowptr[v + 1]; ++p) {
+            int32_t u = M->col[p];
+            if (u != v && colour[u] >= 0) stamp[colour[u]] = v;
+        }
+        for (int64_t p = T.rowptr[v]; p < T.rowptr[v + 1]; ++p) {
+            int32_t u = T.col[p];
+            if (u != v && colour[u] >= 0) stamp[colour[u]] = v;
+        }
+        int32_t c = 0;
+        while (stamp[c] == v) ++c;
+        colour[v] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    /* rows sorted by (colour, index): counting sort, stable in the index */
+    int64_t* start = (int64_t*)calloc((size_t)ncol + 1, sizeof(int64_t));
+    if (!start) { free(order); free(stamp); orc_free_csr(&T); return -1; }
+    for (int32_t v = 0; v < n; ++v) start[colour[v] + 1]++;
+    for (int32_t c = 0; c < ncol; ++c) start[c + 1] += start[c];
+    for (int32_t v = 0; v < n; ++v) perm[start[colour[v]]++] = v;
+    *ncolours = ncol;
+    free(start);
+    free(order);
+    free(stamp);
+    orc_free_csr(&T);
+    return 0;
+}
+
+/* P M P^T: row k is row perm[k] of M with every column j renamed to its
+ * position in perm, the columns of each row sorted ascending. */
+ORC_EXPORT int orc_permute(const orc_csr* M, const int32_t* perm, orc_ocsr* out)
+{
+    const int32_t n = M->nrows;
+    const int64_t nnz = M->rowptr[n];
+    int32_t* iperm = (int32_t*)malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+    out->nrows = n;
+    out->ncols = n;
+    out->nnz = nnz;
+    out->rowptr = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
+    out->col = (int32_t*)malloc((size_t)(nnz ? nnz : 1) * sizeof(int32_t));
+    out->val = (double*)malloc((size_t)(nnz ? nnz : 1) * sizeof(double));
+    if (!iperm || !out->rowptr || !out->col || !out->val) { free(iperm); return -1; }
+    for (int32_t k = 0; k < n; ++k) iperm[perm[k]] = k;
+    out->rowptr[0] = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        const int32_t r = perm[k];
+        int64_t q = out->rowptr[k];
+        for (int64_t p = M->rowptr[r]; p < M->rowptr[r + 1]; ++p, ++q) {
+            /* insertion into the sorted row */
+            int32_t c = iperm[M->col[p]];
+            double v = M->val[p];
+            int64_t j = q;
+            while (j > out->rowptr[k] && out->col[j - 1] > c) {
+                out->col[j] = out->col[j - 1];
+                out->val[j] = out->val[j - 1];
+                --j;
+            }
+            out->col[j] = c;
+            out->val[j] = v;
+        }
+        out->rowptr[k + 1] = q;
+    }
+    free(iperm);
+    return 0;
 }
 
 ORC_EXPORT int orc_prec_sizeof(void) { return (int)sizeof(orc_prec); }

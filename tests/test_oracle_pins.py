@@ -547,3 +547,101 @@ def test_local_solves_do_not_depend_on_thread_count():
     finally:
         O.set_threads(1)
     assert np.array_equal(x1, x4) and np.array_equal(g1, g4)
+
+
+# ------------------------------------------------ multicolour ordering
+_M64 = (1 << 64) - 1
+
+
+def _splitmix_finaliser(v):
+    """SplitMix64 finaliser of v + 1 (Steele, Lea & Flood 2014), retyped here
+    from its published definition in Python integers."""
+    z = ((v + 1) * 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def _ordering_cases():
+    s = W.config2(7)
+    q = O.qsets("nbr", s.A, s.B, s.C)
+    x, _ = O.local_solves(s.A, s.B, s.C, *q)
+    S = O.schur(0, s.A, s.C, s.D, *q, x)
+    c3 = W.config3(12, 10, 6)
+    q3 = O.qsets("thresh", c3.A, c3.B, c3.C, 0.05)
+    x3, _ = O.local_solves(c3.A, c3.B, c3.C, *q3)
+    S3 = O.schur(0, c3.A, c3.C, c3.D, *q3, x3)
+    return [("A full-tensor", s.A.to_scipy()), ("S~ full-tensor", S.to_scipy()),
+            ("A channelised", c3.A.to_scipy()), ("S~ channelised", S3.to_scipy())]
+
+
+def test_multicolour_ordering_is_the_jones_plassmann_colouring():
+    """Every vertex of the graph of M + M^T has the smallest colour that none of
+    its higher-priority neighbours has (the fixed point of Jones & Plassmann's
+    parallel colouring), which makes the colouring proper; the ordering sorts
+    rows by (colour, index)."""
+    import scipy.sparse as sp
+    for name, M in _ordering_cases():
+        colour, perm, nc = O.colour_order(M)
+        G = ((abs(M) + abs(M.T)) != 0).astype(np.int8).tocsr()
+        n = M.shape[0]
+        pri = [_splitmix_finaliser(v) for v in range(n)]
+        for v in range(n):
+            nb = [u for u in G.indices[G.indptr[v]:G.indptr[v + 1]] if u != v]
+            assert all(colour[u] != colour[v] for u in nb), (name, v)
+            higher = {int(colour[u]) for u in nb if pri[u] > pri[v]}
+            mex = 0
+            while mex in higher:
+                mex += 1
+            assert colour[v] == mex, (name, v)
+        assert nc == colour.max() + 1
+        assert np.array_equal(perm, np.lexsort((np.arange(n), colour)))
+        # no edge inside a colour: the lower triangle of P M P^T has at most
+        # nc dependency levels (longest chain of strictly decreasing columns)
+        Pm = sp.csr_matrix(M)[perm][:, perm].tocsr()
+        L = sp.tril(Pm, -1).tocsr()
+        lev = np.zeros(n, int)
+        for i in range(n):
+            js = L.indices[L.indptr[i]:L.indptr[i + 1]]
+            lev[i] = lev[js].max() + 1 if len(js) else 0
+        assert lev.max() + 1 <= nc
+
+
+def test_permute_matches_scipy_fancy_indexing():
+    for name, M in _ordering_cases():
+        _, perm, _ = O.colour_order(M)
+        Pm = O.permute(M, perm)
+        ref = M.tocsr()[perm][:, perm].tocsr()
+        ref.sort_indices()
+        assert np.array_equal(Pm.rowptr, ref.indptr) and np.array_equal(Pm.col, ref.indices), name
+        assert np.array_equal(Pm.val, ref.data), name
+
+
+def test_ordered_apply_is_the_natural_apply_of_the_permuted_system():
+    """With orderings P_a (faces) and P_s (cells), the preconditioner applied to
+    r equals the natural-order preconditioner of the permuted system
+    [P_a A P_a^T, P_a B P_s^T; P_s C P_a^T, P_s D P_s^T] (blocks permuted by
+    scipy) applied to the permuted r, permuted back."""
+    s = W.config2(7)
+    q = O.qsets("nbr", s.A, s.B, s.C)
+    x, _ = O.local_solves(s.A, s.B, s.C, *q)
+    S = O.schur(0, s.A, s.C, s.D, *q, x)
+    _, pa, _ = O.colour_order(s.A)
+    _, ps, _ = O.colour_order(S)
+    r = W.Stream(77).normal(s.n)
+    for variant in (0, 1):
+        z = O.Prec(s.A, s.B, s.C, s.D, S=S, variant=variant, aperm=pa, sperm=ps).apply(r)
+        A, B, C_, D, Ss = (M.to_scipy().tocsr() for M in (s.A, s.B, s.C, s.D, S))
+        Pq = O.Prec(A[pa][:, pa], B[pa][:, ps], C_[ps][:, pa], D[ps][:, ps], S=Ss[ps][:, ps], variant=variant)
+        zq = Pq.apply(np.concatenate([r[:s.Nf][pa], r[s.Nf:][ps]]))
+        zr = np.empty_like(zq)
+        zr[pa] = zq[:s.Nf]
+        zr[s.Nf + ps] = zq[s.Nf:]
+        assert np.abs(z - zr).max() <= 1e-12 * np.abs(zr).max(), variant
+
+
+def test_ordered_preconditioner_fgmres_converges():
+    for sysd, mode in ((W.config2(10), "nbr"), (W.config3(16, 12, 6), "thresh")):
+        for ordering in (1, 2):
+            r = O.edfa_pipeline(sysd, mode=mode, ordering=ordering)
+            assert r["converged"] and r["true_rel"] <= 1e-8, (mode, ordering, r["true_rel"])
