@@ -109,6 +109,15 @@ typedef struct {
                                tau_filt times the Euclidean norm of the vector it belongs to, and
                                diagonal entries of H~ and S~ are always kept */
     double tau_filt;        /* filtration tolerance (>= 0; 0 keeps every entry) */
+    int32_t ordering;       /* ordering of the inner ILU(0) factorisations (the paper leaves the inner
+                               preconditioners open, Sec. 3): 0 = natural (default); 1 = multicolour
+                               ordering of S~; 2 = multicolour orderings of A~ and S~.  Colouring of the
+                               graph of M + M^T by Jones & Plassmann with the SplitMix64 finaliser of
+                               row + 1 as priority, rows sorted by (colour, row); every triangular sweep
+                               of an ordered factor then has at most as many dependency levels as
+                               colours.  With an ordering of S~ its sweeps always run on all SMs (the
+                               single-cluster sweeps of sweep_mode 0 and 2 are for deep natural-order
+                               factors); an ordered A~ is never chain-decomposed */
 } edfa_options;
 
 /* Filtration of the approximate Schur complement (Algorithms 1 and 2). */
@@ -176,6 +185,22 @@ typedef struct {
     const int32_t* s_col;
     const double* s_val;  /* S~ values (FP64 path) */
     const float* s_val_f32;
+    /* orderings of the inner factorisations (edfa_options.ordering); perm[k] is
+       the face / cell at ordered position k, NULL in the natural order */
+    int32_t a_ncolours, s_ncolours;
+    const int32_t* a_perm;   /* [N_f] */
+    const int32_t* s_perm;   /* [N_e] */
+    /* the ILU(0) factors as computed (of the ordered matrices when ordered):
+       pattern and L\U values, L unit lower (its diagonal not stored) */
+    int64_t fa_nnz, fs_nnz;
+    const int64_t* fa_rowptr;
+    const int32_t* fa_col;
+    const double* fa_lu;
+    const float* fa_lu_f32;
+    const int64_t* fs_rowptr;
+    const int32_t* fs_col;
+    const double* fs_lu;
+    const float* fs_lu_f32;
 } edfa_view;
 
 EDFA_API void edfa_default_options(edfa_options* opt);
@@ -331,6 +356,15 @@ EDFA_API int edfa_qsets_noalloc(const edfa_csr* A, const edfa_csr* B, const edfa
  * `stream`; allocates and frees a few hundred bytes of device memory; must not
  * run concurrently with other work of this library on the device. */
 EDFA_API int edfa_selftest_wait_timeout(float* ms, edfa_stream stream);
+
+/* Measurement utility (no counterpart in the paper): the device's fused
+ * multiply-add rate, precision 0 = FP64, 1 = FP32, in FMA per second, from one
+ * timed launch of a kernel running eight independent FMA chains per thread on
+ * every SM (about 30 ms).  It is the ALU denominator for kernels bound by
+ * arithmetic rather than memory, such as the dense per-cell factorisations of
+ * the local solves.  Synchronises `stream`; allocates and frees 8 bytes of
+ * device memory. */
+EDFA_API int edfa_probe_fma_rate(int32_t precision, double* fma_per_s, edfa_stream stream);
 
 /* Number of CUDA kernels this library has launched in this process. */
 EDFA_API int64_t edfa_launch_count(void);

@@ -45,7 +45,7 @@ class Options(C.Structure):
                 ("qidx", C.c_void_p), ("schur_form", C.c_int32), ("variant", C.c_int32),
                 ("precision", C.c_int32), ("warps_per_block", C.c_int32),
                 ("sweep_warps_per_sm", C.c_int32), ("sweep_mode", C.c_int32),
-                ("filtration", C.c_int32), ("tau_filt", C.c_double)]
+                ("filtration", C.c_int32), ("tau_filt", C.c_double), ("ordering", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -69,14 +69,19 @@ class View(C.Structure):
     _fields_ = [("Nf", C.c_int32), ("Ne", C.c_int32), ("qptr", C.c_void_p), ("qidx", C.c_void_p),
                 ("xval", C.c_void_p), ("gval", C.c_void_p), ("xval_f32", C.c_void_p),
                 ("s_nnz", C.c_int64), ("s_rowptr", C.c_void_p), ("s_col", C.c_void_p),
-                ("s_val", C.c_void_p), ("s_val_f32", C.c_void_p)]
+                ("s_val", C.c_void_p), ("s_val_f32", C.c_void_p),
+                ("a_ncolours", C.c_int32), ("s_ncolours", C.c_int32), ("a_perm", C.c_void_p),
+                ("s_perm", C.c_void_p), ("fa_nnz", C.c_int64), ("fs_nnz", C.c_int64),
+                ("fa_rowptr", C.c_void_p), ("fa_col", C.c_void_p), ("fa_lu", C.c_void_p),
+                ("fa_lu_f32", C.c_void_p), ("fs_rowptr", C.c_void_p), ("fs_col", C.c_void_p),
+                ("fs_lu", C.c_void_p), ("fs_lu_f32", C.c_void_p)]
 
 
 _lib = None
 EXPORTS = ("edfa_default_options", "edfa_build", "edfa_setup", "edfa_apply", "edfa_matvec",
            "edfa_solve", "edfa_history", "edfa_get_view", "edfa_get_stats", "edfa_set_profiling",
            "edfa_launch_count", "edfa_qsets_noalloc", "edfa_build_adjoint", "edfa_grad_logk",
-           "edfa_solve_batched", "edfa_solve_bicgstab", "edfa_selftest_wait_timeout",
+           "edfa_solve_batched", "edfa_solve_bicgstab", "edfa_selftest_wait_timeout", "edfa_probe_fma_rate",
            "edfa_free", "edfa_strerror",
            "edfa_last_error_detail")
 
@@ -114,6 +119,8 @@ def lib(build_if_missing: bool = True):
         L.edfa_qsets_noalloc.argtypes = [P(Csr), P(Csr), P(Csr), C.c_int32, C.c_double, vp, vp, C.c_int64,
                                          P(C.c_int64), vp]
         L.edfa_qsets_noalloc.restype = C.c_int
+        L.edfa_probe_fma_rate.argtypes = [C.c_int32, P(C.c_double), vp]
+        L.edfa_probe_fma_rate.restype = C.c_int
         L.edfa_selftest_wait_timeout.argtypes = [P(C.c_float), vp]
         L.edfa_selftest_wait_timeout.restype = C.c_int
         L.edfa_build_adjoint.argtypes = [P(vp), vp, vp]
@@ -208,6 +215,15 @@ def selftest_wait_timeout(stream=None):
     return rc, int(lib().edfa_last_error_detail()), float(ms.value)
 
 
+def probe_fma_rate(precision: int = 0, stream=None) -> float:
+    """edfa_probe_fma_rate: FMA per second of the device (0 = FP64, 1 = FP32)."""
+    r = C.c_double(0)
+    rc = lib().edfa_probe_fma_rate(int(precision), C.byref(r), C.c_void_p(_stream(stream)))
+    if rc != EDFA_OK:
+        raise EdfaError(rc, "edfa_probe_fma_rate")
+    return float(r.value)
+
+
 def launch_count() -> int:
     return int(lib().edfa_launch_count())
 
@@ -244,7 +260,7 @@ class Edfa:
 
     def __init__(self, A, B, C_, D, Nf: int, Ne: int, qmode="own", thresh=0.05, n_add=1, n_ent=4,
                  it_max=100, qsets=None, schur_form=0, variant=0, precision=0, warps_per_block=0,
-                 sweep_warps_per_sm=0, sweep_mode=0, filtration="none", tau_filt=0.0, stream=None):
+                 sweep_warps_per_sm=0, sweep_mode=0, filtration="none", tau_filt=0.0, ordering=0, stream=None):
         self._keep = [A, B, C_, D]
         self.Nf, self.Ne = int(Nf), int(Ne)
         opt = Options()
@@ -264,6 +280,7 @@ class Edfa:
         opt.sweep_mode = int(sweep_mode)
         opt.filtration = FILTERS[filtration] if isinstance(filtration, str) else int(filtration)
         opt.tau_filt = float(tau_filt)
+        opt.ordering = int(ordering)
         self.opt = opt
         self._D = D
         self.h = edfa_build(csr(*A, self.Nf), csr(*B, self.Ne), csr(*C_, self.Nf), csr(*D, self.Ne), opt,
@@ -394,6 +411,33 @@ class Edfa:
         out["s_col"] = wrap(v.s_col, st.s_nnz, torch.int32)
         out["s_val"] = wrap(v.s_val, st.s_nnz, torch.float64) if v.s_val else wrap(v.s_val_f32, st.s_nnz,
                                                                                      torch.float32)
+        return out
+
+    def factors(self):
+        """Copies of the orderings and of the ILU(0) factors as computed (of the
+        ordered matrices when an ordering is on)."""
+        import torch
+        v = self.view()
+        dev = torch.device("cuda", torch.cuda.current_device())
+
+        class _Dev:
+            def __init__(self, ptr, n, typestr):
+                self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                                 "version": 3, "strides": None}
+
+        def wrap(ptr, n, ts):
+            if not ptr or n == 0:
+                return None
+            return torch.as_tensor(_Dev(ptr, int(n), ts), device=dev).clone()
+
+        torch.cuda.synchronize()
+        out = dict(a_ncolours=int(v.a_ncolours), s_ncolours=int(v.s_ncolours),
+                   a_perm=wrap(v.a_perm, self.Nf, "<i4"), s_perm=wrap(v.s_perm, self.Ne, "<i4"))
+        for k, n, nnz in (("fa", self.Nf, v.fa_nnz), ("fs", self.Ne, v.fs_nnz)):
+            out[k + "_rowptr"] = wrap(getattr(v, k + "_rowptr"), n + 1, "<i8")
+            out[k + "_col"] = wrap(getattr(v, k + "_col"), nnz, "<i4")
+            lu = getattr(v, k + "_lu")
+            out[k + "_lu"] = wrap(lu, nnz, "<f8") if lu else wrap(getattr(v, k + "_lu_f32"), nnz, "<f4")
         return out
 
     def close(self):

@@ -155,6 +155,7 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     if (o.filtration < EDFA_FILT_NONE || o.filtration > EDFA_FILT_POST_S || !(o.tau_filt >= 0.0) ||
         !std::isfinite(o.tau_filt))
         return EDFA_ERR_INVALID;
+    if (o.ordering < 0 || o.ordering > 2) return EDFA_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
 
     edfa_handle_s* h = new (std::nothrow) edfa_handle_s();
@@ -207,10 +208,14 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     TRY(prefilter(h, s));
     TRY(build_schur(h, s));
     cudaEventRecord(h->ev[4], s);
-    TRY(factor_plan(h, h->fa, Nf, A->nnz, A->rowptr, A->col, s));
-    if (o.sweep_mode != 1) TRY(chain_plan_build(h, h->fa, s));
-    TRY(factor_numeric(h, h->fa, A->val, h->a32, s));
-    TRY(chain_plan_values(h, h->fa, s));
+    if (o.ordering == 2) {
+        TRY(order_a_factor(h, s));
+    } else {
+        TRY(factor_plan(h, h->fa, Nf, A->nnz, A->rowptr, A->col, s));
+        if (o.sweep_mode != 1) TRY(chain_plan_build(h, h->fa, s));
+        TRY(factor_numeric(h, h->fa, A->val, h->a32, s));
+        TRY(chain_plan_values(h, h->fa, s));
+    }
     cudaEventRecord(h->ev[5], s);
     TRY(check_err(h, s));
 
@@ -221,7 +226,7 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     TRY(stage2_pattern(h, s));
     TRY(stage2_symbolic(h, s));
     cudaEventRecord(h->ev[9], s);
-    TRY(factor_numeric(h, h->fs, h->sf_val, h->sf_val32, s));
+    TRY(stage2_numeric(h, s));
     cudaEventRecord(h->ev[10], s);
     TRY(cluster_plan_fill(h, s));
     cudaEventRecord(h->ev[7], s);
@@ -275,7 +280,7 @@ int edfa_setup(edfa_handle h, const edfa_csr* D, edfa_stream stream)
     if (!rc && replan) rc = stage2_pattern(h, s);
     if (!rc && replan) rc = stage2_symbolic(h, s);
     cudaEventRecord(h->ev[9], s);
-    if (!rc) rc = factor_numeric(h, h->fs, h->sf_val, h->sf_val32, s);
+    if (!rc) rc = stage2_numeric(h, s);
     cudaEventRecord(h->ev[10], s);
     if (!rc) rc = cluster_plan_fill(h, s);
     cudaEventRecord(h->ev[7], s);
@@ -582,6 +587,20 @@ int edfa_get_view(edfa_handle h, edfa_view* v)
     v->s_col = h->sf_col;
     v->s_val = h->sf_val;
     v->s_val_f32 = h->sf_val32;
+    v->a_ncolours = h->oa.on ? h->oa.ncolours : 0;
+    v->s_ncolours = h->os.on ? h->os.ncolours : 0;
+    v->a_perm = h->oa.on ? h->oa.perm : nullptr;
+    v->s_perm = h->os.on ? h->os.perm : nullptr;
+    v->fa_nnz = h->fa.nnz;
+    v->fa_rowptr = h->fa.rowptr;
+    v->fa_col = h->fa.col;
+    v->fa_lu = h->fa.lu64;
+    v->fa_lu_f32 = h->fa.lu32;
+    v->fs_nnz = h->fs.nnz;
+    v->fs_rowptr = h->fs.rowptr;
+    v->fs_col = h->fs.col;
+    v->fs_lu = h->fs.lu64;
+    v->fs_lu_f32 = h->fs.lu32;
     return EDFA_OK;
 }
 

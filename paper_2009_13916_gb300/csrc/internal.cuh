@@ -178,6 +178,26 @@ struct ClusterPlan {
     void* ovf_val = nullptr;
 };
 
+// A multicolour ordering of the rows of a factorised matrix (k_order.cu).
+struct Ordering {
+    int on = 0;
+    int32_t n = 0, ncolours = 0;
+    int32_t* perm = nullptr;   // [n] ordered position -> original row
+    int32_t* iperm = nullptr;  // [n] original row -> ordered position
+    std::vector<int32_t> cstart;  // host: first ordered row of every colour, [ncolours + 1]
+};
+
+// An ordered copy P M Q^T of a CSR matrix: pattern, the position in M of every
+// entry, and the gathered values (FP64 and/or FP32).
+struct OrderedCsr {
+    int64_t nnz = 0;
+    int64_t* ptr = nullptr;
+    int32_t* col = nullptr;
+    int64_t* map = nullptr;
+    double* v64 = nullptr;
+    float* v32 = nullptr;
+};
+
 }  // namespace edfa
 
 struct edfa_handle_s {
@@ -229,6 +249,11 @@ struct edfa_handle_s {
     int64_t* sf_cnt = nullptr;  // [Ne+1] row counts of the filtered copy
     // ILU(0) factors
     edfa::Factor fa, fs;
+    // optional multicolour orderings of the factorised A~ (faces) and S~
+    // (cells), the ordered matrices and the couplings in the ordered numbering
+    // (P_s C P_a^T, P_a B P_s^T)
+    edfa::Ordering oa, os;
+    edfa::OrderedCsr ao, so, co, bo;
     edfa::ClusterPlan cp;
     // sweep synchronisation
     int* flags = nullptr;          // [max(Nf, Ne)] completion epochs
@@ -319,6 +344,15 @@ template <class T>
 int s_cluster_solve(edfa_handle_s* h, const double* rp, const int64_t* mptr, const int32_t* mcol, const T* mval,
                     const T* mv, T* out, cudaStream_t s, cudaEvent_t* pe);
 int matvec(edfa_handle_s* h, const double* x, double* y, cudaStream_t s);
+// multicolour orderings (k_order.cu)
+int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr, const int32_t* col, int64_t nnz,
+                 cudaStream_t s);
+int order_matrix(edfa_handle_s* h, OrderedCsr& m, int32_t nrows, const int64_t* rowptr, const int32_t* col,
+                 int64_t nnz, const int32_t* rperm, const int32_t* cmap, cudaStream_t s);
+int order_values(edfa_handle_s* h, OrderedCsr& m, const double* src64, const float* src32, cudaStream_t s);
+int order_stage2_symbolic(edfa_handle_s* h, cudaStream_t s);
+int order_a_factor(edfa_handle_s* h, cudaStream_t s);
+int stage2_numeric(edfa_handle_s* h, cudaStream_t s);
 int to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
 int to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t s);
 

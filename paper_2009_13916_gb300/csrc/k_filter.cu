@@ -313,8 +313,13 @@ int stage2_symbolic(edfa_handle_s* h, cudaStream_t s)
         h->cp = ClusterPlan{};
     }
     const size_t mark = h->owned.size();
-    int rc = factor_plan(h, h->fs, h->Ne, h->sf_nnz, h->sf_ptr, h->sf_col, s);
-    if (!rc) rc = cluster_plan_build(h, s);
+    int rc;
+    if (h->opt.ordering >= 1) {
+        rc = order_stage2_symbolic(h, s);
+    } else {
+        rc = factor_plan(h, h->fs, h->Ne, h->sf_nnz, h->sf_ptr, h->sf_col, s);
+        if (!rc) rc = cluster_plan_build(h, s);
+    }
     if (replan) {
         for (size_t k = mark; k < h->owned.size(); ++k) h->owned_s2.push_back(h->owned[k]);
         h->owned.resize(mark);

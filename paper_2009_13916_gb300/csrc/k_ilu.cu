@@ -949,6 +949,137 @@ static int launch_sweep(edfa_handle_s* h, const Factor& f, const TB* base, const
     return EDFA_OK;
 }
 
+// ------------------------------------------------------------ multicolour sweeps
+// Sweep of an ordered factor, one launch per colour: the rows of a colour are
+// contiguous in the ordered numbering and depend only on rows of earlier
+// colours (forward) or later colours (backward), which earlier launches have
+// written, so a launch is a plain row-parallel pass (no tickets, no polling).
+//   FWD=1: out_i = rhs_i - sum_{j<i} L_ij out_j
+//   FWD=0: out_i = dinv_i (rhs_i - sum_{j>i} U_ij out_j)
+// rhs_i = base_{bperm[i]} - sum_p M_ip v_p (bperm, the coupling M: optional);
+// with sperm the result is also written, as FP64, to scat[sperm[i]] (the
+// natural numbering).  LPR lanes per row, four entries per lane in flight,
+// rows of a colour in order, the factor entries streamed once; the grid is one
+// resident wave, since a colour holds a few hundred thousand rows at most.
+constexpr int kMcThreads = 256;
+
+template <class T, class TB, class TO, int FWD, int LPR>
+__global__ void __launch_bounds__(kMcThreads)
+k_mc_sweep(int32_t r0, int32_t r1, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+           const T* __restrict__ lu, const int64_t* __restrict__ diag, const T* __restrict__ dinv,
+           const TB* __restrict__ base, const int32_t* __restrict__ bperm, const int64_t* __restrict__ mptr,
+           const int32_t* __restrict__ mcol, const T* __restrict__ mval, const TO* __restrict__ mv, TO* out,
+           const int32_t* __restrict__ sperm, double* scat)
+{
+    constexpr int RPW = 32 / LPR;
+    constexpr int U = 4;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / LPR, gl = lane % LPR;
+    const int64_t warp = ((int64_t)blockIdx.x * kMcThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kMcThreads) >> 5;
+    for (int64_t i0 = r0 + warp * RPW; i0 < r1; i0 += nwarps * RPW) {
+        const int64_t i = i0 + g;
+        const bool live = i < r1;
+        T acc = T(0), bi = T(0), di = T(1);
+        if (live) {
+            // the row's own data first (independent loads)
+            const int64_t lo = FWD ? rowptr[i] : diag[i] + 1;
+            const int64_t hi = FWD ? diag[i] : rowptr[i + 1];
+            bi = (T)to_d(base[bperm ? bperm[i] : i]);
+            if (!FWD) di = dinv[i];
+            int64_t mb = 0, me = 0;
+            if (mptr) { mb = mptr[i]; me = mptr[i + 1]; }
+            for (int64_t p0 = lo; p0 < hi; p0 += U * LPR) {
+                int c[U];
+                T w[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t p = p0 + gl + u * LPR;
+                    c[u] = p < hi ? col[p] : -1;
+                    w[u] = p < hi ? lu[p] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (c[u] >= 0) acc = fma(w[u], (T)out[c[u]], acc);
+            }
+            for (int64_t p0 = mb; p0 < me; p0 += U * LPR) {
+                int c[U];
+                T w[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t p = p0 + gl + u * LPR;
+                    c[u] = p < me ? mcol[p] : -1;
+                    w[u] = p < me ? mval[p] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (c[u] >= 0) acc = fma(w[u], (T)mv[c[u]], acc);
+            }
+        }
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (live && gl == 0) {
+            T r = bi - acc;
+            if (!FWD) r *= di;
+            out[i] = (TO)r;
+            if (sperm) scat[sperm[i]] = (double)r;
+        }
+    }
+}
+
+template <class T, class TB, class TO, int FWD, int LPR>
+static void mc_launch(edfa_handle_s* h, const Factor& f, const Ordering& o, const T* lu, const T* dinv,
+                      const TB* base, const int32_t* bperm, const int64_t* mptr, const int32_t* mcol, const T* mval,
+                      const TO* mv, TO* out, const int32_t* sperm, double* scat, cudaStream_t s)
+{
+    auto fn = k_mc_sweep<T, TB, TO, FWD, LPR>;
+    static thread_local int per_dev = -1, per_sm = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != per_dev) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMcThreads, 0);
+        if (per_sm < 1) per_sm = 1;
+        per_dev = dev;
+    }
+    constexpr int RPW = 32 / LPR;
+    for (int k = 0; k < o.ncolours; ++k) {
+        const int c = FWD ? k : o.ncolours - 1 - k;
+        const int32_t r0 = o.cstart[c], r1 = o.cstart[c + 1];
+        if (r1 <= r0) continue;
+        int64_t blocks = ((int64_t)(r1 - r0) + RPW * (kMcThreads / 32) - 1) / (RPW * (kMcThreads / 32));
+        const int64_t cap = (int64_t)h->nsm * per_sm;
+        if (blocks > cap) blocks = cap;
+        (edfa::count_launch(), fn<<<(unsigned)blocks, kMcThreads, 0, s>>>(r0, r1, f.rowptr, f.col, lu, f.diag, dinv,
+                                                                          base, bperm, mptr, mcol, mval, mv, out,
+                                                                          sperm, scat));
+    }
+}
+
+// lanes per row from the average length of the rows' halves plus the coupling
+template <class T, class TB, class TO, int FWD>
+static int mc_sweep(edfa_handle_s* h, const Factor& f, const Ordering& o, const TB* base, const int32_t* bperm,
+                    const int64_t* mptr, const int32_t* mcol, const T* mval, int64_t mnnz, const TO* mv, TO* out,
+                    const int32_t* sperm, double* scat, cudaStream_t s)
+{
+    if (f.n == 0) return EDFA_OK;
+    const T* lu = nullptr;
+    const T* dinv = nullptr;
+    if constexpr (sizeof(T) == 8) { lu = (const T*)f.lu64; dinv = (const T*)f.dinv64; }
+    else { lu = (const T*)f.lu32; dinv = (const T*)f.dinv32; }
+    const double avg = ((double)(f.nnz - f.n) / 2.0 + (mptr ? (double)mnnz : 0.0)) / (double)f.n;
+    cudaEvent_t* pe = prof_begin(h, (&f == &h->fs ? 2 : 0) + (FWD ? 0 : 1), s);
+    if (avg <= 4.0)
+        mc_launch<T, TB, TO, FWD, 1>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm, scat, s);
+    else if (avg <= 12.0)
+        mc_launch<T, TB, TO, FWD, 2>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm, scat, s);
+    else if (avg <= 32.0)
+        mc_launch<T, TB, TO, FWD, 4>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm, scat, s);
+    else
+        mc_launch<T, TB, TO, FWD, 8>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm, scat, s);
+    if (pe) cudaEventRecord(pe[1], s);
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
 // sweep of the A~ factor: chain-decomposed when its DAG collapses to a few
 // phases of chains (k_chain.cu), else the level-scheduled sync-free sweep
 template <class T, class TB, class TO, int FWD>
@@ -971,9 +1102,64 @@ static int a_sweep(edfa_handle_s* h, const TB* base, const int64_t* mptr, const 
 //   z_p  = S~^{-1} (r_p - C y)           (C y fused into the L sweep of S~)
 //   z_pi = A~^{-1} (r_pi - B z_p)        (B z_p fused into the L sweep of A)
 // variant 1 (upper block triangular): z_p = S~^{-1} r_p, then z_pi as above.
+// The same application with ordered inner factors (edfa_options.ordering):
+// the ILU(0) factors of P_a A P_a^T (P_a = identity without an ordering of
+// A~) and P_s S~ P_s^T; the right-hand sides are read through the orderings,
+// C and B enter as P_s C P_a^T and P_a B P_s^T, and the last sweep of each
+// block writes its result back to the natural numbering:
+//   y    = A_o^{-1} P_a r_pi
+//   z_o  = S_o^{-1} (P_s r_p - C_o y),      z_p  = P_s^T z_o
+//   v    = A_o^{-1} (P_a r_pi - B_o z_o),   z_pi = P_a^T v
+template <class T>
+static int apply_ordered(edfa_handle_s* h, const double* r, double* z, cudaStream_t s)
+{
+    const int32_t Nf = h->Nf;
+    const bool oa = h->oa.on != 0;
+    const int32_t* ap = oa ? h->oa.perm : nullptr;
+    const int32_t* sp = h->os.perm;
+    T* u1 = (T*)h->tmp1;
+    T* u2 = (T*)h->tmp2;
+    T* zo = (T*)h->tmp3;
+    const T* cval;
+    const T* bval;
+    if constexpr (sizeof(T) == 8) { cval = (const T*)h->co.v64; bval = (const T*)h->bo.v64; }
+    else { cval = (const T*)h->co.v32; bval = (const T*)h->bo.v32; }
+    const T* none = nullptr;
+    int rc;
+    if (h->opt.variant == 0) {
+        rc = oa ? mc_sweep<T, double, T, 1>(h, h->fa, h->oa, r, ap, nullptr, nullptr, none, 0, none, u2, nullptr,
+                                           nullptr, s)
+                : a_sweep<T, double, T, 1>(h, r, nullptr, nullptr, none, none, u2, s);
+        if (rc) return rc;
+        rc = oa ? mc_sweep<T, T, T, 0>(h, h->fa, h->oa, (const T*)u2, nullptr, nullptr, nullptr, none, 0, none, u1,
+                                      nullptr, nullptr, s)
+                : a_sweep<T, T, T, 0>(h, u2, nullptr, nullptr, none, none, u1, s);
+        if (rc) return rc;
+        rc = mc_sweep<T, double, T, 1>(h, h->fs, h->os, r + Nf, sp, h->co.ptr, h->co.col, cval, h->co.nnz,
+                                       (const T*)u1, u2, nullptr, nullptr, s);
+    } else {
+        rc = mc_sweep<T, double, T, 1>(h, h->fs, h->os, r + Nf, sp, nullptr, nullptr, none, 0, none, u2, nullptr,
+                                       nullptr, s);
+    }
+    if (rc) return rc;
+    rc = mc_sweep<T, T, T, 0>(h, h->fs, h->os, (const T*)u2, nullptr, nullptr, nullptr, none, 0, none, zo, sp,
+                              z + Nf, s);
+    if (rc) return rc;
+    rc = oa ? mc_sweep<T, double, T, 1>(h, h->fa, h->oa, r, ap, h->bo.ptr, h->bo.col, bval, h->bo.nnz,
+                                       (const T*)zo, u2, nullptr, nullptr, s)
+            : a_sweep<T, double, T, 1>(h, r, h->bo.ptr, h->bo.col, bval, (const T*)zo, u2, s);
+    if (rc) return rc;
+    if (oa) rc = mc_sweep<T, T, T, 0>(h, h->fa, h->oa, (const T*)u2, nullptr, nullptr, nullptr, none, 0, none, u1, ap,
+                                      z, s);
+    else rc = a_sweep<T, T, double, 0>(h, u2, nullptr, nullptr, none, (const double*)nullptr, z, s);
+    if (rc) return rc;
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
 template <class T>
 static int apply_impl(edfa_handle_s* h, const double* r, double* z, cudaStream_t s)
 {
+    if (h->opt.ordering >= 1) return apply_ordered<T>(h, r, z, s);
     const int32_t Nf = h->Nf, Ne = h->Ne;
     const double* rpi = r;
     const double* rp = r + Nf;

@@ -1,0 +1,421 @@
+// Multicolour orderings of the inner ILU(0) factorisations (opt-in,
+// edfa_options.ordering).  The paper leaves the inner preconditioners and
+// their ordering open (Sec. 3, inner preconditioners; Sec. 4 uses incomplete
+// factorisations with partial fill-in).  In the natural order the triangular
+// solves of ILU(0) are chains of hundreds of dependency levels; after a
+// multicolour ordering the rows of one colour depend only on rows of earlier
+// colours, so a sweep has at most as many levels as there are colours.
+//
+// Colouring (Jones & Plassmann 1993) of the graph of M + M^T (an edge {i, j},
+// i != j, wherever M_ij or M_ji is stored): vertex v has priority
+// SplitMix64-finaliser(v + 1) (Steele, Lea & Flood 2014; a bijection, so no
+// ties) and takes the smallest colour not used by its neighbours of higher
+// priority.  Rounds: every uncoloured vertex whose higher-priority neighbours
+// are all coloured takes its colour; a colour, once written, is final, so
+// whatever a round reads (a final colour or "not yet") the result is that
+// fixed point, whatever the timing.  Ordering: rows sorted by (colour, index).
+// The ordered matrices P M Q^T are built once per pattern with a map to the
+// original entries, so new values only need a gather.
+#include "internal.cuh"
+
+namespace edfa {
+
+__device__ __forceinline__ unsigned long long jp_priority(int32_t v)
+{
+    unsigned long long z = ((unsigned long long)v + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ------------------------------------------------------------ transpose pattern
+__global__ void k_tp_count(int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           unsigned long long* cnt)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t p = rowptr[r]; p < rowptr[r + 1]; ++p) atomicAdd(&cnt[col[p]], 1ull);
+}
+
+__global__ void k_tp_fill(int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                          unsigned long long* cursor, int32_t* tcol)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t p = rowptr[r]; p < rowptr[r + 1]; ++p) tcol[atomicAdd(&cursor[col[p]], 1ull)] = (int32_t)r;
+}
+
+// ------------------------------------------------------------ colouring rounds
+// true when every neighbour of v (in M and M^T) with higher priority is coloured
+__device__ __forceinline__ bool jp_ready(int32_t v, unsigned long long pv, const int64_t* rp, const int32_t* cl,
+                                         const int* colour)
+{
+    for (int64_t p = rp[v]; p < rp[v + 1]; ++p) {
+        const int32_t u = cl[p];
+        if (u != v && jp_priority(u) > pv && __ldcg(colour + u) < 0) return false;
+    }
+    return true;
+}
+
+// colours of the higher-priority neighbours below 64 as a bit set
+__device__ __forceinline__ unsigned long long jp_used(int32_t v, unsigned long long pv, const int64_t* rp,
+                                                      const int32_t* cl, const int* colour, unsigned long long used)
+{
+    for (int64_t p = rp[v]; p < rp[v + 1]; ++p) {
+        const int32_t u = cl[p];
+        if (u != v && jp_priority(u) > pv) {
+            const int c = __ldcg(colour + u);
+            if (c < 64) used |= 1ull << c;
+        }
+    }
+    return used;
+}
+
+__device__ __forceinline__ bool jp_uses(int32_t v, unsigned long long pv, const int64_t* rp, const int32_t* cl,
+                                        const int* colour, int c)
+{
+    for (int64_t p = rp[v]; p < rp[v + 1]; ++p) {
+        const int32_t u = cl[p];
+        if (u != v && jp_priority(u) > pv && __ldcg(colour + u) == c) return true;
+    }
+    return false;
+}
+
+__global__ void k_jp_round(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ cl,
+                           const int64_t* __restrict__ tp, const int32_t* __restrict__ tc, int* colour,
+                           unsigned long long* remaining, int* maxcol)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = (int32_t)i;
+        if (colour[v] >= 0) continue;
+        const unsigned long long pv = jp_priority(v);
+        if (!jp_ready(v, pv, rp, cl, colour) || !jp_ready(v, pv, tp, tc, colour)) {
+            atomicAdd(remaining, 1ull);
+            continue;
+        }
+        unsigned long long used = jp_used(v, pv, rp, cl, colour, 0ull);
+        used = jp_used(v, pv, tp, tc, colour, used);
+        int c;
+        if (~used != 0ull) {
+            c = __ffsll((long long)~used) - 1;
+        } else {
+            c = 64;
+            while (jp_uses(v, pv, rp, cl, colour, c) || jp_uses(v, pv, tp, tc, colour, c)) ++c;
+        }
+        atomicMax(maxcol, c);
+        __stcg(colour + v, c);
+    }
+}
+
+// ------------------------------------------------------------ rows sorted by (colour, index)
+constexpr int kOrdChunk = 1024;  // vertices per block in the placement kernels
+constexpr int kOrdMaxColours = 256;
+
+// cnt[c * nchunks + b] = vertices of colour c in chunk b
+__global__ void __launch_bounds__(kOrdChunk) k_col_chunk_count(int32_t n, const int* colour, int ncol, int64_t nchunks,
+                                                              int64_t* cnt)
+{
+    __shared__ int h[kOrdMaxColours];
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) h[c] = 0;
+    __syncthreads();
+    const int64_t v = (int64_t)blockIdx.x * kOrdChunk + threadIdx.x;
+    if (v < n) atomicAdd(&h[colour[v]], 1);
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) cnt[(int64_t)c * nchunks + blockIdx.x] = h[c];
+}
+
+// every vertex goes to position offset(colour, chunk) + (vertices of its colour
+// before it in the chunk); the rank inside the chunk is counted per warp
+// (matching lanes before it) plus the earlier warps' counts of that colour
+__global__ void __launch_bounds__(kOrdChunk) k_col_chunk_place(int32_t n, const int* colour, int ncol, int64_t nchunks,
+                                                              const int64_t* off, int32_t* perm, int32_t* iperm)
+{
+    __shared__ int wc[kOrdChunk / 32][kOrdMaxColours];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < (kOrdChunk / 32) * ncol; k += blockDim.x) wc[k / ncol][k % ncol] = 0;
+    __syncthreads();
+    const int64_t v = (int64_t)blockIdx.x * kOrdChunk + threadIdx.x;
+    const bool live = v < n;
+    const int c = live ? colour[v] : -1 - lane;  // distinct dummies never match a colour
+    const unsigned same = __match_any_sync(0xffffffffu, c);
+    const int rank = __popc(same & ((1u << lane) - 1u));
+    if (live && rank == 0) wc[w][c] = __popc(same);
+    __syncthreads();
+    if (live) {
+        int before = 0;
+        for (int k = 0; k < w; ++k) before += wc[k][c];
+        const int64_t pos = off[(int64_t)c * nchunks + blockIdx.x] + before + rank;
+        perm[pos] = (int32_t)v;
+        iperm[v] = (int32_t)pos;
+    }
+}
+
+// exclusive scan of the (colour-major) chunk counts, in one block
+__global__ void k_col_offsets(int64_t m, int64_t* a)
+{
+    __shared__ long long part[1024];
+    const int64_t per = (m + blockDim.x - 1) / blockDim.x;
+    const int64_t b = threadIdx.x * per, e = b + per < m ? b + per : m;
+    long long s = 0;
+    for (int64_t i = b; i < e; ++i) s += a[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long run = 0;
+        for (unsigned k = 0; k < blockDim.x; ++k) {
+            long long t = part[k];
+            part[k] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    long long run = part[threadIdx.x];
+    for (int64_t i = b; i < e; ++i) {
+        long long t = a[i];
+        a[i] = run;
+        run += t;
+    }
+}
+
+// first ordered row of every colour (the offset of its first chunk)
+__global__ void k_col_starts(int ncol, int64_t nchunks, const int64_t* off, int32_t* starts)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncol) starts[c] = (int32_t)off[(int64_t)c * nchunks];
+}
+
+// ------------------------------------------------------------ P M Q^T patterns
+// row lengths of the permuted matrix: new row k is old row rperm[k]
+__global__ void k_perm_len(int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ rperm,
+                           int64_t* len)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = rperm ? rperm[k] : (int32_t)k;
+        len[k] = rowptr[r + 1] - rowptr[r];
+    }
+}
+
+constexpr int kPermWarps = 4;
+constexpr int kPermRowCache = 1024;  // columns of a row cached in shared memory per warp
+
+// one warp per new row: columns renamed through cmap (old column -> new), and
+// every entry placed at its rank among the row's new columns (distinct), so
+// the row comes out sorted; map[pos] = position of the entry in the original
+__global__ void __launch_bounds__(kPermWarps * 32) k_perm_fill(int32_t n, const int64_t* __restrict__ rowptr,
+                                                               const int32_t* __restrict__ col,
+                                                               const int32_t* __restrict__ rperm,
+                                                               const int32_t* __restrict__ cmap,
+                                                               const int64_t* __restrict__ nptr, int32_t* ncol,
+                                                               int64_t* nmap)
+{
+    __shared__ int32_t cache[kPermWarps][kPermRowCache];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t k = (int64_t)blockIdx.x * kPermWarps + w; k < n; k += (int64_t)gridDim.x * kPermWarps) {
+        const int32_t r = rperm ? rperm[k] : (int32_t)k;
+        const int64_t b = rowptr[r], e = rowptr[r + 1];
+        const int len = (int)(e - b);
+        const bool cached = len <= kPermRowCache;
+        if (cached)
+            for (int q = lane; q < len; q += 32) cache[w][q] = cmap ? cmap[col[b + q]] : col[b + q];
+        __syncwarp();
+        for (int q = lane; q < len; q += 32) {
+            const int32_t c = cached ? cache[w][q] : (cmap ? cmap[col[b + q]] : col[b + q]);
+            int rank = 0;
+            for (int t = 0; t < len; ++t) {
+                const int32_t ct = cached ? cache[w][t] : (cmap ? cmap[col[b + t]] : col[b + t]);
+                rank += ct < c;
+            }
+            ncol[nptr[k] + rank] = c;
+            nmap[nptr[k] + rank] = b + q;
+        }
+        __syncwarp();
+    }
+}
+
+template <class TI, class TO>
+__global__ void k_gather_vals(int64_t n, const int64_t* __restrict__ map, const TI* __restrict__ in, TO* out)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = (TO)in[map[k]];
+}
+
+static unsigned grid_for(edfa_handle_s* h, int64_t n, int threads = 256)
+{
+    int64_t g = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)h->nsm * 32;
+    if (g > cap) g = cap;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+// ------------------------------------------------------------ host side
+int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr, const int32_t* col, int64_t nnz,
+                 cudaStream_t s)
+{
+    o.on = 0;
+    o.n = n;
+    o.ncolours = 0;
+    int rc;
+    if ((rc = dalloc_t(h, &o.perm, (size_t)(n > 0 ? n : 1)))) return rc;
+    if ((rc = dalloc_t(h, &o.iperm, (size_t)(n > 0 ? n : 1)))) return rc;
+    if (n == 0) { o.on = 1; o.cstart.assign(1, 0); return EDFA_OK; }
+    // transpose pattern (rows unordered), colours, counters
+    int64_t *tp = nullptr, *cur = nullptr, *cnt = nullptr;
+    int32_t* tc = nullptr;
+    int* colour = nullptr;
+    unsigned long long* misc = nullptr;  // [0] vertices left uncoloured by a round, [1] max colour (int)
+    auto done = [&](int code) {
+        cudaFreeAsync(tp, s); cudaFreeAsync(cur, s); cudaFreeAsync(tc, s); cudaFreeAsync(colour, s);
+        cudaFreeAsync(misc, s); cudaFreeAsync(cnt, s);
+        return code;
+    };
+    if (cudaMallocAsync((void**)&tp, ((size_t)n + 1) * sizeof(int64_t), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&cur, ((size_t)n + 1) * sizeof(int64_t), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&tc, (size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&colour, (size_t)n * sizeof(int), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&misc, 2 * sizeof(unsigned long long), s) != cudaSuccess) {
+        cudaGetLastError();
+        return done(EDFA_ERR_OOM);
+    }
+    cudaMemsetAsync(tp, 0, ((size_t)n + 1) * sizeof(int64_t), s);
+    const unsigned g = grid_for(h, n);
+    (edfa::count_launch(), k_tp_count<<<g, 256, 0, s>>>(n, rowptr, col, (unsigned long long*)tp));
+    if ((rc = scan_i64(h, tp, n, s))) return done(rc);
+    cudaMemcpyAsync(cur, tp, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+    (edfa::count_launch(), k_tp_fill<<<g, 256, 0, s>>>(n, rowptr, col, (unsigned long long*)cur, tc));
+    cudaMemsetAsync(colour, 0xFF, (size_t)n * sizeof(int), s);
+    cudaMemsetAsync(misc, 0, 2 * sizeof(unsigned long long), s);
+    // rounds until a round leaves no vertex uncoloured; every round colours at
+    // least the uncoloured vertex of highest priority, so n rounds always end it
+    int64_t rounds = 0;
+    int per_check = 4;
+    unsigned long long left = 1;
+    const unsigned gr = grid_for(h, n, 128);
+    while (left > 0) {
+        if (rounds > (int64_t)n + 1) return done(EDFA_ERR_TIMEOUT);
+        for (int k = 0; k < per_check; ++k) {
+            cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s);
+            (edfa::count_launch(), k_jp_round<<<gr, 128, 0, s>>>(n, rowptr, col, tp, tc, colour, misc,
+                                                                 (int*)(misc + 1)));
+        }
+        rounds += per_check;
+        if (per_check < 64) per_check *= 2;
+        cudaMemcpyAsync(&left, misc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return done(EDFA_ERR_CUDA);
+    }
+    int maxcol = 0;
+    cudaMemcpyAsync(&maxcol, (int*)(misc + 1), sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return done(EDFA_ERR_CUDA);
+    const int ncol = maxcol + 1;
+    if (ncol > kOrdMaxColours) {
+        set_detail(ncol);
+        return done(EDFA_ERR_BOUNDS);
+    }
+    // rows sorted by (colour, index)
+    const int64_t nchunks = ((int64_t)n + kOrdChunk - 1) / kOrdChunk;
+    if (cudaMallocAsync((void**)&cnt, (size_t)(ncol * nchunks + 1) * sizeof(int64_t), s) != cudaSuccess) {
+        cudaGetLastError();
+        return done(EDFA_ERR_OOM);
+    }
+    (edfa::count_launch(), k_col_chunk_count<<<(unsigned)nchunks, kOrdChunk, 0, s>>>(n, colour, ncol, nchunks, cnt));
+    (edfa::count_launch(), k_col_offsets<<<1, 1024, 0, s>>>((int64_t)ncol * nchunks, cnt));
+    (edfa::count_launch(), k_col_chunk_place<<<(unsigned)nchunks, kOrdChunk, 0, s>>>(n, colour, ncol, nchunks, cnt,
+                                                                                      o.perm, o.iperm));
+    // colour starts to the host (the colour array is free again: reuse it)
+    (edfa::count_launch(), k_col_starts<<<(unsigned)((ncol + 255) / 256), 256, 0, s>>>(ncol, nchunks, cnt, colour));
+    o.cstart.assign((size_t)ncol + 1, n);
+    cudaMemcpyAsync(o.cstart.data(), colour, (size_t)ncol * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return done(EDFA_ERR_CUDA);
+    o.on = 1;
+    o.ncolours = ncol;
+    return done(cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA);
+}
+
+int order_matrix(edfa_handle_s* h, OrderedCsr& m, int32_t nrows, const int64_t* rowptr, const int32_t* col,
+                 int64_t nnz, const int32_t* rperm, const int32_t* cmap, cudaStream_t s)
+{
+    m.nnz = nnz;
+    int rc;
+    if ((rc = dalloc_t(h, &m.ptr, (size_t)nrows + 1))) return rc;
+    if ((rc = dalloc_t(h, &m.col, (size_t)(nnz > 0 ? nnz : 1)))) return rc;
+    if ((rc = dalloc_t(h, &m.map, (size_t)(nnz > 0 ? nnz : 1)))) return rc;
+    m.v64 = nullptr;
+    m.v32 = nullptr;
+    if (nrows == 0) {
+        cudaMemsetAsync(m.ptr, 0, sizeof(int64_t), s);
+        return EDFA_OK;
+    }
+    (edfa::count_launch(), k_perm_len<<<grid_for(h, nrows), 256, 0, s>>>(nrows, rowptr, rperm, m.ptr));
+    if ((rc = scan_i64(h, m.ptr, nrows, s))) return rc;
+    const int64_t nb = ((int64_t)nrows + kPermWarps - 1) / kPermWarps;
+    const unsigned gb = (unsigned)(nb < (int64_t)h->nsm * 64 ? nb : (int64_t)h->nsm * 64);
+    (edfa::count_launch(), k_perm_fill<<<gb, kPermWarps * 32, 0, s>>>(nrows, rowptr, col, rperm, cmap, m.ptr, m.col,
+                                                                      m.map));
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
+int order_values(edfa_handle_s* h, OrderedCsr& m, const double* src64, const float* src32, cudaStream_t s)
+{
+    const size_t cap = (size_t)(m.nnz > 0 ? m.nnz : 1);
+    int rc;
+    const unsigned g = grid_for(h, m.nnz);
+    if (src64) {
+        if (!m.v64 && (rc = dalloc_t(h, &m.v64, cap))) return rc;
+        if (m.nnz > 0) (edfa::count_launch(), k_gather_vals<double, double><<<g, 256, 0, s>>>(m.nnz, m.map, src64, m.v64));
+    }
+    if (src32) {
+        if (!m.v32 && (rc = dalloc_t(h, &m.v32, cap))) return rc;
+        if (m.nnz > 0) (edfa::count_launch(), k_gather_vals<float, float><<<g, 256, 0, s>>>(m.nnz, m.map, src32, m.v32));
+    }
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
+// Stage-2 symbolic work with an ordering of S~: the colouring of the
+// factorised S~ pattern, P_s S~ P_s^T, the couplings in the ordered numbering
+// (P_s C P_a^T for the right-hand side of the S~ sweep, P_a B P_s^T for the
+// second A~ sweep; P_a = identity without an ordering of A~) and the level
+// plans of the ordered factor.
+int order_stage2_symbolic(edfa_handle_s* h, cudaStream_t s)
+{
+    int rc;
+    const int32_t Ne = h->Ne, Nf = h->Nf;
+    if ((rc = order_colour(h, h->os, Ne, h->sf_ptr, h->sf_col, h->sf_nnz, s))) return rc;
+    if ((rc = order_matrix(h, h->so, Ne, h->sf_ptr, h->sf_col, h->sf_nnz, h->os.perm, h->os.iperm, s))) return rc;
+    const int32_t* ap = h->oa.on ? h->oa.perm : nullptr;
+    const int32_t* aip = h->oa.on ? h->oa.iperm : nullptr;
+    if ((rc = order_matrix(h, h->co, Ne, h->C.rowptr, h->C.col, h->C.nnz, h->os.perm, aip, s))) return rc;
+    if ((rc = order_values(h, h->co, h->C.val, h->c32, s))) return rc;
+    if ((rc = order_matrix(h, h->bo, Nf, h->B.rowptr, h->B.col, h->B.nnz, ap, h->os.iperm, s))) return rc;
+    if ((rc = order_values(h, h->bo, h->B.val, h->b32, s))) return rc;
+    // value arrays of the ordered S~ now, inside the symbolic step, so that a
+    // pattern rebuilt by a later Stage 2 releases them with the rest of its plan
+    const bool f32 = h->opt.precision == 1;
+    if ((rc = order_values(h, h->so, f32 ? nullptr : h->sf_val, f32 ? h->sf_val32 : nullptr, s))) return rc;
+    h->cp = ClusterPlan{};
+    h->cp.state = 0;
+    return factor_plan(h, h->fs, Ne, h->so.nnz, h->so.ptr, h->so.col, s);
+}
+
+// numeric ILU(0) of S~ (ordered when an ordering of S~ is on)
+int stage2_numeric(edfa_handle_s* h, cudaStream_t s)
+{
+    if (h->opt.ordering >= 1) {
+        int rc = order_values(h, h->so, h->opt.precision == 1 ? nullptr : h->sf_val,
+                              h->opt.precision == 1 ? h->sf_val32 : nullptr, s);
+        if (rc) return rc;
+        return factor_numeric(h, h->fs, h->so.v64, h->so.v32, s);
+    }
+    return factor_numeric(h, h->fs, h->sf_val, h->sf_val32, s);
+}
+
+// the A~ factor with an ordering of the faces: colouring of A's pattern,
+// P_a A P_a^T, its level plans and numeric ILU(0)
+int order_a_factor(edfa_handle_s* h, cudaStream_t s)
+{
+    int rc;
+    const int32_t Nf = h->Nf;
+    if ((rc = order_colour(h, h->oa, Nf, h->A.rowptr, h->A.col, h->A.nnz, s))) return rc;
+    if ((rc = order_matrix(h, h->ao, Nf, h->A.rowptr, h->A.col, h->A.nnz, h->oa.perm, h->oa.iperm, s))) return rc;
+    if ((rc = order_values(h, h->ao, h->A.val, h->opt.precision == 1 ? h->a32 : nullptr, s))) return rc;
+    if ((rc = factor_plan(h, h->fa, Nf, h->ao.nnz, h->ao.ptr, h->ao.col, s))) return rc;
+    return factor_numeric(h, h->fa, h->ao.v64, h->ao.v32, s);
+}
+
+}  // namespace edfa
