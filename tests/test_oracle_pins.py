@@ -645,3 +645,43 @@ def test_ordered_preconditioner_fgmres_converges():
         for ordering in (1, 2):
             r = O.edfa_pipeline(sysd, mode=mode, ordering=ordering)
             assert r["converged"] and r["true_rel"] <= 1e-8, (mode, ordering, r["true_rel"])
+
+
+def test_config1_own_face_sets_give_a_schur_approximation_with_negative_spectrum():
+    """Workload 1 (weak-form cell rows with upwind face mobilities) stalls with
+    own-face sets under either reading of "C = -(upwind mobility) B^T":
+    C_Ej = -lambda_j B_jE (the one the generator uses) or the flux-weighted
+    C_Ej = -sum_{f in F_E} lambda_f W^E_fj (same D).  With Q^(m) = the cell's
+    own faces, S~ = D - C X~ has eigenvalues with negative real part in both,
+    so the block preconditioner is indefinite (FGMRES(50) does not reach 1e-8);
+    the exact Schur complement of the flux-weighted form has none, and
+    neighbour-face sets converge for both."""
+    import scipy.sparse as sp
+    s = W.config1()
+    st = W.Stream(1)
+    Ne, nx = 1000, 10
+    W.wexp(st.normal(Ne))
+    lam = W.wexp(0.5 * st.normal(Ne))
+    tmp = W.assemble(nx, nx, nx, W.iso_K(np.ones(Ne)))
+    lam_f = W._face_upwind_mobility(nx, nx, nx, lam, st.uniform(tmp.Nf), tmp.face_cells)
+    assert np.allclose(lam, s.extra["lam_cell"])
+    Wm, cf = s.W.reshape(Ne, 6, 6), s.cell_faces
+    rows, cols, vals = [], [], []
+    for e in range(Ne):
+        for j in range(6):
+            if not s.face_dir[cf[e, j]]:
+                rows.append(e)
+                cols.append(cf[e, j])
+                vals.append(-sum(lam_f[cf[e, l]] * Wm[e, l, j] for l in range(6)))
+    Cw = sp.csr_matrix((vals, (rows, cols)), shape=(Ne, s.Nf))
+    Cw.sort_indices()
+    A, B, D = (M.to_scipy().toarray() for M in (s.A, s.B, s.D))
+    for C in (s.C.to_scipy(), Cw):
+        s2 = W.System(**{**s.__dict__, "C": W.CSR(Ne, s.Nf, C.indptr.astype(np.int64),
+                                                  C.indices.astype(np.int32), C.data)})
+        r = O.edfa_pipeline(s2, mode="own", solve=False)
+        ev = np.linalg.eigvals(r["S"].to_scipy().toarray())
+        assert (ev.real < 0).sum() >= 10
+        assert O.edfa_pipeline(s2, mode="nbr", maxit=1000)["converged"]
+    S_exact = D - Cw.toarray() @ np.linalg.solve(A, B)
+    assert np.linalg.eigvals(S_exact).real.min() > 0
