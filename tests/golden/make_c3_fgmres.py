@@ -1,8 +1,10 @@
 """Write tests/golden/c3_oracle_fgmres.txt: the oracle's FGMRES(50) iteration
-count and true residual on the 128x128x64 channelised workload (Q = own faces
-+ strong A-connections, threshold 0.05), rtol 1e-8, with the digest of the
-generated inputs they belong to.  Calls only the seeded generator and the
-oracle (several minutes of CPU time)."""
+counts and true residuals on the 128x128x64 channelised workload (Q = own
+faces + strong A-connections, threshold 0.05), rtol 1e-8, with the natural
+order of the inner ILU(0) factorisations and with multicolour orderings of
+both (ordering 2), and the digest of the generated inputs they belong to.
+Calls only the seeded generator and the oracle (tens of minutes of CPU
+time)."""
 import os
 import sys
 import time
@@ -14,13 +16,18 @@ import oracle as O  # noqa: E402
 import workloads as W  # noqa: E402
 
 if __name__ == "__main__":
-    t = time.time()
     s = W.config3()
-    r = O.edfa_pipeline(s, mode="thresh", restart=50, rtol=1e-8, maxit=3000)
+    out = []
+    for ordering, suffix in ((0, ""), (2, "_ordering2")):
+        t = time.time()
+        r = O.edfa_pipeline(s, mode="thresh", restart=50, rtol=1e-8, maxit=3000, ordering=ordering)
+        out.append((suffix, r["iters"], r["true_rel"], time.time() - t))
     with open(os.path.join(HERE, "c3_oracle_fgmres.txt"), "w") as f:
         f.write("# oracle FGMRES(50) on the 128x128x64 channelised workload, thresh 0.05 sets, rtol 1e-8\n")
+        f.write("# (natural order; _ordering2: multicolour orderings of A~ and S~)\n")
         f.write("# written by tests/golden/make_c3_fgmres.py (oracle only)\n")
         f.write(f"inputs_sha256 {W.digest(s)}\n")
-        f.write(f"iterations {r['iters']}\n")
-        f.write(f"true_rel {r['true_rel']:.6e}\n")
-        f.write(f"seconds {time.time() - t:.1f}\n")
+        for suffix, it, tr, sec in out:
+            f.write(f"iterations{suffix} {it}\n")
+            f.write(f"true_rel{suffix} {tr:.6e}\n")
+            f.write(f"seconds{suffix} {sec:.1f}\n")
