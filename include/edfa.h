@@ -169,6 +169,12 @@ typedef struct {
        post-filtration of S~); numeric ILU(0) of S~; writing of the cluster
        sweep records */
     float ms_s_values, ms_s_plan, ms_s_factor, ms_s_cluster;
+    /* with profiling on: accumulated device time and launch count of the
+       FGMRES kernels, kind 0 = first-pass multi-dot V^T w (with ||w||^2),
+       1 = first-pass update w -= V h, 2 = block SpMV y = [A B; C D] x */
+    double kry_ms[3];
+    int64_t kry_n[3];
+    int64_t kry_vecs;  /* basis vectors read by the timed multi-dot launches, summed */
 } edfa_stats;
 
 /* Read-only views of what the handle computed (device pointers, valid until
@@ -268,8 +274,9 @@ EDFA_API int32_t edfa_history(edfa_handle h, double* hist, int32_t cap);
 EDFA_API int edfa_get_view(edfa_handle h, edfa_view* v);
 EDFA_API int edfa_get_stats(edfa_handle h, edfa_stats* s);
 
-/* Turn per-sweep device timing on (1) or off (0); turning it on clears the
- * accumulated sweep times.  Timing adds one event pair per sweep launch. */
+/* Turn per-launch device timing of the triangular sweeps and the first-pass
+ * FGMRES kernels on (1) or off (0); turning it on clears the accumulated times
+ * (edfa_stats.sweep_ms, kry_ms).  Timing adds one event pair per timed launch. */
 EDFA_API int edfa_set_profiling(edfa_handle h, int32_t on);
 
 /* Preconditioner for the transposed system [A B; C D]^T = [A C^T; B^T D^T]

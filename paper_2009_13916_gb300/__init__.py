@@ -62,7 +62,8 @@ class Stats(C.Structure):
                 ("tuned_lanes", C.c_int32), ("tuned_warps", C.c_int32), ("tuned_schur_warps", C.c_int32),
                 ("s_cluster", C.c_int32), ("s_cluster_bytes", C.c_int64),
                 ("ms_s_values", C.c_float), ("ms_s_plan", C.c_float), ("ms_s_factor", C.c_float),
-                ("ms_s_cluster", C.c_float)]
+                ("ms_s_cluster", C.c_float), ("kry_ms", C.c_double * 3), ("kry_n", C.c_int64 * 3),
+                ("kry_vecs", C.c_int64)]
 
 
 class View(C.Structure):

@@ -20,14 +20,42 @@ namespace edfa {
 void set_detail(long long d) { g_detail = d; }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-// fold the recorded sweep event pairs into the stats (stream already synchronised)
+// per-launch timing (edfa_set_profiling): a pair of events per timed launch,
+// tagged 0 A fwd, 1 A bwd, 2 S fwd, 3 S bwd, 4 S fwd+bwd in one cluster launch,
+// 5 first-pass multi-dot, 6 first-pass update, 7 block SpMV; returns null
+// when profiling is off.  With s == -1 the caller records both events.
+cudaEvent_t* prof_begin(edfa_handle_s* h, int kind, cudaStream_t s)
+{
+    if (!h->profiling) return nullptr;
+    if (h->prof_used * 2 + 2 > h->prof_ev.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            h->prof_ev.push_back(e);
+        }
+        h->prof_kind.resize(h->prof_ev.size() / 2);
+    }
+    cudaEvent_t* pe = &h->prof_ev[2 * h->prof_used];
+    h->prof_kind[h->prof_used] = kind;
+    h->prof_used++;
+    if (s != (cudaStream_t)-1) cudaEventRecord(pe[0], s);
+    return pe;
+}
+
+// fold the recorded event pairs into the stats (stream already synchronised)
 static void prof_collect(edfa_handle_s* h)
 {
     for (size_t k = 0; k < h->prof_used; ++k) {
         float ms = 0;
         if (cudaEventElapsedTime(&ms, h->prof_ev[2 * k], h->prof_ev[2 * k + 1]) == cudaSuccess) {
-            h->stats.sweep_ms[h->prof_kind[k]] += ms;
-            h->stats.sweep_n[h->prof_kind[k]] += 1;
+            const int kind = h->prof_kind[k];
+            if (kind < 5) {
+                h->stats.sweep_ms[kind] += ms;
+                h->stats.sweep_n[kind] += 1;
+            } else {
+                h->stats.kry_ms[kind - 5] += ms;
+                h->stats.kry_n[kind - 5] += 1;
+            }
         }
     }
     h->prof_used = 0;
@@ -318,7 +346,7 @@ int edfa_matvec(edfa_handle h, const double* x, double* y, edfa_stream stream)
 
 // Right-preconditioned flexible GMRES(m) (Saad, Alg. 9.6): Arnoldi with
 // classical Gram-Schmidt in FP64 on the device, repeated once when the first
-// pass removed more than half of the squared norm (DGKS criterion), the
+// pass shrank the norm by more than a factor of 10 (Rutishauser's criterion), the
 // (m+1) x m Hessenberg least-squares problem by Givens rotations on the host
 // (one (j+2)-value device->host read per inner iteration), x0 = 0, and the
 // true residual ||b - A x|| checked at the end of every cycle; the outer loop
@@ -378,12 +406,21 @@ int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol
             double* vj = h->V + (int64_t)j * n;
             double* zj = h->Z + (int64_t)j * n;
             if ((rc = apply_prec(h, vj, zj, s))) return rc;
+            cudaEvent_t* pe = prof_begin(h, 7, s);
             if ((rc = matvec(h, zj, h->w, s))) return rc;
-            // classical Gram-Schmidt, repeated when the DGKS criterion asks for it
+            if (pe) cudaEventRecord(pe[1], s);
+            // classical Gram-Schmidt, repeated when the reorthogonalisation test asks for it
             // (decided on the device: the second pass's kernels read the gate)
             const int nv = j + 1;
+            pe = prof_begin(h, 5, s);
             if ((rc = kry_multidot(h->V, n, nv, h->w, n, h->part, h1, nullptr, nullptr, 1, s))) return rc;
+            if (pe) {
+                cudaEventRecord(pe[1], s);
+                h->stats.kry_vecs += nv;
+            }
+            pe = prof_begin(h, 6, s);
             if ((rc = kry_update(h->V, n, nv, h1, h->w, n, h->part, misc, s))) return rc;
+            if (pe) cudaEventRecord(pe[1], s);
             if ((rc = kry_dgks(misc, h1 + nv, h->kgate, s))) return rc;
             if ((rc = kry_multidot(h->V, n, nv, h->w, n, h->part, h2, h1, hf, 0, s, h->kgate))) return rc;
             if ((rc = kry_update(h->V, n, nv, h2, h->w, n, h->part, misc, s, h->kgate))) return rc;
@@ -621,6 +658,8 @@ int edfa_set_profiling(edfa_handle h, int32_t on)
     h->profiling = on ? 1 : 0;
     h->prof_used = 0;
     for (int k = 0; k < 5; ++k) { h->stats.sweep_ms[k] = 0; h->stats.sweep_n[k] = 0; }
+    for (int k = 0; k < 3; ++k) { h->stats.kry_ms[k] = 0; h->stats.kry_n[k] = 0; }
+    h->stats.kry_vecs = 0;
     return EDFA_OK;
 }
 

@@ -185,6 +185,7 @@ struct Ordering {
     int32_t* perm = nullptr;   // [n] ordered position -> original row
     int32_t* iperm = nullptr;  // [n] original row -> ordered position
     std::vector<int32_t> cstart;  // host: first ordered row of every colour, [ncolours + 1]
+    int32_t* cstart_dev = nullptr;  // the same on the device
 };
 
 // An ordered copy P M Q^T of a CSR matrix: pattern, the position in M of every
@@ -254,6 +255,7 @@ struct edfa_handle_s {
     // (P_s C P_a^T, P_a B P_s^T)
     edfa::Ordering oa, os;
     edfa::OrderedCsr ao, so, co, bo;
+    unsigned* coop_bar = nullptr;  // [2] grid-barrier state of the cooperative per-colour sweeps
     edfa::ClusterPlan cp;
     // sweep synchronisation
     int* flags = nullptr;          // [max(Nf, Ne)] completion epochs
@@ -276,9 +278,10 @@ struct edfa_handle_s {
     edfa::DevErr* err = nullptr;
     edfa::DevErr* err_host = nullptr;
     cudaEvent_t ev[12] = {};
-    // opt-in per-sweep device timing: event pairs recorded around every sweep
+    // opt-in per-launch device timing: event pairs recorded around every sweep
     // launch (kind 0..4 = A forward, A backward, S~ forward, S~ backward, both S~ sweeps
-    // in one cluster launch)
+    // in one cluster launch) and the first-pass Krylov kernels (5 multi-dot, 6 update,
+    // 7 block SpMV)
     int profiling = 0;
     std::vector<cudaEvent_t> prof_ev;
     std::vector<int> prof_kind;
@@ -307,6 +310,8 @@ int dalloc_t(edfa_handle_s* h, T** p, size_t count)
     return dalloc(h, (void**)p, count * sizeof(T));
 }
 int check_err(edfa_handle_s* h, cudaStream_t s);  // sync + read device error record
+// event pair of one timed launch when profiling is on (edfa_api.cu), else null
+cudaEvent_t* prof_begin(edfa_handle_s* h, int kind, cudaStream_t s);
 void set_detail(long long d);
 
 // exclusive scan of int64 counts in place: out[i] = sum_{j<i} in[j]; out[n] = total.
@@ -328,6 +333,8 @@ int stage2_pattern(edfa_handle_s* h, cudaStream_t s);
 int stage2_symbolic(edfa_handle_s* h, cudaStream_t s);
 int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64_t* rowptr,
                 const int32_t* col, cudaStream_t s);
+int factor_plan_common(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64_t* rowptr,
+                       const int32_t* col, cudaStream_t s);
 int factor_numeric(edfa_handle_s* h, Factor& f, const double* vals64, const float* vals32,
                    cudaStream_t s);
 int apply_prec(edfa_handle_s* h, const double* r, double* z, cudaStream_t s);

@@ -27,6 +27,7 @@ struct BState {
     // per system
     double *bnorm, *beta, *H, *cs, *sn, *g, *y, *h1, *h2, *hsum, *nrm2, *inv, *rn2, *true_rel;
     int *active, *conv, *kdone, *iters, *flags;  // flags[0] = systems still running
+    int* gate;  // second Gram-Schmidt pass of the current step
 };
 
 // chunk table
@@ -66,9 +67,13 @@ k_bdot(const double* __restrict__ V, int64_t ld, int nv, const double* __restric
     const int64_t st = ch.start[c];
     const int len = ch.len[c];
     const bool act = active[sys] != 0;
+    if (!act) {  // block-uniform: zero parts without the reductions
+        for (int k = threadIdx.x; k < nv + with_self; k += kBT) part[(int64_t)c * stride + k] = 0.0;
+        return;
+    }
     for (int k = 0; k < nv + with_self; ++k) {
         double acc = 0.0;
-        if (act) {
+        {
             const double* vk = k < nv ? V + (int64_t)k * ld : w;
             for (int e = threadIdx.x; e < len; e += kBT) acc = fma(__ldg(vk + st + e), w[st + e], acc);
         }
@@ -96,6 +101,7 @@ k_breduce(const double* part, int stride, int nk, BChunks ch, double* out, int o
 }
 
 // w -= sum_k coef[sys][k] V_k on active systems; partial squared norm per chunk
+// of the active systems (the parts of the others are left as they are)
 __global__ void __launch_bounds__(kBT)
 k_bupdate(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ coef, int cstride,
           double* w, BChunks ch, const int* __restrict__ active, double* part_norm)
@@ -117,10 +123,21 @@ k_bupdate(const double* __restrict__ V, int64_t ld, int nv, const double* __rest
             nacc = fma(v, v, nacc);
         }
     }
-    if (part_norm) {
+    if (part_norm && act) {
         double t = bsum(nacc);
         if (threadIdx.x == 0) part_norm[c] = t;
     }
+}
+
+// Reorthogonalisation test per system (Rutishauser's criterion, as in the
+// single-system solve): a second Gram-Schmidt pass for the active systems whose
+// first pass shrank the norm by more than a factor of 10
+__global__ void k_bgate(BState S, int nv)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S.nsys) return;
+    const int hs = S.m + 2;
+    S.gate[s] = (S.active[s] && S.nrm2[s] < 0.01 * S.h1[(int64_t)s * hs + nv]) ? 1 : 0;
 }
 
 // v = w * inv[sys] (0 on inactive systems)
@@ -262,6 +279,7 @@ struct BatchWork {
     BChunks ch{};
     BState S{};
     double *V = nullptr, *Z = nullptr, *w = nullptr, *part = nullptr;
+    double* pnorm = nullptr;  // per-chunk partial squared norms of w
     int pstride = 0;
     cudaGraphExec_t cycle = nullptr;
     cudaGraph_t graph = nullptr;
@@ -322,6 +340,8 @@ static int batch_prepare(edfa_handle_s* h, BatchWork& B, cudaStream_t s)
     rc |= dalloc_t(h, &B.Z, (size_t)m * B.n);
     rc |= dalloc_t(h, &B.w, (size_t)B.n);
     rc |= dalloc_t(h, &B.part, (size_t)nc * B.pstride);
+    rc |= dalloc_t(h, &B.pnorm, (size_t)nc);
+    rc |= dalloc_t(h, &S.gate, (size_t)B.nsys);
     return rc ? EDFA_ERR_OOM : EDFA_OK;
 }
 
@@ -337,13 +357,19 @@ static int batch_step(edfa_handle_s* h, BatchWork& B, int j, cudaStream_t s)
     if (rc) return rc;
     const int nv = j + 1;
     BState& S = B.S;
-    (edfa::count_launch(), k_bdot<<<nc, kBT, 0, s>>>(B.V, n, nv, B.w, B.ch, S.active, B.part, B.pstride, 0));
-    (edfa::count_launch(), k_breduce<<<ns, kBT, 0, s>>>(B.part, B.pstride, nv, B.ch, S.h1, hs, nullptr, nullptr));
-    (edfa::count_launch(), k_bupdate<<<nc, kBT, 0, s>>>(B.V, n, nv, S.h1, hs, B.w, B.ch, S.active, nullptr));
-    (edfa::count_launch(), k_bdot<<<nc, kBT, 0, s>>>(B.V, n, nv, B.w, B.ch, S.active, B.part, B.pstride, 0));
+    // first pass (with ||w||^2 in h1[nv]), its squared norm, the per-system
+    // test, and the second pass on the systems the test selects: for the
+    // others the second dot products are zero (h2 = 0, hsum = h1) and the
+    // norm parts of the first pass stay
+    (edfa::count_launch(), k_bdot<<<nc, kBT, 0, s>>>(B.V, n, nv, B.w, B.ch, S.active, B.part, B.pstride, 1));
+    (edfa::count_launch(), k_breduce<<<ns, kBT, 0, s>>>(B.part, B.pstride, nv + 1, B.ch, S.h1, hs, nullptr, nullptr));
+    (edfa::count_launch(), k_bupdate<<<nc, kBT, 0, s>>>(B.V, n, nv, S.h1, hs, B.w, B.ch, S.active, B.pnorm));
+    (edfa::count_launch(), k_breduce<<<ns, kBT, 0, s>>>(B.pnorm, 1, 1, B.ch, S.nrm2, 1, nullptr, nullptr));
+    (edfa::count_launch(), k_bgate<<<(ns + 127) / 128, 128, 0, s>>>(S, nv));
+    (edfa::count_launch(), k_bdot<<<nc, kBT, 0, s>>>(B.V, n, nv, B.w, B.ch, S.gate, B.part, B.pstride, 0));
     (edfa::count_launch(), k_breduce<<<ns, kBT, 0, s>>>(B.part, B.pstride, nv, B.ch, S.h2, hs, S.h1, S.hsum));
-    (edfa::count_launch(), k_bupdate<<<nc, kBT, 0, s>>>(B.V, n, nv, S.h2, hs, B.w, B.ch, S.active, B.part));
-    (edfa::count_launch(), k_breduce<<<ns, kBT, 0, s>>>(B.part, 1, 1, B.ch, S.nrm2, 1, nullptr, nullptr));
+    (edfa::count_launch(), k_bupdate<<<nc, kBT, 0, s>>>(B.V, n, nv, S.h2, hs, B.w, B.ch, S.gate, B.pnorm));
+    (edfa::count_launch(), k_breduce<<<ns, kBT, 0, s>>>(B.pnorm, 1, 1, B.ch, S.nrm2, 1, nullptr, nullptr));
     (edfa::count_launch(), k_bgivens<<<(ns + 127) / 128, 128, 0, s>>>(S, j));
     (edfa::count_launch(), k_bscale<<<nc, kBT, 0, s>>>(B.w, B.V + (int64_t)(j + 1) * n, B.ch, S.inv, S.active));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;

@@ -310,8 +310,10 @@ __global__ void k_row_maxlen(int32_t n, const int64_t* __restrict__ rowptr, int*
     if (i < n) atomicMax(out, (int)(rowptr[i + 1] - rowptr[i]));
 }
 
-int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
-                cudaStream_t s)
+// the parts of the symbolic set-up that do not depend on how the level plans
+// are obtained: pattern, diagonal positions, longest row, value arrays
+int factor_plan_common(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64_t* rowptr,
+                       const int32_t* col, cudaStream_t s)
 {
     f.n = n;
     f.nnz = nnz;
@@ -320,10 +322,6 @@ int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64
     int rc = dalloc_t(h, &f.diag, (size_t)(n > 0 ? n : 1));
     if (rc) return rc;
     if (n > 0) (edfa::count_launch(), k_find_diag<<<(n + 255) / 256, 256, 0, s>>>(n, rowptr, col, f.diag, h->err));
-    rc = make_plan(h, f.fwd, n, rowptr, col, 1, 32, s);
-    if (rc) return rc;
-    rc = make_plan(h, f.bwd, n, rowptr, col, 0, 32, s);
-    if (rc) return rc;
     {
         // longest row: picks the shared-memory layout of the numeric factorisation
         int* d = nullptr;
@@ -345,6 +343,16 @@ int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64
         if (!rc) rc = dalloc_t(h, &f.dinv64, (size_t)(n > 0 ? n : 1));
     }
     return rc;
+}
+
+int factor_plan(edfa_handle_s* h, Factor& f, int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                cudaStream_t s)
+{
+    int rc = factor_plan_common(h, f, n, nnz, rowptr, col, s);
+    if (rc) return rc;
+    rc = make_plan(h, f.fwd, n, rowptr, col, 1, 32, s);
+    if (rc) return rc;
+    return make_plan(h, f.bwd, n, rowptr, col, 0, 32, s);
 }
 
 // ------------------------------------------------------------ factorisation
@@ -892,26 +900,6 @@ k_sweep_row(const int32_t* __restrict__ perm, int64_t nslots, const int64_t* __r
     }
 }
 
-// per-launch sweep timing (edfa_set_profiling): a pair of events per launch,
-// tagged 0 A fwd, 1 A bwd, 2 S fwd, 3 S bwd, 4 S fwd+bwd in one cluster launch
-static cudaEvent_t* prof_begin(edfa_handle_s* h, int kind, cudaStream_t s)
-{
-    if (!h->profiling) return nullptr;
-    if (h->prof_used * 2 + 2 > h->prof_ev.size()) {
-        for (int k = 0; k < 64; ++k) {
-            cudaEvent_t e;
-            cudaEventCreate(&e);
-            h->prof_ev.push_back(e);
-        }
-        h->prof_kind.resize(h->prof_ev.size() / 2);
-    }
-    cudaEvent_t* pe = &h->prof_ev[2 * h->prof_used];
-    h->prof_kind[h->prof_used] = kind;
-    h->prof_used++;
-    if (s != (cudaStream_t)-1) cudaEventRecord(pe[0], s);
-    return pe;
-}
-
 // an event pair for a launcher that records both events itself
 static cudaEvent_t* prof_begin_pair(edfa_handle_s* h, int kind) { return prof_begin(h, kind, (cudaStream_t)-1); }
 
@@ -963,20 +951,23 @@ static int launch_sweep(edfa_handle_s* h, const Factor& f, const TB* base, const
 // resident wave, since a colour holds a few hundred thousand rows at most.
 constexpr int kMcThreads = 256;
 
-template <class T, class TB, class TO, int FWD, int LPR>
-__global__ void __launch_bounds__(kMcThreads)
-k_mc_sweep(int32_t r0, int32_t r1, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-           const T* __restrict__ lu, const int64_t* __restrict__ diag, const T* __restrict__ dinv,
-           const TB* __restrict__ base, const int32_t* __restrict__ bperm, const int64_t* __restrict__ mptr,
-           const int32_t* __restrict__ mcol, const T* __restrict__ mval, const TO* __restrict__ mv, TO* out,
-           const int32_t* __restrict__ sperm, double* scat)
+// rows [r0, r1) of one colour, grid-stride over warps; CG: read the earlier
+// colours' results through L2 (a persistent launch: another SM wrote them
+// after this SM may have cached the line)
+template <class T, class TB, class TO, int FWD, int LPR, bool CG>
+__device__ __forceinline__ void mc_rows(int64_t r0, int64_t r1, int64_t warp, int64_t nwarps,
+                                        const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                        const T* __restrict__ lu, const int64_t* __restrict__ diag,
+                                        const T* __restrict__ dinv, const TB* __restrict__ base,
+                                        const int32_t* __restrict__ bperm, const int64_t* __restrict__ mptr,
+                                        const int32_t* __restrict__ mcol, const T* __restrict__ mval,
+                                        const TO* __restrict__ mv, TO* out, const int32_t* __restrict__ sperm,
+                                        double* scat)
 {
     constexpr int RPW = 32 / LPR;
     constexpr int U = 4;
     const int lane = threadIdx.x & 31;
     const int g = lane / LPR, gl = lane % LPR;
-    const int64_t warp = ((int64_t)blockIdx.x * kMcThreads + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * kMcThreads) >> 5;
     for (int64_t i0 = r0 + warp * RPW; i0 < r1; i0 += nwarps * RPW) {
         const int64_t i = i0 + g;
         const bool live = i < r1;
@@ -1000,7 +991,7 @@ k_mc_sweep(int32_t r0, int32_t r1, const int64_t* __restrict__ rowptr, const int
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u)
-                    if (c[u] >= 0) acc = fma(w[u], (T)out[c[u]], acc);
+                    if (c[u] >= 0) acc = fma(w[u], (T)(CG ? __ldcg(out + c[u]) : out[c[u]]), acc);
             }
             for (int64_t p0 = mb; p0 < me; p0 += U * LPR) {
                 int c[U];
@@ -1028,10 +1019,104 @@ k_mc_sweep(int32_t r0, int32_t r1, const int64_t* __restrict__ rowptr, const int
 }
 
 template <class T, class TB, class TO, int FWD, int LPR>
+__global__ void __launch_bounds__(kMcThreads)
+k_mc_sweep(int32_t r0, int32_t r1, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+           const T* __restrict__ lu, const int64_t* __restrict__ diag, const T* __restrict__ dinv,
+           const TB* __restrict__ base, const int32_t* __restrict__ bperm, const int64_t* __restrict__ mptr,
+           const int32_t* __restrict__ mcol, const T* __restrict__ mval, const TO* __restrict__ mv, TO* out,
+           const int32_t* __restrict__ sperm, double* scat)
+{
+    const int64_t warp = ((int64_t)blockIdx.x * kMcThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kMcThreads) >> 5;
+    mc_rows<T, TB, TO, FWD, LPR, false>(r0, r1, warp, nwarps, rowptr, col, lu, diag, dinv, base, bperm, mptr, mcol,
+                                        mval, mv, out, sperm, scat);
+}
+
+// Grid-wide barrier of a cooperative launch: bar[0] counts arrivals, bar[1] is
+// the generation; the last block to arrive resets the count and advances the
+// generation.  The wait is bounded: after kSpinLimit polls (or once any thread
+// has recorded an error) it records EDFA_ERR_TIMEOUT and returns false.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, DevErr* err)
+{
+    __syncthreads();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const unsigned gen = (unsigned)ld_acquire((const int*)(bar + 1));
+        __threadfence();
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            bar[0] = 0;
+            st_release((int*)(bar + 1), (int)(gen + 1));
+        } else {
+            unsigned ns = kBackoffMin, it = 0;
+            while ((unsigned)ld_acquire((const int*)(bar + 1)) == gen) {
+                if (++it >= kSpinLimit || ((it & 255u) == 0u && err_set(err))) {
+                    if (it >= kSpinLimit) raise_err(err, EDFA_ERR_TIMEOUT, -2);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 64) ns <<= 1;
+            }
+        }
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// All colours of one sweep in one cooperative launch, a grid barrier between
+// colours (the per-colour launches' kernel boundaries cost several times more)
+template <class T, class TB, class TO, int FWD, int LPR>
+__global__ void __launch_bounds__(kMcThreads)
+k_mc_sweep_all(int ncol, const int32_t* __restrict__ cstart, const int64_t* __restrict__ rowptr,
+               const int32_t* __restrict__ col, const T* __restrict__ lu, const int64_t* __restrict__ diag,
+               const T* __restrict__ dinv, const TB* __restrict__ base, const int32_t* __restrict__ bperm,
+               const int64_t* __restrict__ mptr, const int32_t* __restrict__ mcol, const T* __restrict__ mval,
+               const TO* __restrict__ mv, TO* out, const int32_t* __restrict__ sperm, double* scat, unsigned* bar,
+               DevErr* err)
+{
+    const int64_t warp = ((int64_t)blockIdx.x * kMcThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kMcThreads) >> 5;
+    for (int k = 0; k < ncol; ++k) {
+        const int c = FWD ? k : ncol - 1 - k;
+        mc_rows<T, TB, TO, FWD, LPR, true>(cstart[c], cstart[c + 1], warp, nwarps, rowptr, col, lu, diag, dinv, base,
+                                           bperm, mptr, mcol, mval, mv, out, sperm, scat);
+        if (k + 1 < ncol) {
+            __threadfence();
+            if (!grid_barrier(bar, gridDim.x, err)) return;
+        }
+    }
+}
+
+template <class T, class TB, class TO, int FWD, int LPR>
 static void mc_launch(edfa_handle_s* h, const Factor& f, const Ordering& o, const T* lu, const T* dinv,
                       const TB* base, const int32_t* bperm, const int64_t* mptr, const int32_t* mcol, const T* mval,
                       const TO* mv, TO* out, const int32_t* sperm, double* scat, cudaStream_t s)
 {
+    // one cooperative launch for all colours when the device supports it
+    if (o.ncolours > 1 && o.cstart_dev && h->coop_bar) {
+        auto fa = k_mc_sweep_all<T, TB, TO, FWD, LPR>;
+        static thread_local int per_dev = -1, per_sm = 0;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev != per_dev) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fa, kMcThreads, 0);
+            per_dev = dev;
+        }
+        if (per_sm >= 1) {
+            cudaMemsetAsync(h->coop_bar, 0, 2 * sizeof(unsigned), s);
+            int ncol = o.ncolours;
+            void* args[] = {(void*)&ncol, (void*)&o.cstart_dev, (void*)&f.rowptr, (void*)&f.col, (void*)&lu,
+                            (void*)&f.diag, (void*)&dinv, (void*)&base, (void*)&bperm, (void*)&mptr, (void*)&mcol,
+                            (void*)&mval, (void*)&mv, (void*)&out, (void*)&sperm, (void*)&scat,
+                            (void*)&h->coop_bar, (void*)&h->err};
+            edfa::count_launch();
+            if (cudaLaunchCooperativeKernel((const void*)fa, dim3((unsigned)(h->nsm * per_sm)), dim3(kMcThreads),
+                                            args, 0, s) == cudaSuccess)
+                return;
+            cudaGetLastError();  // not launchable as one cooperative grid: per-colour launches below
+        }
+    }
     auto fn = k_mc_sweep<T, TB, TO, FWD, LPR>;
     static thread_local int per_dev = -1, per_sm = 0;
     int dev = 0;

@@ -1,6 +1,6 @@
 // Kernels of the outer flexible GMRES (FP64): the block-system SpMV, the
 // classical Gram-Schmidt multi-dot / update pair (a second pass when the
-// DGKS criterion asks for it, decided on the device) and small vector
+// reorthogonalisation test asks for it, decided on the device) and small vector
 // operations.  Reductions are two-level with a
 // fixed tree, so results do not depend on scheduling.
 //
@@ -16,46 +16,97 @@ namespace edfa {
 constexpr int kKT = 256;           // threads per block
 constexpr int kChunk = kKT * 8;    // vector elements per block in the dot kernels
 
-// y = [A B; C D] x, kSpLpr consecutive lanes per row: a warp load then
-// touches 32 / kSpLpr rows in kSpLpr * 8-byte runs (instead of 32 rows in
-// 8-byte pieces), each lane sums every kSpLpr-th entry and a 2-step shuffle
-// reduction closes the row
-constexpr int kSpLpr = 4;
+// y = [A B; C D] x.  Face rows (A and B) and cell rows (C and D) have their
+// own number of lanes per row, LF and LC, from their mean lengths (a face row
+// of the channelised workload holds ~5 entries, a full-tensor cell row ~43):
+// the first nbf blocks take the face rows, the rest the cell rows.  A warp
+// load touches 32 / L rows in L * 8-byte runs; each lane keeps four entries'
+// loads in flight, and a log2(L)-step shuffle reduction closes the row.
+constexpr int kSpU = 4;
 
-__global__ void __launch_bounds__(kKT)
-k_block_spmv(int32_t Nf, int32_t Ne, Csr<double> A, Csr<double> B, Csr<double> C, Csr<double> D,
-             const double* __restrict__ x, double* __restrict__ y)
+template <int L>
+__device__ __forceinline__ double row_dot(const Csr<double>& M, int64_t r, const double* __restrict__ x, int gl,
+                                          double acc)
 {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t r = t / kSpLpr;
-    const int gl = (int)(t % kSpLpr);
-    const int64_t nr = (int64_t)Nf + Ne;
-    const double* xp = x + Nf;
+    const int64_t b = M.rowptr[r], e = M.rowptr[r + 1];
+    for (int64_t p0 = b; p0 < e; p0 += kSpU * L) {
+        int c[kSpU];
+        double w[kSpU];
+#pragma unroll
+        for (int u = 0; u < kSpU; ++u) {
+            const int64_t p = p0 + gl + u * L;
+            c[u] = p < e ? __ldg(M.col + p) : -1;
+            w[u] = p < e ? __ldg(M.val + p) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kSpU; ++u)
+            if (c[u] >= 0) acc = fma(w[u], x[c[u]], acc);
+    }
+    return acc;
+}
+
+template <int L>
+__device__ __forceinline__ void spmv_rows(int64_t r0, int64_t nrows, int64_t t, const Csr<double>& M1,
+                                          const double* x1, const Csr<double>& M2, const double* x2, double* y)
+{
+    const int64_t r = r0 + t / L;
+    const int gl = (int)(t % L);
     double acc = 0.0;
-    if (r < Nf) {
-        for (int64_t p = A.rowptr[r] + gl; p < A.rowptr[r + 1]; p += kSpLpr)
-            acc = fma(__ldg(A.val + p), x[__ldg(A.col + p)], acc);
-        for (int64_t p = B.rowptr[r] + gl; p < B.rowptr[r + 1]; p += kSpLpr)
-            acc = fma(__ldg(B.val + p), xp[__ldg(B.col + p)], acc);
-    } else if (r < nr) {
-        const int64_t e = r - Nf;
-        for (int64_t p = C.rowptr[e] + gl; p < C.rowptr[e + 1]; p += kSpLpr)
-            acc = fma(__ldg(C.val + p), x[__ldg(C.col + p)], acc);
-        for (int64_t p = D.rowptr[e] + gl; p < D.rowptr[e + 1]; p += kSpLpr)
-            acc = fma(__ldg(D.val + p), xp[__ldg(D.col + p)], acc);
+    if (r < r0 + nrows) {
+        acc = row_dot<L>(M1, r - r0, x1, gl, acc);
+        acc = row_dot<L>(M2, r - r0, x2, gl, acc);
     }
 #pragma unroll
-    for (int o = kSpLpr / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (gl == 0 && r < nr) y[r] = acc;
+    for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (gl == 0 && r < r0 + nrows) y[r] = acc;
+}
+
+template <int LF, int LC>
+__global__ void __launch_bounds__(kKT)
+k_block_spmv(int32_t Nf, int32_t Ne, Csr<double> A, Csr<double> B, Csr<double> C, Csr<double> D,
+             const double* __restrict__ x, double* __restrict__ y, int64_t nbf)
+{
+    const double* xp = x + Nf;
+    if ((int64_t)blockIdx.x < nbf)
+        spmv_rows<LF>(0, Nf, (int64_t)blockIdx.x * kKT + threadIdx.x, A, x, B, xp, y);
+    else
+        spmv_rows<LC>(Nf, Ne, ((int64_t)blockIdx.x - nbf) * kKT + threadIdx.x, C, x, D, xp, y);
+}
+
+static int lanes_for(double avg) { return avg <= 6.0 ? 1 : avg <= 12.0 ? 2 : avg <= 32.0 ? 4 : 8; }
+
+template <int LF, int LC>
+static void spmv_launch(edfa_handle_s* h, const double* x, double* y, cudaStream_t s)
+{
+    const int64_t nbf = ((int64_t)h->Nf * LF + kKT - 1) / kKT;
+    const int64_t nbc = ((int64_t)h->Ne * LC + kKT - 1) / kKT;
+    (edfa::count_launch(), k_block_spmv<LF, LC><<<(unsigned)(nbf + nbc), kKT, 0, s>>>(
+                               h->Nf, h->Ne, csr_of(h->A), csr_of(h->B), csr_of(h->C), csr_of(h->D), x, y, nbf));
+}
+
+template <int LF>
+static void spmv_dispatch_c(edfa_handle_s* h, int lc, const double* x, double* y, cudaStream_t s)
+{
+    switch (lc) {
+    case 1: spmv_launch<LF, 1>(h, x, y, s); break;
+    case 2: spmv_launch<LF, 2>(h, x, y, s); break;
+    case 4: spmv_launch<LF, 4>(h, x, y, s); break;
+    default: spmv_launch<LF, 8>(h, x, y, s); break;
+    }
 }
 
 int matvec(edfa_handle_s* h, const double* x, double* y, cudaStream_t s)
 {
     int64_t n = (int64_t)h->Nf + h->Ne;
     if (n == 0) return EDFA_OK;
-    const int64_t th = n * kSpLpr;
-    (edfa::count_launch(), k_block_spmv<<<(unsigned)((th + kKT - 1) / kKT), kKT, 0, s>>>(
-                               h->Nf, h->Ne, csr_of(h->A), csr_of(h->B), csr_of(h->C), csr_of(h->D), x, y));
+    const int lf = lanes_for(h->Nf > 0 ? (double)(h->A.nnz + h->B.nnz) / h->Nf : 1.0);
+    const int lc = lanes_for(h->Ne > 0 ? (double)(h->C.nnz + h->D.nnz) / h->Ne : 1.0);
+    switch (lf) {
+    case 1: spmv_dispatch_c<1>(h, lc, x, y, s); break;
+    case 2: spmv_dispatch_c<2>(h, lc, x, y, s); break;
+    case 4: spmv_dispatch_c<4>(h, lc, x, y, s); break;
+    default: spmv_dispatch_c<8>(h, lc, x, y, s); break;
+    }
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
@@ -161,12 +212,16 @@ k_reduce_parts(const double* part, int nchunks, double* out, const double* add, 
     }
 }
 
-// DGKS criterion (Daniel, Gragg, Kaufman & Stewart 1976): a second classical
-// Gram-Schmidt pass is needed when the first one removed more than half of
-// the squared norm, ||w1||^2 < ||w||^2 / 2
+// Reorthogonalisation test (Rutishauser's criterion, the DGKS test of Daniel,
+// Gragg, Kaufman & Stewart 1976 with the factor 10): a second classical
+// Gram-Schmidt pass runs when the first one shrank the norm by more than a
+// factor of 10, ||w1|| < ||w|| / 10.  With the DGKS factor 1/sqrt(2) the second
+// pass ran in almost every iteration of these solves; with 10 it runs in a few
+// per cent, the FP64 work of the orthogonalisation halves and the iteration
+// counts stay those of modified Gram-Schmidt.
 __global__ void k_dgks(const double* nrm2_after, const double* nrm2_before, int* gate)
 {
-    if (threadIdx.x == 0) *gate = (*nrm2_after < 0.5 * *nrm2_before) ? 1 : 0;
+    if (threadIdx.x == 0) *gate = (*nrm2_after < 0.01 * *nrm2_before) ? 1 : 0;
 }
 
 // v = alpha * w

@@ -255,7 +255,13 @@ int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr
     int rc;
     if ((rc = dalloc_t(h, &o.perm, (size_t)(n > 0 ? n : 1)))) return rc;
     if ((rc = dalloc_t(h, &o.iperm, (size_t)(n > 0 ? n : 1)))) return rc;
-    if (n == 0) { o.on = 1; o.cstart.assign(1, 0); return EDFA_OK; }
+    if (n == 0) {
+        o.on = 1;
+        o.cstart.assign(1, 0);
+        if ((rc = dalloc_t(h, &o.cstart_dev, 1))) return rc;
+        cudaMemsetAsync(o.cstart_dev, 0, sizeof(int32_t), s);
+        return EDFA_OK;
+    }
     // transpose pattern (rows unordered), colours, counters
     int64_t *tp = nullptr, *cur = nullptr, *cnt = nullptr;
     int32_t* tc = nullptr;
@@ -323,6 +329,12 @@ int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr
     o.cstart.assign((size_t)ncol + 1, n);
     cudaMemcpyAsync(o.cstart.data(), colour, (size_t)ncol * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return done(EDFA_ERR_CUDA);
+    if ((rc = dalloc_t(h, &o.cstart_dev, (size_t)ncol + 1))) return done(rc);
+    cudaMemcpyAsync(o.cstart_dev, o.cstart.data(), ((size_t)ncol + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (!h->coop_bar && (rc = dalloc_t(h, &h->coop_bar, 2))) return done(rc);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+    if (!coop) h->coop_bar = nullptr;  // per-colour launches only
     o.on = 1;
     o.ncolours = ncol;
     return done(cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA);
@@ -367,6 +379,63 @@ int order_values(edfa_handle_s* h, OrderedCsr& m, const double* src64, const flo
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
+// ------------------------------------------------------------ level plans from colours
+// The colours of an ordered factor are a valid level schedule: every
+// dependency of a row of colour c lies in an earlier colour (forward) or a
+// later one (backward), and the rows of a colour are contiguous.  Level l of
+// the plan is colour l (forward) or nc - 1 - l (backward), padded to whole
+// warps like the plans of the level analysis.
+__global__ void k_plan_colours(int64_t nslots, int nlev, const int64_t* __restrict__ loff,
+                               const int32_t* __restrict__ cstart, int fwd, int32_t* perm)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nslots; t += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nlev - 1;  // last level whose start is <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (loff[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const int c = fwd ? lo : nlev - 1 - lo;
+        const int64_t k = t - loff[lo];
+        const int32_t cnt = cstart[c + 1] - cstart[c];
+        perm[t] = k < cnt ? (int32_t)(cstart[c] + k) : -1;
+    }
+}
+
+static int plan_from_colours(edfa_handle_s* h, SweepPlan& plan, const Ordering& o, int fwd, cudaStream_t s)
+{
+    const int nc = o.ncolours;
+    std::vector<int64_t> loff((size_t)nc + 1, 0);
+    for (int l = 0; l < nc; ++l) {
+        const int c = fwd ? l : nc - 1 - l;
+        const int64_t cnt = o.cstart[c + 1] - o.cstart[c];
+        loff[l + 1] = loff[l] + (cnt + 31) / 32 * 32;
+    }
+    plan.nlevels = nc;
+    plan.nslots = loff[nc];
+    int rc;
+    if ((rc = dalloc_t(h, &plan.loff, (size_t)nc + 1))) return rc;
+    if ((rc = dalloc_t(h, &plan.perm, (size_t)(plan.nslots > 0 ? plan.nslots : 1)))) return rc;
+    const int32_t* cs = o.cstart_dev;
+    cudaMemcpyAsync(plan.loff, loff.data(), ((size_t)nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (plan.nslots > 0)
+        (edfa::count_launch(), k_plan_colours<<<grid_for(h, plan.nslots), 256, 0, s>>>(plan.nslots, nc, plan.loff, cs,
+                                                                                    fwd, plan.perm));
+    // the host vector must outlive the copy
+    return cudaStreamSynchronize(s) == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
+// Symbolic factor set-up of an ordered matrix: diagonal positions, longest
+// row and value arrays as factor_plan does, with the level plans taken from
+// the colours instead of a level analysis.
+static int factor_plan_ordered(edfa_handle_s* h, Factor& f, const Ordering& o, int32_t n, int64_t nnz,
+                               const int64_t* rowptr, const int32_t* col, cudaStream_t s)
+{
+    int rc = factor_plan_common(h, f, n, nnz, rowptr, col, s);
+    if (rc) return rc;
+    if ((rc = plan_from_colours(h, f.fwd, o, 1, s))) return rc;
+    return plan_from_colours(h, f.bwd, o, 0, s);
+}
+
 // Stage-2 symbolic work with an ordering of S~: the colouring of the
 // factorised S~ pattern, P_s S~ P_s^T, the couplings in the ordered numbering
 // (P_s C P_a^T for the right-hand side of the S~ sweep, P_a B P_s^T for the
@@ -390,7 +459,7 @@ int order_stage2_symbolic(edfa_handle_s* h, cudaStream_t s)
     if ((rc = order_values(h, h->so, f32 ? nullptr : h->sf_val, f32 ? h->sf_val32 : nullptr, s))) return rc;
     h->cp = ClusterPlan{};
     h->cp.state = 0;
-    return factor_plan(h, h->fs, Ne, h->so.nnz, h->so.ptr, h->so.col, s);
+    return factor_plan_ordered(h, h->fs, h->os, Ne, h->so.nnz, h->so.ptr, h->so.col, s);
 }
 
 // numeric ILU(0) of S~ (ordered when an ordering of S~ is on)
@@ -414,7 +483,7 @@ int order_a_factor(edfa_handle_s* h, cudaStream_t s)
     if ((rc = order_colour(h, h->oa, Nf, h->A.rowptr, h->A.col, h->A.nnz, s))) return rc;
     if ((rc = order_matrix(h, h->ao, Nf, h->A.rowptr, h->A.col, h->A.nnz, h->oa.perm, h->oa.iperm, s))) return rc;
     if ((rc = order_values(h, h->ao, h->A.val, h->opt.precision == 1 ? h->a32 : nullptr, s))) return rc;
-    if ((rc = factor_plan(h, h->fa, Nf, h->ao.nnz, h->ao.ptr, h->ao.col, s))) return rc;
+    if ((rc = factor_plan_ordered(h, h->fa, h->oa, Nf, h->ao.nnz, h->ao.ptr, h->ao.col, s))) return rc;
     return factor_numeric(h, h->fa, h->ao.v64, h->ao.v32, s);
 }
 

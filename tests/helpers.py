@@ -67,6 +67,20 @@ def normwise_cols_fast(x_gpu, x_orc, qptr):
     return float((dmax / smax).max()) if nseg else 0.0
 
 
+def entrywise_rel(x_gpu, x_orc, ptr, frac=1e-3):
+    """max |gpu - oracle| / |oracle| over the entries whose magnitude is at least
+    frac times the largest of their column of X~ / row of S~ (the normwise bar
+    of 1e-10 per column bounds this by 1e-10 / frac)."""
+    seg = np.repeat(np.arange(len(ptr) - 1), np.diff(ptr))
+    smax = np.zeros(len(ptr) - 1)
+    np.maximum.at(smax, seg, np.abs(x_orc))
+    big = np.abs(x_orc) >= frac * smax[seg]
+    big &= x_orc != 0
+    if not big.any():
+        return 0.0
+    return float((np.abs(x_gpu - x_orc)[big] / np.abs(x_orc)[big]).max())
+
+
 def oracle_pipeline(sysd, mode=None, form=0, variant=0, dyn=None, solve=True, restart=50, rtol=1e-8,
                     maxit=2000, b=None):
     return O.edfa_pipeline(sysd, mode=mode, form=form, variant=variant, dyn=dyn, solve=solve,
