@@ -80,6 +80,13 @@ __device__ __forceinline__ bool wait_flag(const int* flag, int epoch, DevErr* er
 template <class T>
 __device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
 
+// 1/x rounded to nearest: the same value as the IEEE division 1/x, from the
+// reciprocal intrinsics, which take fewer FP64 (FP32) instructions than a
+// division; used for the pivots of the dense per-cell factorisations, where
+// every warp-wide FP64 instruction occupies the narrow FP64 pipe of this part
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+
 // ------------------------------------------------------------------ CSR
 template <class T>
 struct Csr {
@@ -142,6 +149,7 @@ struct Factor {
     SweepPlan fwd, bwd;
     ChainPlan chf, chb;  // chain decomposition of the sweeps (k_chain.cu), used when ok
     int fac_R = 0;  // longest row (picks the shared-memory layout of the numeric factorisation)
+    const struct Ordering* ord = nullptr;  // set for an ordered factor: factorised colour by colour
 };
 
 // Packed per-CTA level chunks of both S~ sweeps for the single-cluster solve
@@ -186,6 +194,10 @@ struct Ordering {
     int32_t* iperm = nullptr;  // [n] original row -> ordered position
     std::vector<int32_t> cstart;  // host: first ordered row of every colour, [ncolours + 1]
     int32_t* cstart_dev = nullptr;  // the same on the device
+    // first row group of every colour in processing order, for groups of
+    // 32, 16, 8 and 4 rows (1, 2, 4, 8 lanes per row): [dir][lanes][ncolours + 1],
+    // dir 0 forward (colours ascending), 1 backward (descending)
+    int64_t* tstart_dev = nullptr;
 };
 
 // An ordered copy P M Q^T of a CSR matrix: pattern, the position in M of every
@@ -255,7 +267,7 @@ struct edfa_handle_s {
     // (P_s C P_a^T, P_a B P_s^T)
     edfa::Ordering oa, os;
     edfa::OrderedCsr ao, so, co, bo;
-    unsigned* coop_bar = nullptr;  // [2] grid-barrier state of the cooperative per-colour sweeps
+    int coop_ok = 0;  // cooperative launches possible (the dataflow sweeps of ordered factors)
     edfa::ClusterPlan cp;
     // sweep synchronisation
     int* flags = nullptr;          // [max(Nf, Ne)] completion epochs

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kDynWarps * 32) k_qsets_dynamic(DynArgs a)
             for (int kk = 0; kk < s; ++kk) {
                 const double d = M[kk * (kk + 1) / 2 + kk];
                 if (!(d < 0.0) || !isfinite(d)) { ok = false; break; }
-                const double inv = 1.0 / d;
+                const double inv = rcp_rn(d);
                 if (lane == 0) dv[kk] = inv;
                 const int n = s - kk - 1;
                 for (int t = lane; t < n; t += 32) {

@@ -606,9 +606,135 @@ k_ilu0(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr, const int32_t
     }
 }
 
+// ILU(0) of an ordered factor, one launch per colour: every dependency of a
+// row of colour c lies in an earlier colour, finished by an earlier launch,
+// so nothing is awaited and nothing is staged ahead.  A warp per row keeps the
+// row, a column -> position hash and its dependencies' 1/u_kk and U ranges in
+// shared memory (~3 KB, so up to 64 warps per SM) and reads the dependencies'
+// U rows through the caches.  The arithmetic and its order are those of
+// k_ilu0 (l_ik = a_ik (1/u_kk), then a_ij -= l_ik u_kj, dependencies in
+// ascending column order), so the factors are the same.
+template <int R_, int HB_>
+struct McFacLayout {
+    static constexpr int R = R_, HB = HB_, H = 1 << HB_;
+};
+
+template <class T, class L>
+struct alignas(16) McFacSmem {
+    T rv[L::R];          // the row being factored
+    T dk[L::R];          // 1 / u_kk of every dependency
+    long long ub[L::R];  // first U entry of every dependency
+    int ul[L::R];        // its U length
+    int rc[L::R];        // row columns
+    int hk[L::H];        // hash keys (column, -1 empty)
+    int hp[L::H];        // hash values (position in the row)
+};
+
+constexpr int kMcFacWarps = 8;
+
+template <class T, class L>
+__global__ void __launch_bounds__(kMcFacWarps * 32)
+k_ilu0_colour(int32_t r0, int32_t r1, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+              const int64_t* __restrict__ diag, const T* __restrict__ vals, T* lu, T* dinv, DevErr* err)
+{
+    extern __shared__ __align__(16) unsigned char mfs_raw[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    McFacSmem<T, L>& S = reinterpret_cast<McFacSmem<T, L>*>(mfs_raw)[wid];
+    const int64_t nw = (int64_t)gridDim.x * kMcFacWarps;
+    for (int64_t i = r0 + (int64_t)blockIdx.x * kMcFacWarps + wid; i < r1; i += nw) {
+        const int64_t b = rowptr[i], e = rowptr[i + 1];
+        const int len = (int)(e - b);
+        const int dpos = (int)(diag[i] - b);
+        if (len > L::R) {
+            if (lane == 0) raise_err(err, EDFA_ERR_BOUNDS, i);
+            continue;
+        }
+        for (int k = lane; k < L::H; k += 32) S.hk[k] = -1;
+        __syncwarp();
+        for (int u = lane; u < len; u += 32) {
+            const int j = col[b + u];
+            S.rv[u] = vals[b + u];
+            S.rc[u] = j;
+            int sl = (int)(((unsigned)j * 2654435769u) >> (32 - L::HB));
+            for (int it = 0; it < L::H; ++it) {
+                if (atomicCAS(&S.hk[sl], -1, j) == -1) { S.hp[sl] = u; break; }
+                sl = (sl + 1) & (L::H - 1);
+            }
+        }
+        // the dependencies' 1/u_kk and U ranges, all lanes at once
+        for (int u = lane; u < dpos; u += 32) {
+            const int k = S.rc[u];
+            const long long ubk = diag[k] + 1;
+            S.ub[u] = ubk;
+            S.ul[u] = (int)(rowptr[k + 1] - ubk);
+            S.dk[u] = dinv[k];
+        }
+        __syncwarp();
+        for (int t = 0; t < dpos; ++t) {
+            const T lik = S.rv[t] * S.dk[t];
+            __syncwarp();
+            if (lane == 0) S.rv[t] = lik;
+            const long long ubk = S.ub[t];
+            const int n_u = S.ul[t];
+            for (int q = lane; q < n_u; q += 32) {
+                const int j = col[ubk + q];
+                int sl = (int)(((unsigned)j * 2654435769u) >> (32 - L::HB));
+                int pos = -1;
+                for (int it = 0; it < L::H; ++it) {
+                    const int kk = S.hk[sl];
+                    if (kk == j) { pos = S.hp[sl]; break; }
+                    if (kk < 0) break;
+                    sl = (sl + 1) & (L::H - 1);
+                }
+                if (pos >= 0) S.rv[pos] -= lik * lu[ubk + q];
+            }
+            __syncwarp();
+        }
+        const T piv = S.rv[dpos];
+        for (int u = lane; u < len; u += 32) lu[b + u] = S.rv[u];
+        if (lane == 0) {
+            if (!(piv != T(0)) || !isfinite((double)piv)) raise_err(err, EDFA_ERR_BREAKDOWN, i);
+            dinv[i] = T(1) / piv;
+        }
+        __syncwarp();
+    }
+}
+
+template <class T, class L>
+static void ilu0_colour_launch(edfa_handle_s* h, const Factor& f, const Ordering& o, const T* vals, T* lu, T* dinv,
+                               cudaStream_t s)
+{
+    auto fn = k_ilu0_colour<T, L>;
+    const size_t smem = sizeof(McFacSmem<T, L>) * kMcFacWarps;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kMcFacWarps * 32, smem);
+    if (per < 1) per = 1;
+    for (int c = 0; c < o.ncolours; ++c) {
+        const int32_t r0 = o.cstart[c], r1 = o.cstart[c + 1];
+        if (r1 <= r0) continue;
+        int64_t blocks = ((int64_t)(r1 - r0) + kMcFacWarps - 1) / kMcFacWarps;
+        if (blocks > (int64_t)per * h->nsm) blocks = (int64_t)per * h->nsm;
+        (edfa::count_launch(), fn<<<(unsigned)blocks, kMcFacWarps * 32, smem, s>>>(r0, r1, f.rowptr, f.col, f.diag, vals,
+                                                                                  lu, dinv, h->err));
+    }
+}
+
 int factor_numeric(edfa_handle_s* h, Factor& f, const double* vals64, const float* vals32, cudaStream_t s)
 {
     if (f.n == 0) return EDFA_OK;
+    if (f.ord && f.fac_R <= 128) {
+        using L64 = McFacLayout<64, 7>;
+        using L128 = McFacLayout<128, 8>;
+        if (h->opt.precision == 1) {
+            if (f.fac_R <= 64) ilu0_colour_launch<float, L64>(h, f, *f.ord, vals32, f.lu32, f.dinv32, s);
+            else ilu0_colour_launch<float, L128>(h, f, *f.ord, vals32, f.lu32, f.dinv32, s);
+        } else {
+            if (f.fac_R <= 64) ilu0_colour_launch<double, L64>(h, f, *f.ord, vals64, f.lu64, f.dinv64, s);
+            else ilu0_colour_launch<double, L128>(h, f, *f.ord, vals64, f.lu64, f.dinv64, s);
+        }
+        return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+    }
     h->epoch += 1;
     if (h->epoch == INT_MAX) {
         h->epoch = 1;
@@ -951,10 +1077,8 @@ static int launch_sweep(edfa_handle_s* h, const Factor& f, const TB* base, const
 // resident wave, since a colour holds a few hundred thousand rows at most.
 constexpr int kMcThreads = 256;
 
-// rows [r0, r1) of one colour, grid-stride over warps; CG: read the earlier
-// colours' results through L2 (a persistent launch: another SM wrote them
-// after this SM may have cached the line)
-template <class T, class TB, class TO, int FWD, int LPR, bool CG>
+// rows [r0, r1) of one colour, grid-stride over warps
+template <class T, class TB, class TO, int FWD, int LPR>
 __device__ __forceinline__ void mc_rows(int64_t r0, int64_t r1, int64_t warp, int64_t nwarps,
                                         const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                         const T* __restrict__ lu, const int64_t* __restrict__ diag,
@@ -991,7 +1115,7 @@ __device__ __forceinline__ void mc_rows(int64_t r0, int64_t r1, int64_t warp, in
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u)
-                    if (c[u] >= 0) acc = fma(w[u], (T)(CG ? __ldcg(out + c[u]) : out[c[u]]), acc);
+                    if (c[u] >= 0) acc = fma(w[u], (T)out[c[u]], acc);
             }
             for (int64_t p0 = mb; p0 < me; p0 += U * LPR) {
                 int c[U];
@@ -1028,62 +1152,116 @@ k_mc_sweep(int32_t r0, int32_t r1, const int64_t* __restrict__ rowptr, const int
 {
     const int64_t warp = ((int64_t)blockIdx.x * kMcThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kMcThreads) >> 5;
-    mc_rows<T, TB, TO, FWD, LPR, false>(r0, r1, warp, nwarps, rowptr, col, lu, diag, dinv, base, bperm, mptr, mcol,
+    mc_rows<T, TB, TO, FWD, LPR>(r0, r1, warp, nwarps, rowptr, col, lu, diag, dinv, base, bperm, mptr, mcol,
                                         mval, mv, out, sperm, scat);
 }
 
-// Grid-wide barrier of a cooperative launch: bar[0] counts arrivals, bar[1] is
-// the generation; the last block to arrive resets the count and advances the
-// generation.  The wait is bounded: after kSpinLimit polls (or once any thread
-// has recorded an error) it records EDFA_ERR_TIMEOUT and returns false.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, DevErr* err)
+// blocks of the cooperative sweeps: 512 threads, two per SM (the register
+// budget of that shape holds the kernel without spills)
+constexpr int kMcAllThreads = 512;
+
+// All colours of one sweep in one cooperative launch without barriers
+// (dataflow): the row groups of RPW consecutive ordered rows (never straddling
+// two colours: every colour's rows are split into its own groups) are dealt to
+// the warps statically in processing order (colours ascending forward,
+// descending backward), and a row waits only for the results it reads, which
+// it polls in `out` (filled with the all-ones pattern before the launch;
+// arithmetic never produces it).  Deadlock free: a warp takes its groups in
+// processing order, a group depends only on groups earlier in that order, and
+// all warps are resident (cooperative launch); the earliest unfinished group
+// therefore has its inputs.  Every wait is bounded (a timeout records
+// EDFA_ERR_TIMEOUT and the value reads as 0).  tstart[l] = first group of the
+// l-th colour in processing order.
+template <class T, class TB, class TO, int FWD, int LPR>
+__global__ void __launch_bounds__(kMcAllThreads, 2)
+k_mc_sweep_df(int ncol, const int64_t* __restrict__ tstart, const int32_t* __restrict__ cstart,
+              const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const T* __restrict__ lu,
+              const int64_t* __restrict__ diag, const T* __restrict__ dinv, const TB* __restrict__ base,
+              const int32_t* __restrict__ bperm, const int64_t* __restrict__ mptr, const int32_t* __restrict__ mcol,
+              const T* __restrict__ mval, const TO* __restrict__ mv, TO* out, const int32_t* __restrict__ sperm,
+              double* scat, DevErr* err)
 {
-    __syncthreads();
-    __shared__ int ok;
-    if (threadIdx.x == 0) {
-        ok = 1;
-        const unsigned gen = (unsigned)ld_acquire((const int*)(bar + 1));
-        __threadfence();
-        if (atomicAdd(bar, 1u) == nblocks - 1) {
-            bar[0] = 0;
-            st_release((int*)(bar + 1), (int)(gen + 1));
-        } else {
-            unsigned ns = kBackoffMin, it = 0;
-            while ((unsigned)ld_acquire((const int*)(bar + 1)) == gen) {
-                if (++it >= kSpinLimit || ((it & 255u) == 0u && err_set(err))) {
-                    if (it >= kSpinLimit) raise_err(err, EDFA_ERR_TIMEOUT, -2);
-                    ok = 0;
-                    break;
+    constexpr int RPW = 32 / LPR;
+    constexpr int U = 4;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / LPR, gl = lane % LPR;
+    const int64_t warp = ((int64_t)blockIdx.x * kMcAllThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kMcAllThreads) >> 5;
+    const int64_t ntasks = tstart[ncol];
+    for (int64_t t = warp; t < ntasks; t += nwarps) {
+        int lo = 0, hi = ncol - 1;  // colour position: last l with tstart[l] <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tstart[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const int c = FWD ? lo : ncol - 1 - lo;
+        const int64_t i = (int64_t)cstart[c] + (t - tstart[lo]) * RPW + g;
+        const bool live = i < cstart[c + 1];
+        T acc = T(0), bi = T(0), di = T(1);
+        if (live) {
+            const int64_t rlo = FWD ? rowptr[i] : diag[i] + 1;
+            const int64_t rhi = FWD ? diag[i] : rowptr[i + 1];
+            bi = (T)to_d(base[bperm ? bperm[i] : i]);
+            if (!FWD) di = dinv[i];
+            int64_t mb = 0, me = 0;
+            if (mptr) { mb = mptr[i]; me = mptr[i + 1]; }
+            for (int64_t p0 = mb; p0 < me; p0 += U * LPR) {
+                int cc[U];
+                T w[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t p = p0 + gl + u * LPR;
+                    cc[u] = p < me ? mcol[p] : -1;
+                    w[u] = p < me ? mval[p] : T(0);
                 }
-                __nanosleep(ns);
-                if (ns < 64) ns <<= 1;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (cc[u] >= 0) acc = fma(w[u], (T)mv[cc[u]], acc);
+            }
+            for (int64_t p0 = rlo; p0 < rhi; p0 += U * LPR) {
+                int cc[U];
+                T w[U], x[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t p = p0 + gl + u * LPR;
+                    cc[u] = p < rhi ? col[p] : -1;
+                    w[u] = p < rhi ? lu[p] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) x[u] = cc[u] >= 0 ? (T)ld_poll(out + cc[u]) : T(0);
+                unsigned pending = 0;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (cc[u] >= 0 && is_sentinel(x[u])) pending |= 1u << u;
+                unsigned it = 0;
+                while (pending && it < (kSpinLimit << 2)) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if ((pending >> u) & 1u) {
+                            x[u] = (T)ld_poll(out + cc[u]);
+                            if (!is_sentinel(x[u])) pending &= ~(1u << u);
+                        }
+                    ++it;
+                    if ((it & 255u) == 0u && err_set(err)) break;
+                }
+                if (pending) {
+                    raise_err(err, EDFA_ERR_TIMEOUT, i);
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if ((pending >> u) & 1u) x[u] = T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (cc[u] >= 0) acc = fma(w[u], x[u], acc);
             }
         }
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
-// All colours of one sweep in one cooperative launch, a grid barrier between
-// colours (the per-colour launches' kernel boundaries cost several times more)
-template <class T, class TB, class TO, int FWD, int LPR>
-__global__ void __launch_bounds__(kMcThreads)
-k_mc_sweep_all(int ncol, const int32_t* __restrict__ cstart, const int64_t* __restrict__ rowptr,
-               const int32_t* __restrict__ col, const T* __restrict__ lu, const int64_t* __restrict__ diag,
-               const T* __restrict__ dinv, const TB* __restrict__ base, const int32_t* __restrict__ bperm,
-               const int64_t* __restrict__ mptr, const int32_t* __restrict__ mcol, const T* __restrict__ mval,
-               const TO* __restrict__ mv, TO* out, const int32_t* __restrict__ sperm, double* scat, unsigned* bar,
-               DevErr* err)
-{
-    const int64_t warp = ((int64_t)blockIdx.x * kMcThreads + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * kMcThreads) >> 5;
-    for (int k = 0; k < ncol; ++k) {
-        const int c = FWD ? k : ncol - 1 - k;
-        mc_rows<T, TB, TO, FWD, LPR, true>(cstart[c], cstart[c + 1], warp, nwarps, rowptr, col, lu, diag, dinv, base,
-                                           bperm, mptr, mcol, mval, mv, out, sperm, scat);
-        if (k + 1 < ncol) {
-            __threadfence();
-            if (!grid_barrier(bar, gridDim.x, err)) return;
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (live && gl == 0) {
+            T r = bi - acc;
+            if (!FWD) r *= di;
+            if (sperm) scat[sperm[i]] = (double)r;
+            st_relaxed(out + i, (TO)r);
         }
     }
 }
@@ -1093,28 +1271,30 @@ static void mc_launch(edfa_handle_s* h, const Factor& f, const Ordering& o, cons
                       const TB* base, const int32_t* bperm, const int64_t* mptr, const int32_t* mcol, const T* mval,
                       const TO* mv, TO* out, const int32_t* sperm, double* scat, cudaStream_t s)
 {
-    // one cooperative launch for all colours when the device supports it
-    if (o.ncolours > 1 && o.cstart_dev && h->coop_bar) {
-        auto fa = k_mc_sweep_all<T, TB, TO, FWD, LPR>;
+    // one cooperative dataflow launch for all colours when the device supports it
+    if (o.ncolours > 1 && o.tstart_dev && h->coop_ok) {
+        auto fd = k_mc_sweep_df<T, TB, TO, FWD, LPR>;
         static thread_local int per_dev = -1, per_sm = 0;
         int dev = 0;
         cudaGetDevice(&dev);
         if (dev != per_dev) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fa, kMcThreads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fd, kMcAllThreads, 0);
             per_dev = dev;
         }
         if (per_sm >= 1) {
-            cudaMemsetAsync(h->coop_bar, 0, 2 * sizeof(unsigned), s);
+            constexpr int li = LPR == 1 ? 0 : LPR == 2 ? 1 : LPR == 4 ? 2 : 3;
+            const int64_t* ts = o.tstart_dev + ((int64_t)(FWD ? 0 : 1) * 4 + li) * (o.ncolours + 1);
+            cudaMemsetAsync(out, 0xFF, (size_t)f.n * sizeof(TO), s);
             int ncol = o.ncolours;
-            void* args[] = {(void*)&ncol, (void*)&o.cstart_dev, (void*)&f.rowptr, (void*)&f.col, (void*)&lu,
-                            (void*)&f.diag, (void*)&dinv, (void*)&base, (void*)&bperm, (void*)&mptr, (void*)&mcol,
-                            (void*)&mval, (void*)&mv, (void*)&out, (void*)&sperm, (void*)&scat,
-                            (void*)&h->coop_bar, (void*)&h->err};
+            void* args[] = {(void*)&ncol, (void*)&ts, (void*)&o.cstart_dev, (void*)&f.rowptr, (void*)&f.col,
+                            (void*)&lu, (void*)&f.diag, (void*)&dinv, (void*)&base, (void*)&bperm, (void*)&mptr,
+                            (void*)&mcol, (void*)&mval, (void*)&mv, (void*)&out, (void*)&sperm, (void*)&scat,
+                            (void*)&h->err};
             edfa::count_launch();
-            if (cudaLaunchCooperativeKernel((const void*)fa, dim3((unsigned)(h->nsm * per_sm)), dim3(kMcThreads),
+            if (cudaLaunchCooperativeKernel((const void*)fd, dim3((unsigned)(h->nsm * per_sm)), dim3(kMcAllThreads),
                                             args, 0, s) == cudaSuccess)
                 return;
-            cudaGetLastError();  // not launchable as one cooperative grid: per-colour launches below
+            cudaGetLastError();
         }
     }
     auto fn = k_mc_sweep<T, TB, TO, FWD, LPR>;

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256) k_local(LocalArgs<T> a)
         for (int k = 0; k < s; ++k) {
             const T d = M[k * (k + 1) / 2 + k];
             if (bad_pivot(d)) { ok = false; break; }
-            const T inv = T(1) / d;
+            const T inv = rcp_rn(d);
             if (gl == 0) dv[k] = inv;
             const int n = s - k - 1;
             for (int t = gl; t < n; t += LPC) {

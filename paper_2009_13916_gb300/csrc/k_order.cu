@@ -331,10 +331,25 @@ int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr
     if (cudaStreamSynchronize(s) != cudaSuccess) return done(EDFA_ERR_CUDA);
     if ((rc = dalloc_t(h, &o.cstart_dev, (size_t)ncol + 1))) return done(rc);
     cudaMemcpyAsync(o.cstart_dev, o.cstart.data(), ((size_t)ncol + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    if (!h->coop_bar && (rc = dalloc_t(h, &h->coop_bar, 2))) return done(rc);
+    // row groups per colour for the dataflow sweeps
+    {
+        std::vector<int64_t> ts((size_t)2 * 4 * (ncol + 1), 0);
+        for (int dir = 0; dir < 2; ++dir)
+            for (int li = 0; li < 4; ++li) {
+                const int rpw = 32 >> li;
+                int64_t* t = ts.data() + ((size_t)dir * 4 + li) * (ncol + 1);
+                for (int l = 0; l < ncol; ++l) {
+                    const int c = dir == 0 ? l : ncol - 1 - l;
+                    t[l + 1] = t[l] + ((int64_t)o.cstart[c + 1] - o.cstart[c] + rpw - 1) / rpw;
+                }
+            }
+        if ((rc = dalloc_t(h, &o.tstart_dev, ts.size()))) return done(rc);
+        cudaMemcpyAsync(o.tstart_dev, ts.data(), ts.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return done(EDFA_ERR_CUDA);
+    }
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
-    if (!coop) h->coop_bar = nullptr;  // per-colour launches only
+    h->coop_ok = coop != 0;  // else per-colour launches
     o.on = 1;
     o.ncolours = ncol;
     return done(cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA);
@@ -432,6 +447,7 @@ static int factor_plan_ordered(edfa_handle_s* h, Factor& f, const Ordering& o, i
 {
     int rc = factor_plan_common(h, f, n, nnz, rowptr, col, s);
     if (rc) return rc;
+    f.ord = &o;
     if ((rc = plan_from_colours(h, f.fwd, o, 1, s))) return rc;
     return plan_from_colours(h, f.bwd, o, 0, s);
 }
