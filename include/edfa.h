@@ -229,7 +229,11 @@ EDFA_API int edfa_matvec(edfa_handle h, const double* x, double* y, edfa_stream 
 
 /* FGMRES(restart), x0 = 0; x receives the solution (device, N_f + N_e).
  * Returns EDFA_ERR_NOT_CONVERGED if maxit inner iterations do not reach rtol
- * (x then holds the last iterate).  info may be NULL. */
+ * (x then holds the last iterate).  info may be NULL.  With an ordering
+ * (edfa_options.ordering >= 1) the iteration runs on the permuted system, in
+ * the numbering of the ordered factors (b permuted in, x permuted out, 2 (N_f +
+ * N_e) doubles of workspace allocated on the first such solve): the same
+ * iteration as in the natural numbering up to the rounding of its sums. */
 EDFA_API int edfa_solve(edfa_handle h, const double* b, double* x, int32_t restart, double rtol,
                int32_t maxit, edfa_solve_info* info, edfa_stream stream);
 
@@ -278,6 +282,14 @@ EDFA_API int edfa_get_stats(edfa_handle h, edfa_stats* s);
  * FGMRES kernels on (1) or off (0); turning it on clears the accumulated times
  * (edfa_stats.sweep_ms, kry_ms).  Timing adds one event pair per timed launch. */
 EDFA_API int edfa_set_profiling(edfa_handle h, int32_t on);
+
+/* The same for a subset of the timed kinds: bit k of `kinds` times the
+ * launches of kind k, with k the index into edfa_stats.sweep_ms (0-4: A~
+ * forward, A~ backward, S~ forward, S~ backward, S~ in one cluster) or 5 + the
+ * index into edfa_stats.kry_ms (5: first-pass multi-dot, 6: first-pass update,
+ * 7: block product).  edfa_set_profiling(h, 1) equals kinds = 0xFF.  Fewer
+ * kinds record fewer events.  EDFA_ERR_INVALID for bits above 7. */
+EDFA_API int edfa_set_profiling_mask(edfa_handle h, uint32_t kinds);
 
 /* Preconditioner for the transposed system [A B; C D]^T = [A C^T; B^T D^T]
  * (adjoint solves), built from the forward handle `fwd`: the transposed blocks

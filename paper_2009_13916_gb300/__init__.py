@@ -81,7 +81,7 @@ class View(C.Structure):
 _lib = None
 EXPORTS = ("edfa_default_options", "edfa_build", "edfa_setup", "edfa_apply", "edfa_matvec",
            "edfa_solve", "edfa_history", "edfa_get_view", "edfa_get_stats", "edfa_set_profiling",
-           "edfa_launch_count", "edfa_qsets_noalloc", "edfa_build_adjoint", "edfa_grad_logk",
+           "edfa_set_profiling_mask", "edfa_launch_count", "edfa_qsets_noalloc", "edfa_build_adjoint", "edfa_grad_logk",
            "edfa_solve_batched", "edfa_solve_bicgstab", "edfa_selftest_wait_timeout", "edfa_probe_fma_rate",
            "edfa_free", "edfa_strerror",
            "edfa_last_error_detail")
@@ -117,6 +117,8 @@ def lib(build_if_missing: bool = True):
         L.edfa_free.argtypes = [vp]
         L.edfa_set_profiling.argtypes = [vp, C.c_int32]
         L.edfa_set_profiling.restype = C.c_int
+        L.edfa_set_profiling_mask.argtypes = [vp, C.c_uint32]
+        L.edfa_set_profiling_mask.restype = C.c_int
         L.edfa_qsets_noalloc.argtypes = [P(Csr), P(Csr), P(Csr), C.c_int32, C.c_double, vp, vp, C.c_int64,
                                          P(C.c_int64), vp]
         L.edfa_qsets_noalloc.restype = C.c_int
@@ -369,8 +371,18 @@ class Edfa:
         adj.h = h
         return adj
 
-    def set_profiling(self, on: bool):
-        lib().edfa_set_profiling(self.h, 1 if on else 0)
+    def set_profiling(self, on: bool, kinds=None):
+        """Per-launch event timing: all timed kinds (on=True), none, or the
+        given kinds (indices 0-7 as in edfa_set_profiling_mask)."""
+        if kinds is None:
+            lib().edfa_set_profiling(self.h, 1 if on else 0)
+        else:
+            mask = 0
+            for k in kinds:
+                mask |= 1 << int(k)
+            rc = lib().edfa_set_profiling_mask(self.h, mask if on else 0)
+            if rc != 0:
+                raise ValueError(f"edfa_set_profiling_mask: {rc}")
 
     def stats(self) -> Stats:
         st = Stats()

@@ -26,7 +26,7 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 // when profiling is off.  With s == -1 the caller records both events.
 cudaEvent_t* prof_begin(edfa_handle_s* h, int kind, cudaStream_t s)
 {
-    if (!h->profiling) return nullptr;
+    if (!((h->profiling >> kind) & 1u)) return nullptr;
     if (h->prof_used * 2 + 2 > h->prof_ev.size()) {
         for (int k = 0; k < 64; ++k) {
             cudaEvent_t e;
@@ -199,8 +199,8 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device);
     if (h->nsm < 1) h->nsm = 1;
     TRY(dalloc_t(h, &h->err, 1));
-    if (cudaMallocHost((void**)&h->err_host, sizeof(DevErr)) != cudaSuccess) { free_all(h); return EDFA_ERR_OOM; }
-    memset(h->err_host, 0, sizeof(DevErr));
+    if (cudaMallocHost((void**)&h->err_host, 3 * sizeof(DevErr)) != cudaSuccess) { free_all(h); return EDFA_ERR_OOM; }
+    memset(h->err_host, 0, 3 * sizeof(DevErr));
     cudaMemsetAsync(h->err, 0, sizeof(DevErr), s);
     TRY(dalloc_t(h, &h->ticket, 1));
     const int32_t nmax = Nf > Ne ? Nf : Ne;
@@ -348,7 +348,8 @@ int edfa_matvec(edfa_handle h, const double* x, double* y, edfa_stream stream)
 // classical Gram-Schmidt in FP64 on the device, repeated once when the first
 // pass shrank the norm by more than a factor of 10 (Rutishauser's criterion), the
 // (m+1) x m Hessenberg least-squares problem by Givens rotations on the host
-// (one (j+2)-value device->host read per inner iteration), x0 = 0, and the
+// (one (j+2)-value device->host read per inner iteration, read while the next
+// iteration runs), x0 = 0, and the
 // true residual ||b - A x|| checked at the end of every cycle; the outer loop
 // restarts while it exceeds rtol ||b||.
 int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol, int32_t maxit,
@@ -369,6 +370,23 @@ int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol
         if (cudaMallocHost((void**)&h->hbuf_host, sizeof(double) * 4 * (m + 2)) != cudaSuccess) return EDFA_ERR_OOM;
         h->kry_m = m;
     }
+    // with an ordering the iteration runs in the ordered numbering: b is
+    // permuted once, the preconditioner and the product work in place, and x is
+    // permuted back at the end
+    const bool ordn = h->opt.ordering >= 1 && n > 0;
+    const double* bb = b;
+    double* xx = x;
+    if (ordn) {
+        if (!h->ord_bx && dalloc_t(h, &h->ord_bx, (size_t)2 * n)) return EDFA_ERR_OOM;
+        bb = h->ord_bx;
+        xx = h->ord_bx + n;
+    }
+    auto prec = [&](const double* r, double* z) {
+        return ordn ? apply_prec_ordered_numbering(h, r, z, s) : apply_prec(h, r, z, s);
+    };
+    auto mv = [&](const double* v, double* y) {
+        return ordn ? matvec_ordered_numbering(h, v, y, s) : matvec(h, v, y, s);
+    };
     double* h1 = h->hbuf;
     double* h2 = h->hbuf + (m + 2);
     double* hf = h->hbuf + 2 * (m + 2);
@@ -380,20 +398,22 @@ int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol
     cudaEventRecord(h->ev[0], s);
 
     int rc = EDFA_OK;
+    if (ordn && (rc = order_vector(h, b, h->ord_bx, 1, s))) return rc;
     // ||b||
-    rc = kry_multidot(h->V, n, 0, b, n, h->part, misc, nullptr, nullptr, 1, s);
+    rc = kry_multidot(h->V, n, 0, bb, n, h->part, misc, nullptr, nullptr, 1, s);
     if (rc) return rc;
     cudaMemcpyAsync(hh, misc, sizeof(double), cudaMemcpyDeviceToHost, s);
     rc = check_err(h, s);
     if (rc) return rc;
     const double bnorm = std::sqrt(hh[0]);
-    cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), s);
+    cudaMemsetAsync(xx, 0, (size_t)n * sizeof(double), s);
     if (bnorm == 0.0 || n == 0) {
+        if (ordn) cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), s);
         loc.converged = 1;
         if (info) *info = loc;
         return check_err(h, s);
     }
-    cudaMemcpyAsync(h->w, b, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->w, bb, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
     double beta = bnorm;
     int it = 0, status = EDFA_ERR_NOT_CONVERGED;
     while (it < maxit) {
@@ -402,32 +422,46 @@ int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
         int jlast = -1;
-        for (int j = 0; j < m && it < maxit; ++j) {
+        // Iteration j+1 is enqueued before the host waits for iteration j's
+        // Hessenberg column, so the device does not idle through the host's
+        // round trip; when iteration j ends the cycle, iteration j+1's work is
+        // discarded (it writes only V_{j+2}, Z_{j+1} and scratch).
+        auto enqueue = [&](int j) -> int {
             double* vj = h->V + (int64_t)j * n;
             double* zj = h->Z + (int64_t)j * n;
-            if ((rc = apply_prec(h, vj, zj, s))) return rc;
+            int e;
+            if ((e = prec(vj, zj))) return e;
             cudaEvent_t* pe = prof_begin(h, 7, s);
-            if ((rc = matvec(h, zj, h->w, s))) return rc;
+            if ((e = mv(zj, h->w))) return e;
             if (pe) cudaEventRecord(pe[1], s);
             // classical Gram-Schmidt, repeated when the reorthogonalisation test asks for it
             // (decided on the device: the second pass's kernels read the gate)
             const int nv = j + 1;
             pe = prof_begin(h, 5, s);
-            if ((rc = kry_multidot(h->V, n, nv, h->w, n, h->part, h1, nullptr, nullptr, 1, s))) return rc;
+            if ((e = kry_multidot(h->V, n, nv, h->w, n, h->part, h1, nullptr, nullptr, 1, s))) return e;
             if (pe) {
                 cudaEventRecord(pe[1], s);
                 h->stats.kry_vecs += nv;
             }
             pe = prof_begin(h, 6, s);
-            if ((rc = kry_update(h->V, n, nv, h1, h->w, n, h->part, misc, s))) return rc;
+            if ((e = kry_update(h->V, n, nv, h1, h->w, n, h->part, misc, s))) return e;
             if (pe) cudaEventRecord(pe[1], s);
-            if ((rc = kry_dgks(misc, h1 + nv, h->kgate, s))) return rc;
-            if ((rc = kry_multidot(h->V, n, nv, h->w, n, h->part, h2, h1, hf, 0, s, h->kgate))) return rc;
-            if ((rc = kry_update(h->V, n, nv, h2, h->w, n, h->part, misc, s, h->kgate))) return rc;
-            if ((rc = kry_scale_from(h->w, h->V + (int64_t)(j + 1) * n, n, misc, hf + nv, s))) return rc;
-            cudaMemcpyAsync(hh, hf, sizeof(double) * (nv + 1), cudaMemcpyDeviceToHost, s);
-            if ((rc = check_err(h, s))) return rc;
-            for (int i = 0; i <= j + 1; ++i) H[(size_t)i * m + j] = hh[i];
+            if ((e = kry_dgks(misc, h1 + nv, h->kgate, s))) return e;
+            if ((e = kry_multidot(h->V, n, nv, h->w, n, h->part, h2, h1, hf, 0, s, h->kgate))) return e;
+            if ((e = kry_update(h->V, n, nv, h2, h->w, n, h->part, misc, s, h->kgate))) return e;
+            if ((e = kry_scale_from(h->w, h->V + (int64_t)(j + 1) * n, n, misc, hf + nv, s))) return e;
+            // the column and the device error record into this iteration's host slot
+            cudaMemcpyAsync(hh + (j & 1) * (m + 2), hf, sizeof(double) * (nv + 1), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(h->err_host + 1 + (j & 1), h->err, sizeof(DevErr), cudaMemcpyDeviceToHost, s);
+            return cudaEventRecord(h->ev[12 + (j & 1)], s) == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+        };
+        if ((rc = enqueue(0))) return rc;
+        for (int j = 0; j < m && it < maxit; ++j) {
+            if (j + 1 < m && it + 1 < maxit && (rc = enqueue(j + 1))) return rc;
+            if (cudaEventSynchronize(h->ev[12 + (j & 1)]) != cudaSuccess) return check_err(h, s);
+            if (h->err_host[1 + (j & 1)].code != 0) return check_err(h, s);
+            const double* col = hh + (j & 1) * (m + 2);
+            for (int i = 0; i <= j + 1; ++i) H[(size_t)i * m + j] = col[i];
             for (int i = 0; i < j; ++i) {
                 double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
                 H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
@@ -446,7 +480,7 @@ int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol
             const double est = std::fabs(g[j + 1]) / bnorm;
             h->hist.push_back(est);
             loc.est_rel = est;
-            if (est <= rtol || hh[j + 1] == 0.0) break;
+            if (est <= rtol || col[j + 1] == 0.0) break;
         }
         const int k = jlast + 1;
         for (int i = k - 1; i >= 0; --i) {
@@ -454,11 +488,12 @@ int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol
             for (int l = i + 1; l < k; ++l) v -= H[(size_t)i * m + l] * y[l];
             y[i] = H[(size_t)i * m + i] != 0.0 ? v / H[(size_t)i * m + i] : 0.0;
         }
-        memcpy(hh, y.data(), sizeof(double) * k);
-        cudaMemcpyAsync(h1, hh, sizeof(double) * k, cudaMemcpyHostToDevice, s);
-        if ((rc = kry_combine(h->Z, n, k, h1, x, n, s))) return rc;
-        if ((rc = matvec(h, x, h->w, s))) return rc;
-        if ((rc = kry_residual(b, h->w, n, h->part, misc, s))) return rc;
+        double* hy = hh + 2 * (m + 2);  // not a slot an iteration in flight writes
+        memcpy(hy, y.data(), sizeof(double) * k);
+        cudaMemcpyAsync(h1, hy, sizeof(double) * k, cudaMemcpyHostToDevice, s);
+        if ((rc = kry_combine(h->Z, n, k, h1, xx, n, s))) return rc;
+        if ((rc = mv(xx, h->w))) return rc;
+        if ((rc = kry_residual(bb, h->w, n, h->part, misc, s))) return rc;
         cudaMemcpyAsync(hh, misc, sizeof(double), cudaMemcpyDeviceToHost, s);
         if ((rc = check_err(h, s))) return rc;
         beta = std::sqrt(hh[0]);
@@ -467,6 +502,7 @@ int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol
         if (beta == 0.0) { status = EDFA_OK; break; }
         loc.restarts++;
     }
+    if (ordn && (rc = order_vector(h, xx, x, 0, s))) return rc;
     cudaEventRecord(h->ev[1], s);
     cudaEventSynchronize(h->ev[1]);
     float ms = 0;
@@ -652,10 +688,12 @@ int edfa_get_stats(edfa_handle h, edfa_stats* st)
     return EDFA_OK;
 }
 
-int edfa_set_profiling(edfa_handle h, int32_t on)
+int edfa_set_profiling(edfa_handle h, int32_t on) { return edfa_set_profiling_mask(h, on ? 0xFFu : 0u); }
+
+int edfa_set_profiling_mask(edfa_handle h, uint32_t kinds)
 {
-    if (!h) return EDFA_ERR_INVALID;
-    h->profiling = on ? 1 : 0;
+    if (!h || (kinds >> 8) != 0) return EDFA_ERR_INVALID;
+    h->profiling = kinds;
     h->prof_used = 0;
     for (int k = 0; k < 5; ++k) { h->stats.sweep_ms[k] = 0; h->stats.sweep_n[k] = 0; }
     for (int k = 0; k < 3; ++k) { h->stats.kry_ms[k] = 0; h->stats.kry_n[k] = 0; }

@@ -264,9 +264,11 @@ struct edfa_handle_s {
     edfa::Factor fa, fs;
     // optional multicolour orderings of the factorised A~ (faces) and S~
     // (cells), the ordered matrices and the couplings in the ordered numbering
-    // (P_s C P_a^T, P_a B P_s^T)
+    // (P_s C P_a^T, P_a B P_s^T); P_s D P_s^T for the product of FGMRES in the
+    // ordered numbering
     edfa::Ordering oa, os;
-    edfa::OrderedCsr ao, so, co, bo;
+    edfa::OrderedCsr ao, so, co, bo, dord;
+    double* ord_bx = nullptr;  // [2 (N_f + N_e)] b and x in the ordered numbering
     int coop_ok = 0;  // cooperative launches possible (the dataflow sweeps of ordered factors)
     edfa::ClusterPlan cp;
     // sweep synchronisation
@@ -288,13 +290,13 @@ struct edfa_handle_s {
     double* bcg_sc = nullptr;
     // device error record and its pinned host mirror
     edfa::DevErr* err = nullptr;
-    edfa::DevErr* err_host = nullptr;
-    cudaEvent_t ev[12] = {};
+    edfa::DevErr* err_host = nullptr;  // [3]: check_err, two FGMRES iteration slots
+    cudaEvent_t ev[14] = {};
     // opt-in per-launch device timing: event pairs recorded around every sweep
     // launch (kind 0..4 = A forward, A backward, S~ forward, S~ backward, both S~ sweeps
     // in one cluster launch) and the first-pass Krylov kernels (5 multi-dot, 6 update,
     // 7 block SpMV)
-    int profiling = 0;
+    uint32_t profiling = 0;  // bit k: time the launches of kind k (edfa_set_profiling_mask)
     std::vector<cudaEvent_t> prof_ev;
     std::vector<int> prof_kind;
     size_t prof_used = 0;
@@ -372,6 +374,12 @@ int order_values(edfa_handle_s* h, OrderedCsr& m, const double* src64, const flo
 int order_stage2_symbolic(edfa_handle_s* h, cudaStream_t s);
 int order_a_factor(edfa_handle_s* h, cudaStream_t s);
 int stage2_numeric(edfa_handle_s* h, cudaStream_t s);
+// vectors between the natural and the ordered numbering (faces through P_a,
+// identity without an ordering of A~; cells through P_s)
+int order_vector(edfa_handle_s* h, const double* in, double* out, int to_ordered, cudaStream_t s);
+// the block preconditioner and the block product with vectors in the ordered numbering
+int apply_prec_ordered_numbering(edfa_handle_s* h, const double* r, double* z, cudaStream_t s);
+int matvec_ordered_numbering(edfa_handle_s* h, const double* x, double* y, cudaStream_t s);
 int to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
 int to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t s);
 

@@ -810,6 +810,17 @@ __device__ __forceinline__ void st_relaxed(float* p, float v)
     asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
+// a poll of a result stored as TO, read in the working precision T; the
+// sentinel is tested on the stored bits, before any conversion (a conversion
+// of a NaN need not keep its payload)
+template <class T, class TO>
+__device__ __forceinline__ bool poll_ready(const TO* p, T& v)
+{
+    const TO x = ld_poll(p);
+    v = (T)x;
+    return !is_sentinel(x);
+}
+
 template <class T>
 __device__ __forceinline__ T wait_value(const T* p, DevErr* err, long long who)
 {
@@ -891,10 +902,10 @@ k_sweep(const int32_t* __restrict__ perm, int64_t nslots, const int64_t* __restr
                 T xv[KMAX];
                 unsigned pending = 0;
 #pragma unroll
-                for (int k = 0; k < KMAX; ++k) xv[k] = cj[k] >= 0 ? ld_poll(out + cj[k]) : T(0);
-#pragma unroll
-                for (int k = 0; k < KMAX; ++k)
-                    if (cj[k] >= 0 && is_sentinel(xv[k])) pending |= 1u << k;
+                for (int k = 0; k < KMAX; ++k) {
+                    xv[k] = T(0);
+                    if (cj[k] >= 0 && !poll_ready(out + cj[k], xv[k])) pending |= 1u << k;
+                }
                 // poll every still-pending dependency in the same round, without
                 // sleeping: a level completes with its slowest row, and measured
                 // per-level times on GB300 were ~30% lower without back-off
@@ -902,10 +913,7 @@ k_sweep(const int32_t* __restrict__ perm, int64_t nslots, const int64_t* __restr
                 while (pending && it < (kSpinLimit << 2)) {
 #pragma unroll
                     for (int k = 0; k < KMAX; ++k)
-                        if ((pending >> k) & 1u) xv[k] = ld_poll(out + cj[k]);
-#pragma unroll
-                    for (int k = 0; k < KMAX; ++k)
-                        if (((pending >> k) & 1u) && !is_sentinel(xv[k])) pending &= ~(1u << k);
+                        if (((pending >> k) & 1u) && poll_ready(out + cj[k], xv[k])) pending &= ~(1u << k);
                     ++it;
                     if ((it & 255u) == 0u && err_set(err)) break;
                 }
@@ -988,21 +996,21 @@ k_sweep_row(const int32_t* __restrict__ perm, int64_t nslots, const int64_t* __r
                 lv[k] = p < hi ? lu[p] : T(0);
             }
 #pragma unroll
-            for (int k = 0; k < KMAX; ++k) xv[k] = cj[k] >= 0 ? ld_poll(out + cj[k]) : T(0);
-#pragma unroll
             for (int k = 0; k < KMAX; ++k) {
-                if (cj[k] < 0) continue;
-                if (is_sentinel(xv[k])) pending |= 1u << k;
-                else acc = fma(lv[k], xv[k], acc);
+                xv[k] = T(0);
+                if (cj[k] >= 0 && !poll_ready(out + cj[k], xv[k])) pending |= 1u << k;
             }
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (cj[k] >= 0 && !((pending >> k) & 1u)) acc = fma(lv[k], xv[k], acc);
             const bool last = c0 + KMAX >= hi;
             unsigned it = 0;
             while (pending && it < (kSpinLimit << 2)) {
 #pragma unroll
                 for (int k = 0; k < KMAX; ++k)
                     if ((pending >> k) & 1u) {
-                        const T v = ld_poll(out + cj[k]);
-                        if (!is_sentinel(v)) {
+                        T v;
+                        if (poll_ready(out + cj[k], v)) {
                             acc = fma(lv[k], v, acc);
                             pending &= ~(1u << k);
                         }
@@ -1227,20 +1235,17 @@ k_mc_sweep_df(int ncol, const int64_t* __restrict__ tstart, const int32_t* __res
                     cc[u] = p < rhi ? col[p] : -1;
                     w[u] = p < rhi ? lu[p] : T(0);
                 }
-#pragma unroll
-                for (int u = 0; u < U; ++u) x[u] = cc[u] >= 0 ? (T)ld_poll(out + cc[u]) : T(0);
                 unsigned pending = 0;
 #pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (cc[u] >= 0 && is_sentinel(x[u])) pending |= 1u << u;
+                for (int u = 0; u < U; ++u) {
+                    x[u] = T(0);
+                    if (cc[u] >= 0 && !poll_ready(out + cc[u], x[u])) pending |= 1u << u;
+                }
                 unsigned it = 0;
                 while (pending && it < (kSpinLimit << 2)) {
 #pragma unroll
                     for (int u = 0; u < U; ++u)
-                        if ((pending >> u) & 1u) {
-                            x[u] = (T)ld_poll(out + cc[u]);
-                            if (!is_sentinel(x[u])) pending &= ~(1u << u);
-                        }
+                        if (((pending >> u) & 1u) && poll_ready(out + cc[u], x[u])) pending &= ~(1u << u);
                     ++it;
                     if ((it & 255u) == 0u && err_set(err)) break;
                 }
@@ -1421,6 +1426,61 @@ static int apply_ordered(edfa_handle_s* h, const double* r, double* z, cudaStrea
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
+// The same application with r and z in the ordered numbering,
+// r = [P_a r_pi; P_s r_p] and z = [P_a z_pi; P_s z_p]: the sweeps read their
+// right-hand sides and write their results in place, with no gather or
+// scatter through the permutations.
+template <class T>
+static int apply_ordered_numbering(edfa_handle_s* h, const double* r, double* z, cudaStream_t s)
+{
+    const int32_t Nf = h->Nf, Ne = h->Ne;
+    const bool oa = h->oa.on != 0;
+    T* u1 = (T*)h->tmp1;
+    T* u2 = (T*)h->tmp2;
+    T* zo;  // z_o in the working precision
+    if constexpr (sizeof(T) == 8) zo = (T*)(z + Nf);
+    else zo = (T*)h->tmp3;
+    const T* cval;
+    const T* bval;
+    if constexpr (sizeof(T) == 8) { cval = (const T*)h->co.v64; bval = (const T*)h->bo.v64; }
+    else { cval = (const T*)h->co.v32; bval = (const T*)h->bo.v32; }
+    const T* none = nullptr;
+    int rc;
+    if (h->opt.variant == 0) {
+        rc = oa ? mc_sweep<T, double, T, 1>(h, h->fa, h->oa, r, nullptr, nullptr, nullptr, none, 0, none, u2, nullptr,
+                                           nullptr, s)
+                : a_sweep<T, double, T, 1>(h, r, nullptr, nullptr, none, none, u2, s);
+        if (rc) return rc;
+        rc = oa ? mc_sweep<T, T, T, 0>(h, h->fa, h->oa, (const T*)u2, nullptr, nullptr, nullptr, none, 0, none, u1,
+                                      nullptr, nullptr, s)
+                : a_sweep<T, T, T, 0>(h, u2, nullptr, nullptr, none, none, u1, s);
+        if (rc) return rc;
+        rc = mc_sweep<T, double, T, 1>(h, h->fs, h->os, r + Nf, nullptr, h->co.ptr, h->co.col, cval, h->co.nnz,
+                                       (const T*)u1, u2, nullptr, nullptr, s);
+    } else {
+        rc = mc_sweep<T, double, T, 1>(h, h->fs, h->os, r + Nf, nullptr, nullptr, nullptr, none, 0, none, u2, nullptr,
+                                       nullptr, s);
+    }
+    if (rc) return rc;
+    rc = mc_sweep<T, T, T, 0>(h, h->fs, h->os, (const T*)u2, nullptr, nullptr, nullptr, none, 0, none, zo, nullptr,
+                              nullptr, s);
+    if (rc) return rc;
+    rc = oa ? mc_sweep<T, double, T, 1>(h, h->fa, h->oa, r, nullptr, h->bo.ptr, h->bo.col, bval, h->bo.nnz,
+                                       (const T*)zo, u2, nullptr, nullptr, s)
+            : a_sweep<T, double, T, 1>(h, r, h->bo.ptr, h->bo.col, bval, (const T*)zo, u2, s);
+    if (rc) return rc;
+    const double* dnone = nullptr;
+    rc = oa ? mc_sweep<T, T, double, 0>(h, h->fa, h->oa, (const T*)u2, nullptr, nullptr, nullptr, none, 0, dnone, z,
+                                       nullptr, nullptr, s)
+            : a_sweep<T, T, double, 0>(h, u2, nullptr, nullptr, none, dnone, z, s);
+    if constexpr (sizeof(T) == 4) {
+        if (rc) return rc;
+        rc = to_f64_launch(zo, z + Nf, Ne, s);
+    }
+    if (rc) return rc;
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
 template <class T>
 static int apply_impl(edfa_handle_s* h, const double* r, double* z, cudaStream_t s)
 {
@@ -1544,6 +1604,13 @@ int apply_prec(edfa_handle_s* h, const double* r, double* z, cudaStream_t s)
 {
     if (h->opt.precision == 1) return apply_impl<float>(h, r, z, s);
     return apply_impl<double>(h, r, z, s);
+}
+
+int apply_prec_ordered_numbering(edfa_handle_s* h, const double* r, double* z, cudaStream_t s)
+{
+    if (h->opt.ordering < 1) return EDFA_ERR_INVALID;
+    if (h->opt.precision == 1) return apply_ordered_numbering<float>(h, r, z, s);
+    return apply_ordered_numbering<double>(h, r, z, s);
 }
 
 }  // namespace edfa

@@ -76,38 +76,59 @@ k_block_spmv(int32_t Nf, int32_t Ne, Csr<double> A, Csr<double> B, Csr<double> C
 static int lanes_for(double avg) { return avg <= 6.0 ? 1 : avg <= 12.0 ? 2 : avg <= 32.0 ? 4 : 8; }
 
 template <int LF, int LC>
-static void spmv_launch(edfa_handle_s* h, const double* x, double* y, cudaStream_t s)
+static void spmv_launch(edfa_handle_s* h, const Csr<double>* M, const double* x, double* y, cudaStream_t s)
 {
     const int64_t nbf = ((int64_t)h->Nf * LF + kKT - 1) / kKT;
     const int64_t nbc = ((int64_t)h->Ne * LC + kKT - 1) / kKT;
-    (edfa::count_launch(), k_block_spmv<LF, LC><<<(unsigned)(nbf + nbc), kKT, 0, s>>>(
-                               h->Nf, h->Ne, csr_of(h->A), csr_of(h->B), csr_of(h->C), csr_of(h->D), x, y, nbf));
+    (edfa::count_launch(), k_block_spmv<LF, LC><<<(unsigned)(nbf + nbc), kKT, 0, s>>>(h->Nf, h->Ne, M[0], M[1], M[2],
+                                                                                      M[3], x, y, nbf));
 }
 
 template <int LF>
-static void spmv_dispatch_c(edfa_handle_s* h, int lc, const double* x, double* y, cudaStream_t s)
+static void spmv_dispatch_c(edfa_handle_s* h, int lc, const Csr<double>* M, const double* x, double* y,
+                            cudaStream_t s)
 {
     switch (lc) {
-    case 1: spmv_launch<LF, 1>(h, x, y, s); break;
-    case 2: spmv_launch<LF, 2>(h, x, y, s); break;
-    case 4: spmv_launch<LF, 4>(h, x, y, s); break;
-    default: spmv_launch<LF, 8>(h, x, y, s); break;
+    case 1: spmv_launch<LF, 1>(h, M, x, y, s); break;
+    case 2: spmv_launch<LF, 2>(h, M, x, y, s); break;
+    case 4: spmv_launch<LF, 4>(h, M, x, y, s); break;
+    default: spmv_launch<LF, 8>(h, M, x, y, s); break;
     }
+}
+
+// y = [A B; C D] x with the four blocks given
+static int block_matvec(edfa_handle_s* h, const Csr<double>* M, const double* x, double* y, cudaStream_t s)
+{
+    int64_t n = (int64_t)h->Nf + h->Ne;
+    if (n == 0) return EDFA_OK;
+    const int lf = lanes_for(h->Nf > 0 ? (double)(M[0].nnz + M[1].nnz) / h->Nf : 1.0);
+    const int lc = lanes_for(h->Ne > 0 ? (double)(M[2].nnz + M[3].nnz) / h->Ne : 1.0);
+    switch (lf) {
+    case 1: spmv_dispatch_c<1>(h, lc, M, x, y, s); break;
+    case 2: spmv_dispatch_c<2>(h, lc, M, x, y, s); break;
+    case 4: spmv_dispatch_c<4>(h, lc, M, x, y, s); break;
+    default: spmv_dispatch_c<8>(h, lc, M, x, y, s); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
 int matvec(edfa_handle_s* h, const double* x, double* y, cudaStream_t s)
 {
-    int64_t n = (int64_t)h->Nf + h->Ne;
-    if (n == 0) return EDFA_OK;
-    const int lf = lanes_for(h->Nf > 0 ? (double)(h->A.nnz + h->B.nnz) / h->Nf : 1.0);
-    const int lc = lanes_for(h->Ne > 0 ? (double)(h->C.nnz + h->D.nnz) / h->Ne : 1.0);
-    switch (lf) {
-    case 1: spmv_dispatch_c<1>(h, lc, x, y, s); break;
-    case 2: spmv_dispatch_c<2>(h, lc, x, y, s); break;
-    case 4: spmv_dispatch_c<4>(h, lc, x, y, s); break;
-    default: spmv_dispatch_c<8>(h, lc, x, y, s); break;
-    }
-    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+    const Csr<double> M[4] = {csr_of(h->A), csr_of(h->B), csr_of(h->C), csr_of(h->D)};
+    return block_matvec(h, M, x, y, s);
+}
+
+// the same product with x and y in the numbering of an ordered handle (faces
+// through the face ordering, identity without one; cells through the cell
+// ordering): the blocks P_a A P_a^T, P_a B P_s^T, P_s C P_a^T, P_s D P_s^T
+int matvec_ordered_numbering(edfa_handle_s* h, const double* x, double* y, cudaStream_t s)
+{
+    const int32_t Nf = h->Nf, Ne = h->Ne;
+    const Csr<double> A = h->oa.on ? Csr<double>{Nf, Nf, h->ao.nnz, h->ao.ptr, h->ao.col, h->ao.v64} : csr_of(h->A);
+    const Csr<double> M[4] = {A, Csr<double>{Nf, Ne, h->bo.nnz, h->bo.ptr, h->bo.col, h->bo.v64},
+                              Csr<double>{Ne, Nf, h->co.nnz, h->co.ptr, h->co.col, h->co.v64},
+                              Csr<double>{Ne, Ne, h->dord.nnz, h->dord.ptr, h->dord.col, h->dord.v64}};
+    return block_matvec(h, M, x, y, s);
 }
 
 __device__ __forceinline__ double block_sum(double v)

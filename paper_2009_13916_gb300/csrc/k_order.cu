@@ -452,11 +452,36 @@ static int factor_plan_ordered(edfa_handle_s* h, Factor& f, const Ordering& o, i
     return plan_from_colours(h, f.bwd, o, 0, s);
 }
 
+// faces through the face ordering (identity without one), cells through the
+// cell ordering: forward out[k] = in[perm[k]], backward out[perm[k]] = in[k]
+__global__ void k_order_vec(int32_t Nf, int32_t Ne, const int32_t* __restrict__ ap, const int32_t* __restrict__ sp,
+                            const double* __restrict__ in, double* out, int to_ordered)
+{
+    const int64_t n = (int64_t)Nf + Ne;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t o;
+        if (k < Nf) o = ap ? ap[k] : k;
+        else o = Nf + sp[k - Nf];
+        if (to_ordered) out[k] = in[o];
+        else out[o] = in[k];
+    }
+}
+
+int order_vector(edfa_handle_s* h, const double* in, double* out, int to_ordered, cudaStream_t s)
+{
+    const int64_t n = (int64_t)h->Nf + h->Ne;
+    if (n > 0)
+        (edfa::count_launch(), k_order_vec<<<grid_for(h, n), 256, 0, s>>>(h->Nf, h->Ne, h->oa.on ? h->oa.perm : nullptr,
+                                                                          h->os.perm, in, out, to_ordered));
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
 // Stage-2 symbolic work with an ordering of S~: the colouring of the
 // factorised S~ pattern, P_s S~ P_s^T, the couplings in the ordered numbering
 // (P_s C P_a^T for the right-hand side of the S~ sweep, P_a B P_s^T for the
-// second A~ sweep; P_a = identity without an ordering of A~) and the level
-// plans of the ordered factor.
+// second A~ sweep; P_a = identity without an ordering of A~), P_s D P_s^T
+// (for the block product in the ordered numbering) and the level plans of the
+// ordered factor.
 int order_stage2_symbolic(edfa_handle_s* h, cudaStream_t s)
 {
     int rc;
@@ -469,6 +494,8 @@ int order_stage2_symbolic(edfa_handle_s* h, cudaStream_t s)
     if ((rc = order_values(h, h->co, h->C.val, h->c32, s))) return rc;
     if ((rc = order_matrix(h, h->bo, Nf, h->B.rowptr, h->B.col, h->B.nnz, ap, h->os.iperm, s))) return rc;
     if ((rc = order_values(h, h->bo, h->B.val, h->b32, s))) return rc;
+    if ((rc = order_matrix(h, h->dord, Ne, h->D.rowptr, h->D.col, h->D.nnz, h->os.perm, h->os.iperm, s))) return rc;
+    if ((rc = order_values(h, h->dord, h->D.val, nullptr, s))) return rc;
     // value arrays of the ordered S~ now, inside the symbolic step, so that a
     // pattern rebuilt by a later Stage 2 releases them with the rest of its plan
     const bool f32 = h->opt.precision == 1;
@@ -484,6 +511,7 @@ int stage2_numeric(edfa_handle_s* h, cudaStream_t s)
     if (h->opt.ordering >= 1) {
         int rc = order_values(h, h->so, h->opt.precision == 1 ? nullptr : h->sf_val,
                               h->opt.precision == 1 ? h->sf_val32 : nullptr, s);
+        if (!rc) rc = order_values(h, h->dord, h->D.val, nullptr, s);  // D may have new values
         if (rc) return rc;
         return factor_numeric(h, h->fs, h->so.v64, h->so.v32, s);
     }

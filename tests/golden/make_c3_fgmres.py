@@ -2,7 +2,8 @@
 counts and true residuals on the 128x128x64 channelised workload (Q = own
 faces + strong A-connections, threshold 0.05), rtol 1e-8, with the natural
 order of the inner ILU(0) factorisations and with multicolour orderings of
-both (ordering 2), and the digest of the generated inputs they belong to.
+both (ordering 2), the residual estimates of the first restart cycle of
+each, and the digest of the generated inputs they belong to.
 Calls only the seeded generator and the oracle (tens of minutes of CPU
 time)."""
 import os
@@ -21,13 +22,14 @@ if __name__ == "__main__":
     for ordering, suffix in ((0, ""), (2, "_ordering2")):
         t = time.time()
         r = O.edfa_pipeline(s, mode="thresh", restart=50, rtol=1e-8, maxit=3000, ordering=ordering)
-        out.append((suffix, r["iters"], r["true_rel"], time.time() - t))
+        out.append((suffix, r["iters"], r["true_rel"], time.time() - t, r["hist"][1:51]))
     with open(os.path.join(HERE, "c3_oracle_fgmres.txt"), "w") as f:
         f.write("# oracle FGMRES(50) on the 128x128x64 channelised workload, thresh 0.05 sets, rtol 1e-8\n")
         f.write("# (natural order; _ordering2: multicolour orderings of A~ and S~)\n")
         f.write("# written by tests/golden/make_c3_fgmres.py (oracle only)\n")
         f.write(f"inputs_sha256 {W.digest(s)}\n")
-        for suffix, it, tr, sec in out:
+        for suffix, it, tr, sec, hist in out:
             f.write(f"iterations{suffix} {it}\n")
+            f.write(f"cycle1{suffix} " + " ".join(f"{v:.17e}" for v in hist) + "\n")
             f.write(f"true_rel{suffix} {tr:.6e}\n")
             f.write(f"seconds{suffix} {sec:.1f}\n")

@@ -38,6 +38,20 @@ def oracle_iterations(sysd):
     return int(r["iters"])
 
 
+def check_first_cycle(h, suffix, sysd):
+    """Residual estimates of the first restart cycle against the oracle's
+    (stored beside its counts): the GPU iteration is the oracle's up to
+    rounding, so the two agree closely before rounding differences compound."""
+    g = golden()
+    key = "cycle1" + suffix
+    if g.get("inputs_sha256") != W.digest(sysd) or key not in g:
+        return
+    ref = np.array([float(v) for v in g[key].split()])
+    hist = np.asarray(h.history())[1: 1 + len(ref)]
+    assert len(hist) == len(ref)
+    assert np.allclose(hist, ref, rtol=1e-6, atol=0), np.abs(hist / ref - 1).max()
+
+
 def test_config3_full_size():
     import torch
     if not torch.cuda.is_available():
@@ -60,6 +74,7 @@ def test_config3_full_size():
     assert info.converged and res <= 1.05e-8
     it_orc = oracle_iterations(sysd)
     assert abs(info.iterations - it_orc) <= 1, (info.iterations, it_orc)
+    check_first_cycle(h, "", sysd)
     h.close()
     h32 = gpu_handle(sysd, mode="thresh", thresh=0.05, precision=1)
     x32, info32 = h32.solve(b, restart=50, rtol=1e-8, maxit=3000)
@@ -83,9 +98,14 @@ def test_config3_full_size_multicolour_ordering():
     (ordering 2, the benchmark's configuration): colourings and orderings
     bit-exact, ordered factor patterns bit-exact and values within 1e-10 of
     the oracle's ILU(0) of the ordered matrices, one application within 1e-9,
-    FGMRES within one iteration of the oracle's count with the same orderings
-    (stored beside the natural one) and converged to 1e-8; FP32-mixed
-    converges too."""
+    FGMRES converged to 1e-8 with the first cycle's residual estimates within
+    1e-6 of the oracle's and the count within 0.5% of the oracle's with the same
+    orderings (stored beside the natural one); FP32-mixed converges too.
+    The library runs this FGMRES in the ordered numbering, the oracle in the
+    natural one: FGMRES is invariant under a symmetric permutation of the
+    system in exact arithmetic (inner products and norms are unchanged), but
+    the dot products are summed in another order, and over the 17 restart
+    cycles of this solve the rounding moves the count by a few iterations."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -118,7 +138,8 @@ def test_config3_full_size_multicolour_ordering():
         it_orc = int(g["iterations_ordering2"])
     else:
         it_orc = O.fgmres(Pc, sysd.b, 50, 1e-8, 3000)["iters"]
-    assert abs(info.iterations - it_orc) <= 1, (info.iterations, it_orc)
+    assert abs(info.iterations - it_orc) <= max(1, 0.005 * it_orc), (info.iterations, it_orc)
+    check_first_cycle(h, "_ordering2", sysd)
     h.close()
     h32 = gpu_handle(sysd, mode="thresh", thresh=0.05, precision=1, ordering=2)
     x32, info32 = h32.solve(b, restart=50, rtol=1e-8, maxit=3000)
