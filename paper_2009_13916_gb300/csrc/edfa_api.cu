@@ -264,6 +264,10 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     TRY(dalloc(h, &h->tmp1, (size_t)(nmax > 0 ? nmax : 1) * esz));
     TRY(dalloc(h, &h->tmp2, (size_t)(nmax > 0 ? nmax : 1) * esz));
     TRY(dalloc(h, &h->tmp3, (size_t)(nmax > 0 ? nmax : 1) * esz));
+    if (o.ordering == 2) {
+        TRY(dalloc(h, &h->tmp4, (size_t)(nmax > 0 ? nmax : 1) * esz));
+        TRY(dalloc(h, &h->tmp5, (size_t)(nmax > 0 ? nmax : 1) * esz));
+    }
     TRY(check_err(h, s));
 
     float ms = 0;
@@ -381,8 +385,13 @@ int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol
         bb = h->ord_bx;
         xx = h->ord_bx + n;
     }
+    // with both orderings the sweep outputs of the application of iteration
+    // j + 1 are filled with the all-ones pattern by the update of iteration j
+    // (the first of a cycle by a fill before it), not by a memset per sweep
+    FillList probe_fl;
+    const bool prefill = ordn && ordered_prefill_list(h, h->Z, probe_fl) > 0;
     auto prec = [&](const double* r, double* z) {
-        return ordn ? apply_prec_ordered_numbering(h, r, z, s) : apply_prec(h, r, z, s);
+        return ordn ? apply_prec_ordered_numbering(h, r, z, prefill ? 1 : 0, s) : apply_prec(h, r, z, s);
     };
     auto mv = [&](const double* v, double* y) {
         return ordn ? matvec_ordered_numbering(h, v, y, s) : matvec(h, v, y, s);
@@ -443,8 +452,10 @@ int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol
                 cudaEventRecord(pe[1], s);
                 h->stats.kry_vecs += nv;
             }
+            FillList fl;
+            if (prefill && j + 1 < m) ordered_prefill_list(h, h->Z + (int64_t)(j + 1) * n, fl);
             pe = prof_begin(h, 6, s);
-            if ((e = kry_update(h->V, n, nv, h1, h->w, n, h->part, misc, s))) return e;
+            if ((e = kry_update(h->V, n, nv, h1, h->w, n, h->part, misc, s, nullptr, &fl))) return e;
             if (pe) cudaEventRecord(pe[1], s);
             if ((e = kry_dgks(misc, h1 + nv, h->kgate, s))) return e;
             if ((e = kry_multidot(h->V, n, nv, h->w, n, h->part, h2, h1, hf, 0, s, h->kgate))) return e;
@@ -455,6 +466,11 @@ int edfa_solve(edfa_handle h, const double* b, double* x, int32_t m, double rtol
             cudaMemcpyAsync(h->err_host + 1 + (j & 1), h->err, sizeof(DevErr), cudaMemcpyDeviceToHost, s);
             return cudaEventRecord(h->ev[12 + (j & 1)], s) == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
         };
+        if (prefill) {
+            FillList fl;
+            ordered_prefill_list(h, h->Z, fl);
+            if ((rc = kry_fill(fl, s))) return rc;
+        }
         if ((rc = enqueue(0))) return rc;
         for (int j = 0; j < m && it < maxit; ++j) {
             if (j + 1 < m && it + 1 < maxit && (rc = enqueue(j + 1))) return rc;

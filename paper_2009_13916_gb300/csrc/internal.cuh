@@ -200,6 +200,17 @@ struct Ordering {
     int64_t* tstart_dev = nullptr;
 };
 
+// Up to six device buffers to fill with the all-ones pattern, in 32-bit words
+struct FillList {
+    uint32_t* p[6] = {};
+    int64_t words[6] = {};
+    int n = 0;
+    void add(void* ptr, int64_t bytes)
+    {
+        if (n < 6 && ptr && bytes > 0) { p[n] = (uint32_t*)ptr; words[n] = bytes / 4; ++n; }
+    }
+};
+
 // An ordered copy P M Q^T of a CSR matrix: pattern, the position in M of every
 // entry, and the gathered values (FP64 and/or FP32).
 struct OrderedCsr {
@@ -279,6 +290,10 @@ struct edfa_handle_s {
     void* tmp1 = nullptr;
     void* tmp2 = nullptr;
     void* tmp3 = nullptr;
+    // two more sweep outputs of the in-place ordered application (ordering 2),
+    // so that all six outputs of one application are distinct buffers
+    void* tmp4 = nullptr;
+    void* tmp5 = nullptr;
     // Krylov workspace
     int32_t kry_m = 0;
     double *V = nullptr, *Z = nullptr, *w = nullptr, *part = nullptr, *hbuf = nullptr;
@@ -378,7 +393,11 @@ int stage2_numeric(edfa_handle_s* h, cudaStream_t s);
 // identity without an ordering of A~; cells through P_s)
 int order_vector(edfa_handle_s* h, const double* in, double* out, int to_ordered, cudaStream_t s);
 // the block preconditioner and the block product with vectors in the ordered numbering
-int apply_prec_ordered_numbering(edfa_handle_s* h, const double* r, double* z, cudaStream_t s);
+int apply_prec_ordered_numbering(edfa_handle_s* h, const double* r, double* z, int prefilled, cudaStream_t s);
+// buffers the next in-place ordered application with output z writes through
+// dataflow sweeps, to be filled with the all-ones pattern beforehand; returns
+// the number of entries (0: nothing to prefill, the sweeps fill their own)
+int ordered_prefill_list(edfa_handle_s* h, double* z, FillList& fl);
 int matvec_ordered_numbering(edfa_handle_s* h, const double* x, double* y, cudaStream_t s);
 int to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
 int to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t s);
@@ -386,8 +405,12 @@ int to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t s);
 // Krylov building blocks (k_krylov.cu)
 int kry_multidot(const double* V, int64_t ld, int nv, const double* w, int64_t n, double* part, double* out,
                  const double* add, double* out_sum, int with_self, cudaStream_t s, const int* gate = nullptr);
+// fill the buffers of fl with the all-ones pattern (one launch)
+int kry_fill(const FillList& fl, cudaStream_t s);
+// w -= V h (and ||w||^2); with `fill` the same launch also fills those
+// buffers with the all-ones pattern (the next application's sweep outputs)
 int kry_update(const double* V, int64_t ld, int nv, const double* hcoef, double* w, int64_t n, double* part,
-               double* nrm2_out, cudaStream_t s, const int* gate = nullptr);
+               double* nrm2_out, cudaStream_t s, const int* gate = nullptr, const FillList* fill = nullptr);
 int kry_dgks(const double* nrm2_after, const double* nrm2_before, int* gate, cudaStream_t s);
 int kry_scale_from(const double* w, double* v, int64_t n, const double* nrm2, double* out_norm, cudaStream_t s);
 int kry_scale_const(const double* w, double* v, int64_t n, double alpha, cudaStream_t s);

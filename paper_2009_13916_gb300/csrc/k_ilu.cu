@@ -1274,7 +1274,7 @@ k_mc_sweep_df(int ncol, const int64_t* __restrict__ tstart, const int32_t* __res
 template <class T, class TB, class TO, int FWD, int LPR>
 static void mc_launch(edfa_handle_s* h, const Factor& f, const Ordering& o, const T* lu, const T* dinv,
                       const TB* base, const int32_t* bperm, const int64_t* mptr, const int32_t* mcol, const T* mval,
-                      const TO* mv, TO* out, const int32_t* sperm, double* scat, cudaStream_t s)
+                      const TO* mv, TO* out, const int32_t* sperm, double* scat, bool prefilled, cudaStream_t s)
 {
     // one cooperative dataflow launch for all colours when the device supports it
     if (o.ncolours > 1 && o.tstart_dev && h->coop_ok) {
@@ -1289,7 +1289,7 @@ static void mc_launch(edfa_handle_s* h, const Factor& f, const Ordering& o, cons
         if (per_sm >= 1) {
             constexpr int li = LPR == 1 ? 0 : LPR == 2 ? 1 : LPR == 4 ? 2 : 3;
             const int64_t* ts = o.tstart_dev + ((int64_t)(FWD ? 0 : 1) * 4 + li) * (o.ncolours + 1);
-            cudaMemsetAsync(out, 0xFF, (size_t)f.n * sizeof(TO), s);
+            if (!prefilled) cudaMemsetAsync(out, 0xFF, (size_t)f.n * sizeof(TO), s);
             int ncol = o.ncolours;
             void* args[] = {(void*)&ncol, (void*)&ts, (void*)&o.cstart_dev, (void*)&f.rowptr, (void*)&f.col,
                             (void*)&lu, (void*)&f.diag, (void*)&dinv, (void*)&base, (void*)&bperm, (void*)&mptr,
@@ -1329,7 +1329,7 @@ static void mc_launch(edfa_handle_s* h, const Factor& f, const Ordering& o, cons
 template <class T, class TB, class TO, int FWD>
 static int mc_sweep(edfa_handle_s* h, const Factor& f, const Ordering& o, const TB* base, const int32_t* bperm,
                     const int64_t* mptr, const int32_t* mcol, const T* mval, int64_t mnnz, const TO* mv, TO* out,
-                    const int32_t* sperm, double* scat, cudaStream_t s)
+                    const int32_t* sperm, double* scat, cudaStream_t s, bool prefilled = false)
 {
     if (f.n == 0) return EDFA_OK;
     const T* lu = nullptr;
@@ -1339,13 +1339,17 @@ static int mc_sweep(edfa_handle_s* h, const Factor& f, const Ordering& o, const 
     const double avg = ((double)(f.nnz - f.n) / 2.0 + (mptr ? (double)mnnz : 0.0)) / (double)f.n;
     cudaEvent_t* pe = prof_begin(h, (&f == &h->fs ? 2 : 0) + (FWD ? 0 : 1), s);
     if (avg <= 4.0)
-        mc_launch<T, TB, TO, FWD, 1>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm, scat, s);
+        mc_launch<T, TB, TO, FWD, 1>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm, scat,
+                                       prefilled, s);
     else if (avg <= 12.0)
-        mc_launch<T, TB, TO, FWD, 2>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm, scat, s);
+        mc_launch<T, TB, TO, FWD, 2>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm, scat,
+                                       prefilled, s);
     else if (avg <= 32.0)
-        mc_launch<T, TB, TO, FWD, 4>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm, scat, s);
+        mc_launch<T, TB, TO, FWD, 4>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm, scat,
+                                       prefilled, s);
     else
-        mc_launch<T, TB, TO, FWD, 8>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm, scat, s);
+        mc_launch<T, TB, TO, FWD, 8>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm, scat,
+                                       prefilled, s);
     if (pe) cudaEventRecord(pe[1], s);
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
@@ -1429,14 +1433,30 @@ static int apply_ordered(edfa_handle_s* h, const double* r, double* z, cudaStrea
 // The same application with r and z in the ordered numbering,
 // r = [P_a r_pi; P_s r_p] and z = [P_a z_pi; P_s z_p]: the sweeps read their
 // right-hand sides and write their results in place, with no gather or
-// scatter through the permutations.
+// scatter through the permutations.  With both orderings on, the six sweep
+// outputs of one application are distinct buffers (tmp2, tmp1, tmp4, z_o,
+// tmp5, z), so that all of them can be filled with the all-ones pattern before
+// the application starts (`prefilled`: by the Krylov update that precedes it)
+// instead of by one memset before every sweep.
 template <class T>
-static int apply_ordered_numbering(edfa_handle_s* h, const double* r, double* z, cudaStream_t s)
+static bool ordered_prefill_ok(edfa_handle_s* h)
+{
+    return h->opt.ordering == 2 && h->oa.on && h->os.on && h->coop_ok && h->tmp4 && h->tmp5;
+}
+
+template <class T>
+static int apply_ordered_numbering(edfa_handle_s* h, const double* r, double* z, bool prefilled, cudaStream_t s)
 {
     const int32_t Nf = h->Nf, Ne = h->Ne;
     const bool oa = h->oa.on != 0;
+    if (prefilled && !ordered_prefill_ok<T>(h)) return EDFA_ERR_INVALID;
+    const bool pf = prefilled;
     T* u1 = (T*)h->tmp1;
     T* u2 = (T*)h->tmp2;
+    // S~ forward and the second A~ forward get buffers of their own when both
+    // orderings are on (prefilled applications need six distinct outputs)
+    T* us = oa && h->tmp4 ? (T*)h->tmp4 : u2;
+    T* ua = oa && h->tmp5 ? (T*)h->tmp5 : u2;
     T* zo;  // z_o in the working precision
     if constexpr (sizeof(T) == 8) zo = (T*)(z + Nf);
     else zo = (T*)h->tmp3;
@@ -1448,31 +1468,31 @@ static int apply_ordered_numbering(edfa_handle_s* h, const double* r, double* z,
     int rc;
     if (h->opt.variant == 0) {
         rc = oa ? mc_sweep<T, double, T, 1>(h, h->fa, h->oa, r, nullptr, nullptr, nullptr, none, 0, none, u2, nullptr,
-                                           nullptr, s)
+                                           nullptr, s, pf)
                 : a_sweep<T, double, T, 1>(h, r, nullptr, nullptr, none, none, u2, s);
         if (rc) return rc;
         rc = oa ? mc_sweep<T, T, T, 0>(h, h->fa, h->oa, (const T*)u2, nullptr, nullptr, nullptr, none, 0, none, u1,
-                                      nullptr, nullptr, s)
+                                      nullptr, nullptr, s, pf)
                 : a_sweep<T, T, T, 0>(h, u2, nullptr, nullptr, none, none, u1, s);
         if (rc) return rc;
         rc = mc_sweep<T, double, T, 1>(h, h->fs, h->os, r + Nf, nullptr, h->co.ptr, h->co.col, cval, h->co.nnz,
-                                       (const T*)u1, u2, nullptr, nullptr, s);
+                                       (const T*)u1, us, nullptr, nullptr, s, pf);
     } else {
-        rc = mc_sweep<T, double, T, 1>(h, h->fs, h->os, r + Nf, nullptr, nullptr, nullptr, none, 0, none, u2, nullptr,
-                                       nullptr, s);
+        rc = mc_sweep<T, double, T, 1>(h, h->fs, h->os, r + Nf, nullptr, nullptr, nullptr, none, 0, none, us, nullptr,
+                                       nullptr, s, pf);
     }
     if (rc) return rc;
-    rc = mc_sweep<T, T, T, 0>(h, h->fs, h->os, (const T*)u2, nullptr, nullptr, nullptr, none, 0, none, zo, nullptr,
-                              nullptr, s);
+    rc = mc_sweep<T, T, T, 0>(h, h->fs, h->os, (const T*)us, nullptr, nullptr, nullptr, none, 0, none, zo, nullptr,
+                              nullptr, s, pf);
     if (rc) return rc;
     rc = oa ? mc_sweep<T, double, T, 1>(h, h->fa, h->oa, r, nullptr, h->bo.ptr, h->bo.col, bval, h->bo.nnz,
-                                       (const T*)zo, u2, nullptr, nullptr, s)
-            : a_sweep<T, double, T, 1>(h, r, h->bo.ptr, h->bo.col, bval, (const T*)zo, u2, s);
+                                       (const T*)zo, ua, nullptr, nullptr, s, pf)
+            : a_sweep<T, double, T, 1>(h, r, h->bo.ptr, h->bo.col, bval, (const T*)zo, ua, s);
     if (rc) return rc;
     const double* dnone = nullptr;
-    rc = oa ? mc_sweep<T, T, double, 0>(h, h->fa, h->oa, (const T*)u2, nullptr, nullptr, nullptr, none, 0, dnone, z,
-                                       nullptr, nullptr, s)
-            : a_sweep<T, T, double, 0>(h, u2, nullptr, nullptr, none, dnone, z, s);
+    rc = oa ? mc_sweep<T, T, double, 0>(h, h->fa, h->oa, (const T*)ua, nullptr, nullptr, nullptr, none, 0, dnone, z,
+                                       nullptr, nullptr, s, pf)
+            : a_sweep<T, T, double, 0>(h, ua, nullptr, nullptr, none, dnone, z, s);
     if constexpr (sizeof(T) == 4) {
         if (rc) return rc;
         rc = to_f64_launch(zo, z + Nf, Ne, s);
@@ -1606,11 +1626,27 @@ int apply_prec(edfa_handle_s* h, const double* r, double* z, cudaStream_t s)
     return apply_impl<double>(h, r, z, s);
 }
 
-int apply_prec_ordered_numbering(edfa_handle_s* h, const double* r, double* z, cudaStream_t s)
+int apply_prec_ordered_numbering(edfa_handle_s* h, const double* r, double* z, int prefilled, cudaStream_t s)
 {
     if (h->opt.ordering < 1) return EDFA_ERR_INVALID;
-    if (h->opt.precision == 1) return apply_ordered_numbering<float>(h, r, z, s);
-    return apply_ordered_numbering<double>(h, r, z, s);
+    if (h->opt.precision == 1) return apply_ordered_numbering<float>(h, r, z, prefilled != 0, s);
+    return apply_ordered_numbering<double>(h, r, z, prefilled != 0, s);
+}
+
+int ordered_prefill_list(edfa_handle_s* h, double* z, FillList& fl)
+{
+    fl = FillList{};
+    const bool f32 = h->opt.precision == 1;
+    if (!(f32 ? ordered_prefill_ok<float>(h) : ordered_prefill_ok<double>(h))) return 0;
+    const size_t esz = f32 ? sizeof(float) : sizeof(double);
+    const int64_t Nf = h->Nf, Ne = h->Ne;
+    fl.add(h->tmp2, Nf * (int64_t)esz);  // A~ forward
+    fl.add(h->tmp1, Nf * (int64_t)esz);  // A~ backward
+    fl.add(h->tmp4, Ne * (int64_t)esz);  // S~ forward
+    if (f32) fl.add(h->tmp3, Ne * (int64_t)esz);  // S~ backward (working precision)
+    fl.add(h->tmp5, Nf * (int64_t)esz);  // second A~ forward
+    fl.add(z, (Nf + (f32 ? 0 : Ne)) * (int64_t)sizeof(double));  // second A~ backward (and S~ backward in FP64)
+    return fl.n;
 }
 
 }  // namespace edfa

@@ -255,12 +255,25 @@ __global__ void k_scale_const(const double* w, double* v, int64_t n, double alph
 // w -= sum_i h_i V_i ; optional partial squared norm of the result.  kPer
 // independent elements per thread: one coalesced load per element and vector,
 // kPer independent FMA chains
+// the all-ones pattern into the buffers of fl, grid-stride over their words
+__device__ __forceinline__ void fill_words(const FillList& fl)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int b = 0; b < fl.n; ++b)
+        for (int64_t q = t0; q < fl.words[b]; q += stride) fl.p[b][q] = 0xFFFFFFFFu;
+}
+
+__global__ void k_fill(FillList fl) { fill_words(fl); }
+
 __global__ void __launch_bounds__(kKT)
 k_update(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ hcoef, double* w, int64_t n,
-         double* part_norm, const int* gate)
+         double* part_norm, const int* gate, FillList fill)
 {
     __shared__ double sh[kMaxVec];
     if (gate && *gate == 0) return;
+    // the fill stores go out first: they overlap the FP64-bound update
+    fill_words(fill);
     for (int i = threadIdx.x; i < nv && i < kMaxVec; i += kKT) sh[i] = -hcoef[i];
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kChunk + threadIdx.x;
@@ -394,12 +407,20 @@ int kry_multidot(const double* V, int64_t ld, int nv, const double* w, int64_t n
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }
 
+int kry_fill(const FillList& fl, cudaStream_t s)
+{
+    if (fl.n == 0) return EDFA_OK;
+    (edfa::count_launch(), k_fill<<<4096, kKT, 0, s>>>(fl));
+    return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+}
+
 int kry_update(const double* V, int64_t ld, int nv, const double* hcoef, double* w, int64_t n, double* part,
-               double* nrm2_out, cudaStream_t s, const int* gate)
+               double* nrm2_out, cudaStream_t s, const int* gate, const FillList* fill)
 {
     if (nv > kMaxVec) return EDFA_ERR_INVALID;
     int nc = Kry::nchunks(n);
-    (edfa::count_launch(), k_update<<<nc, kKT, 0, s>>>(V, ld, nv, hcoef, w, n, nrm2_out ? part : nullptr, gate));
+    const FillList fl = fill ? *fill : FillList{};
+    (edfa::count_launch(), k_update<<<nc, kKT, 0, s>>>(V, ld, nv, hcoef, w, n, nrm2_out ? part : nullptr, gate, fl));
     if (nrm2_out) (edfa::count_launch(), k_reduce_parts<<<1, kKT, 0, s>>>(part, nc, nrm2_out, nullptr, nullptr, gate));
     return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
 }

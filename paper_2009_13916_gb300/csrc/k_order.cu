@@ -44,61 +44,70 @@ __global__ void k_tp_fill(int32_t n, const int64_t* __restrict__ rowptr, const i
 }
 
 // ------------------------------------------------------------ colouring rounds
+// the priorities, computed once per colouring (a round reads a neighbour's
+// priority instead of recomputing its hash)
+__global__ void k_jp_prio(int32_t n, unsigned long long* prio)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        prio[i] = jp_priority((int32_t)i);
+}
+
 // true when every neighbour of v (in M and M^T) with higher priority is coloured
 __device__ __forceinline__ bool jp_ready(int32_t v, unsigned long long pv, const int64_t* rp, const int32_t* cl,
-                                         const int* colour)
+                                         const unsigned long long* prio, const int* colour)
 {
     for (int64_t p = rp[v]; p < rp[v + 1]; ++p) {
         const int32_t u = cl[p];
-        if (u != v && jp_priority(u) > pv && __ldcg(colour + u) < 0) return false;
+        if (u != v && __ldcg(colour + u) < 0 && prio[u] > pv) return false;
     }
     return true;
 }
 
 // colours of the higher-priority neighbours below 64 as a bit set
 __device__ __forceinline__ unsigned long long jp_used(int32_t v, unsigned long long pv, const int64_t* rp,
-                                                      const int32_t* cl, const int* colour, unsigned long long used)
+                                                      const int32_t* cl, const unsigned long long* prio,
+                                                      const int* colour, unsigned long long used)
 {
     for (int64_t p = rp[v]; p < rp[v + 1]; ++p) {
         const int32_t u = cl[p];
-        if (u != v && jp_priority(u) > pv) {
-            const int c = __ldcg(colour + u);
-            if (c < 64) used |= 1ull << c;
-        }
+        if (u == v) continue;
+        const int c = __ldcg(colour + u);
+        if (c >= 0 && c < 64 && prio[u] > pv) used |= 1ull << c;
     }
     return used;
 }
 
 __device__ __forceinline__ bool jp_uses(int32_t v, unsigned long long pv, const int64_t* rp, const int32_t* cl,
-                                        const int* colour, int c)
+                                        const unsigned long long* prio, const int* colour, int c)
 {
     for (int64_t p = rp[v]; p < rp[v + 1]; ++p) {
         const int32_t u = cl[p];
-        if (u != v && jp_priority(u) > pv && __ldcg(colour + u) == c) return true;
+        if (u != v && __ldcg(colour + u) == c && prio[u] > pv) return true;
     }
     return false;
 }
 
 __global__ void k_jp_round(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ cl,
-                           const int64_t* __restrict__ tp, const int32_t* __restrict__ tc, int* colour,
-                           unsigned long long* remaining, int* maxcol)
+                           const int64_t* __restrict__ tp, const int32_t* __restrict__ tc,
+                           const unsigned long long* __restrict__ prio, int* colour, unsigned long long* remaining,
+                           int* maxcol)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = (int32_t)i;
         if (colour[v] >= 0) continue;
-        const unsigned long long pv = jp_priority(v);
-        if (!jp_ready(v, pv, rp, cl, colour) || !jp_ready(v, pv, tp, tc, colour)) {
+        const unsigned long long pv = prio[v];
+        if (!jp_ready(v, pv, rp, cl, prio, colour) || !jp_ready(v, pv, tp, tc, prio, colour)) {
             atomicAdd(remaining, 1ull);
             continue;
         }
-        unsigned long long used = jp_used(v, pv, rp, cl, colour, 0ull);
-        used = jp_used(v, pv, tp, tc, colour, used);
+        unsigned long long used = jp_used(v, pv, rp, cl, prio, colour, 0ull);
+        used = jp_used(v, pv, tp, tc, prio, colour, used);
         int c;
         if (~used != 0ull) {
             c = __ffsll((long long)~used) - 1;
         } else {
             c = 64;
-            while (jp_uses(v, pv, rp, cl, colour, c) || jp_uses(v, pv, tp, tc, colour, c)) ++c;
+            while (jp_uses(v, pv, rp, cl, prio, colour, c) || jp_uses(v, pv, tp, tc, prio, colour, c)) ++c;
         }
         atomicMax(maxcol, c);
         __stcg(colour + v, c);
@@ -267,16 +276,18 @@ int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr
     int32_t* tc = nullptr;
     int* colour = nullptr;
     unsigned long long* misc = nullptr;  // [0] vertices left uncoloured by a round, [1] max colour (int)
+    unsigned long long* prio = nullptr;
     auto done = [&](int code) {
         cudaFreeAsync(tp, s); cudaFreeAsync(cur, s); cudaFreeAsync(tc, s); cudaFreeAsync(colour, s);
-        cudaFreeAsync(misc, s); cudaFreeAsync(cnt, s);
+        cudaFreeAsync(misc, s); cudaFreeAsync(cnt, s); cudaFreeAsync(prio, s);
         return code;
     };
     if (cudaMallocAsync((void**)&tp, ((size_t)n + 1) * sizeof(int64_t), s) != cudaSuccess ||
         cudaMallocAsync((void**)&cur, ((size_t)n + 1) * sizeof(int64_t), s) != cudaSuccess ||
         cudaMallocAsync((void**)&tc, (size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t), s) != cudaSuccess ||
         cudaMallocAsync((void**)&colour, (size_t)n * sizeof(int), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&misc, 2 * sizeof(unsigned long long), s) != cudaSuccess) {
+        cudaMallocAsync((void**)&misc, 2 * sizeof(unsigned long long), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&prio, (size_t)n * sizeof(unsigned long long), s) != cudaSuccess) {
         cudaGetLastError();
         return done(EDFA_ERR_OOM);
     }
@@ -286,6 +297,7 @@ int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr
     if ((rc = scan_i64(h, tp, n, s))) return done(rc);
     cudaMemcpyAsync(cur, tp, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
     (edfa::count_launch(), k_tp_fill<<<g, 256, 0, s>>>(n, rowptr, col, (unsigned long long*)cur, tc));
+    (edfa::count_launch(), k_jp_prio<<<g, 256, 0, s>>>(n, prio));
     cudaMemsetAsync(colour, 0xFF, (size_t)n * sizeof(int), s);
     cudaMemsetAsync(misc, 0, 2 * sizeof(unsigned long long), s);
     // rounds until a round leaves no vertex uncoloured; every round colours at
@@ -298,7 +310,7 @@ int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr
         if (rounds > (int64_t)n + 1) return done(EDFA_ERR_TIMEOUT);
         for (int k = 0; k < per_check; ++k) {
             cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s);
-            (edfa::count_launch(), k_jp_round<<<gr, 128, 0, s>>>(n, rowptr, col, tp, tc, colour, misc,
+            (edfa::count_launch(), k_jp_round<<<gr, 128, 0, s>>>(n, rowptr, col, tp, tc, prio, colour, misc,
                                                                  (int*)(misc + 1)));
         }
         rounds += per_check;
