@@ -61,13 +61,16 @@ __global__ void __launch_bounds__(256) k_local(LocalArgs<T> a)
     const int g = lane / LPC, gl = lane % LPC;
     const int P = a.pitch;
     const int tri = P * (P + 1) / 2;
-    const int per_cell = tri + (NRHS + 2) * P;
+    // odd strides (in elements) between the cells' records: the groups of a
+    // warp (every lane, with one lane per cell) then address different banks
+    const int per_cell = (tri + (NRHS + 2) * P) | 1;
+    const int qstride = P | 1;
     const int slot = wid * G + g;
     T* M = (T*)smem_raw + (size_t)slot * per_cell;
     T* rhs = M + tri;
     T* lc = rhs + NRHS * P;
     T* dv = lc + P;
-    int* q = (int*)((T*)smem_raw + (size_t)nw * G * per_cell) + (size_t)slot * P;
+    int* q = (int*)((T*)smem_raw + (size_t)nw * G * per_cell) + (size_t)slot * qstride;
     const unsigned gmask = (LPC == 32) ? 0xffffffffu : (((1u << LPC) - 1u) << (g * LPC));
     const long long ngroups = (long long)gridDim.x * nw * G;
 
@@ -177,7 +180,7 @@ static int launch_local_t(edfa_handle_s* h, const LocalArgs<T>& a, int warps, cu
 {
     constexpr int G = 32 / LPC;
     const int P = a.pitch;
-    const size_t per_cell = (size_t)(P * (P + 1) / 2 + (NRHS + 2) * P) * sizeof(T) + (size_t)P * sizeof(int);
+    const size_t per_cell = (size_t)((P * (P + 1) / 2 + (NRHS + 2) * P) | 1) * sizeof(T) + (size_t)(P | 1) * sizeof(int);
     size_t smem = per_cell * G * warps;
     while (warps > 1 && smem > 220 * 1024) { --warps; smem = per_cell * G * warps; }
     if (smem > 220 * 1024) return EDFA_ERR_BOUNDS;
@@ -213,6 +216,9 @@ static std::vector<std::pair<TuneKey, TuneVal>> g_tune;
 template <class T, int NRHS>
 static int launch_local_cfg(edfa_handle_s* h, const LocalArgs<T>& a, int lpc, int warps, cudaStream_t s)
 {
+    if (lpc == 1) return launch_local_t<T, NRHS, 1>(h, a, warps, s);
+    if (lpc == 2) return launch_local_t<T, NRHS, 2>(h, a, warps, s);
+    if (lpc == 4) return launch_local_t<T, NRHS, 4>(h, a, warps, s);
     if (lpc == 8) return launch_local_t<T, NRHS, 8>(h, a, warps, s);
     if (lpc == 16) return launch_local_t<T, NRHS, 16>(h, a, warps, s);
     return launch_local_t<T, NRHS, 32>(h, a, warps, s);
@@ -240,9 +246,13 @@ static int launch_local_n(edfa_handle_s* h, const LocalArgs<T>& a, cudaStream_t 
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
             float best = 1e30f;
-            const int lpcs[3] = {8, 16, 32};
+            // small sets (pitch <= 16) also try fewer lanes per cell, down to
+            // one cell per lane: every FP64 instruction then carries more
+            // cells, at the price of shared memory per warp
+            const int lpcs[6] = {8, 16, 32, 4, 2, 1};
+            const int nl = a.pitch <= 16 ? 6 : 3;
             const int wps[2] = {4, 8};
-            for (int li = 0; li < 3; ++li)
+            for (int li = 0; li < nl; ++li)
                 for (int wi = 0; wi < 2; ++wi) {
                     const int c = lpcs[li], w = wps[wi];
                     if (launch_local_cfg<T, NRHS>(h, sample, c, w, s)) { cudaGetLastError(); continue; }

@@ -52,23 +52,35 @@ __global__ void k_jp_prio(int32_t n, unsigned long long* prio)
         prio[i] = jp_priority((int32_t)i);
 }
 
-// true when every neighbour of v (in M and M^T) with higher priority is coloured
-__device__ __forceinline__ bool jp_ready(int32_t v, unsigned long long pv, const int64_t* rp, const int32_t* cl,
-                                         const unsigned long long* prio, const int* colour)
+// A group of G lanes examines one vertex v: every lane takes every G-th entry
+// of the rows of v in M and in M^T, and the group combines the lanes' findings
+// (G consecutive lanes, G a power of two uniform over the warp, group mask gm).
+__device__ __forceinline__ bool grp_any(bool x, unsigned gm) { return (__ballot_sync(0xffffffffu, x) & gm) != 0u; }
+
+__device__ __forceinline__ unsigned long long grp_or(unsigned long long x, int G)
 {
-    for (int64_t p = rp[v]; p < rp[v + 1]; ++p) {
-        const int32_t u = cl[p];
-        if (u != v && __ldcg(colour + u) < 0 && prio[u] > pv) return false;
-    }
-    return true;
+    for (int o = G / 2; o > 0; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
 }
 
-// colours of the higher-priority neighbours below 64 as a bit set
+// some neighbour u of v (in M and M^T) has higher priority and no colour yet
+__device__ __forceinline__ bool jp_blocked(int32_t v, unsigned long long pv, const int64_t* rp, const int32_t* cl,
+                                           const unsigned long long* prio, const int* colour, int gl, int G)
+{
+    for (int64_t p = rp[v] + gl; p < rp[v + 1]; p += G) {
+        const int32_t u = cl[p];
+        if (u != v && __ldcg(colour + u) < 0 && prio[u] > pv) return true;
+    }
+    return false;
+}
+
+// colours below 64 of the higher-priority neighbours, as a bit set
 __device__ __forceinline__ unsigned long long jp_used(int32_t v, unsigned long long pv, const int64_t* rp,
                                                       const int32_t* cl, const unsigned long long* prio,
-                                                      const int* colour, unsigned long long used)
+                                                      const int* colour, int gl, int G)
 {
-    for (int64_t p = rp[v]; p < rp[v + 1]; ++p) {
+    unsigned long long used = 0ull;
+    for (int64_t p = rp[v] + gl; p < rp[v + 1]; p += G) {
         const int32_t u = cl[p];
         if (u == v) continue;
         const int c = __ldcg(colour + u);
@@ -78,39 +90,86 @@ __device__ __forceinline__ unsigned long long jp_used(int32_t v, unsigned long l
 }
 
 __device__ __forceinline__ bool jp_uses(int32_t v, unsigned long long pv, const int64_t* rp, const int32_t* cl,
-                                        const unsigned long long* prio, const int* colour, int c)
+                                        const unsigned long long* prio, const int* colour, int c, int gl, int G)
 {
-    for (int64_t p = rp[v]; p < rp[v + 1]; ++p) {
+    for (int64_t p = rp[v] + gl; p < rp[v + 1]; p += G) {
         const int32_t u = cl[p];
         if (u != v && __ldcg(colour + u) == c && prio[u] > pv) return true;
     }
     return false;
 }
 
-__global__ void k_jp_round(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ cl,
-                           const int64_t* __restrict__ tp, const int32_t* __restrict__ tc,
-                           const unsigned long long* __restrict__ prio, int* colour, unsigned long long* remaining,
-                           int* maxcol)
+__global__ void k_jp_iota(int32_t n, int32_t* wl)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t v = (int32_t)i;
-        if (colour[v] >= 0) continue;
-        const unsigned long long pv = prio[v];
-        if (!jp_ready(v, pv, rp, cl, prio, colour) || !jp_ready(v, pv, tp, tc, prio, colour)) {
-            atomicAdd(remaining, 1ull);
-            continue;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        wl[i] = (int32_t)i;
+}
+
+// One round over the worklist of still uncoloured vertices: a vertex whose
+// higher-priority neighbours are all coloured takes the smallest colour they
+// do not use, the others go to the next round's list (appended a warp at a
+// time; the list's order does not matter, the colouring is the greedy one in
+// priority order whatever the order of work).  Long lists take one lane per
+// vertex (most vertices stop at their first blocking neighbour); short lists,
+// the last rounds, where a round lasts as long as its slowest vertex, take 8
+// or 32 lanes per vertex, by the mean row length.  The counts rotate over
+// three words: round r reads wcnt[r % 3], appends to wcnt[(r + 1) % 3] and
+// clears wcnt[(r + 2) % 3] for round r + 1.  A round with an empty list does
+// nothing.
+__global__ void k_jp_round(const int64_t* __restrict__ rp, const int32_t* __restrict__ cl,
+                           const int64_t* __restrict__ tp, const int32_t* __restrict__ tc,
+                           const unsigned long long* __restrict__ prio, int* colour, const int32_t* __restrict__ wl_in,
+                           int32_t* wl_out, unsigned* wcnt, int r, int gwide, int* maxcol)
+{
+    const unsigned m = wcnt[r % 3];
+    unsigned* out_cnt = wcnt + (r + 1) % 3;
+    if (blockIdx.x == 0 && threadIdx.x == 0) wcnt[(r + 2) % 3] = 0u;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int G = (int64_t)m >= nwarps * 32 ? 1 : gwide;  // uniform over the grid
+    const int VPW = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const int gi = lane / G, gl = lane % G;
+    const unsigned gm = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gi * G));
+    for (int64_t b = warp * VPW; b < m; b += nwarps * VPW) {
+        const int64_t i = b + gi;
+        const bool live = i < m;
+        const int32_t v = live ? wl_in[i] : 0;
+        const unsigned long long pv = live ? prio[v] : 0ull;
+        bool blk = live && (jp_blocked(v, pv, rp, cl, prio, colour, gl, G) ||
+                            jp_blocked(v, pv, tp, tc, prio, colour, gl, G));
+        blk = grp_any(blk, gm);
+        const bool go = live && !blk;
+        unsigned long long used = 0ull;
+        if (go) used = jp_used(v, pv, rp, cl, prio, colour, gl, G) | jp_used(v, pv, tp, tc, prio, colour, gl, G);
+        used = grp_or(used, G);
+        int c = 0;
+        if (go) {
+            if (~used != 0ull) c = __ffsll((long long)~used) - 1;
+            else c = 64;
         }
-        unsigned long long used = jp_used(v, pv, rp, cl, prio, colour, 0ull);
-        used = jp_used(v, pv, tp, tc, prio, colour, used);
-        int c;
-        if (~used != 0ull) {
-            c = __ffsll((long long)~used) - 1;
-        } else {
-            c = 64;
-            while (jp_uses(v, pv, rp, cl, prio, colour, c) || jp_uses(v, pv, tp, tc, prio, colour, c)) ++c;
+        // the rare vertex whose higher-priority neighbours hold all colours
+        // below 64 (every lane of the warp takes part in the group votes)
+        bool more = go && c >= 64;
+        while (__any_sync(0xffffffffu, more)) {
+            bool hit = more && (jp_uses(v, pv, rp, cl, prio, colour, c, gl, G) ||
+                                jp_uses(v, pv, tp, tc, prio, colour, c, gl, G));
+            hit = grp_any(hit, gm);
+            if (more && hit) ++c;
+            else more = false;
         }
-        atomicMax(maxcol, c);
-        __stcg(colour + v, c);
+        if (go && gl == 0) {
+            atomicMax(maxcol, c);
+            __stcg(colour + v, c);
+        }
+        const bool defer = live && blk && gl == 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, defer);
+        if (bal) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(out_cnt, (unsigned)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (defer) wl_out[base + __popc(bal & ((1u << lane) - 1u))] = v;
+        }
     }
 }
 
@@ -277,9 +336,12 @@ int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr
     int* colour = nullptr;
     unsigned long long* misc = nullptr;  // [0] vertices left uncoloured by a round, [1] max colour (int)
     unsigned long long* prio = nullptr;
+    int32_t* wl = nullptr;  // [2 n] worklists of uncoloured vertices
+    unsigned* wcnt = nullptr;  // [3] their lengths, rotating
     auto done = [&](int code) {
         cudaFreeAsync(tp, s); cudaFreeAsync(cur, s); cudaFreeAsync(tc, s); cudaFreeAsync(colour, s);
-        cudaFreeAsync(misc, s); cudaFreeAsync(cnt, s); cudaFreeAsync(prio, s);
+        cudaFreeAsync(misc, s); cudaFreeAsync(cnt, s); cudaFreeAsync(prio, s); cudaFreeAsync(wl, s);
+        cudaFreeAsync(wcnt, s);
         return code;
     };
     if (cudaMallocAsync((void**)&tp, ((size_t)n + 1) * sizeof(int64_t), s) != cudaSuccess ||
@@ -287,7 +349,9 @@ int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr
         cudaMallocAsync((void**)&tc, (size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t), s) != cudaSuccess ||
         cudaMallocAsync((void**)&colour, (size_t)n * sizeof(int), s) != cudaSuccess ||
         cudaMallocAsync((void**)&misc, 2 * sizeof(unsigned long long), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&prio, (size_t)n * sizeof(unsigned long long), s) != cudaSuccess) {
+        cudaMallocAsync((void**)&prio, (size_t)n * sizeof(unsigned long long), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&wl, (size_t)2 * n * sizeof(int32_t), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&wcnt, 3 * sizeof(unsigned), s) != cudaSuccess) {
         cudaGetLastError();
         return done(EDFA_ERR_OOM);
     }
@@ -302,20 +366,27 @@ int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr
     cudaMemsetAsync(misc, 0, 2 * sizeof(unsigned long long), s);
     // rounds until a round leaves no vertex uncoloured; every round colours at
     // least the uncoloured vertex of highest priority, so n rounds always end it
+    (edfa::count_launch(), k_jp_iota<<<g, 256, 0, s>>>(n, wl));
+    {
+        const unsigned init[3] = {(unsigned)n, 0u, 0u};
+        cudaMemcpyAsync(wcnt, init, sizeof init, cudaMemcpyHostToDevice, s);
+    }
     int64_t rounds = 0;
-    int per_check = 4;
-    unsigned long long left = 1;
+    int per_check = 8;
+    unsigned left = 1;
     const unsigned gr = grid_for(h, n, 128);
+    // lanes per vertex from the mean number of entries of its rows in M and M^T
+    const bool wide = n > 0 && 2.0 * (double)nnz / (double)n > 48.0;
     while (left > 0) {
         if (rounds > (int64_t)n + 1) return done(EDFA_ERR_TIMEOUT);
-        for (int k = 0; k < per_check; ++k) {
-            cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s);
-            (edfa::count_launch(), k_jp_round<<<gr, 128, 0, s>>>(n, rowptr, col, tp, tc, prio, colour, misc,
-                                                                 (int*)(misc + 1)));
+        for (int k = 0; k < per_check; ++k, ++rounds) {
+            const int32_t* win = wl + (rounds & 1) * (int64_t)n;
+            int32_t* wout = wl + ((rounds + 1) & 1) * (int64_t)n;
+            (edfa::count_launch(), k_jp_round<<<gr, 128, 0, s>>>(rowptr, col, tp, tc, prio, colour, win, wout, wcnt,
+                                                                 (int)(rounds % 3), wide ? 32 : 8, (int*)(misc + 1)));
         }
-        rounds += per_check;
         if (per_check < 64) per_check *= 2;
-        cudaMemcpyAsync(&left, misc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&left, wcnt + rounds % 3, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return done(EDFA_ERR_CUDA);
     }
     int maxcol = 0;

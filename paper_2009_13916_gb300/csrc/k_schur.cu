@@ -7,7 +7,9 @@
 //
 // Two passes, one warp per row of S~: a shared-memory hash set collects the
 // column candidates (cells m whose set Q^(m) meets the faces reached from row
-// E) and pass 0 counts them.  The numeric pass (k_schur_num) sorts them, maps
+// E; in the one-sided form the (cell, X~ value) pairs of all faces of the row
+// are loaded at once, the lanes taking the flattened list) and pass 0 counts
+// them.  The numeric pass (k_schur_num) sorts them, maps
 // every column to its position through the same hash, and forms the row as a
 // row-wise (Gustavson) product: for every face f of row E of C in ascending
 // order, the lanes take the cells m of row f of X~ (distinct within one f) and
@@ -220,7 +222,42 @@ __global__ void __launch_bounds__(kSWarps * 32) k_schur_count(SchurArgs<T> a)
         if (lane == 0) { if (hs_insert(tab, (int)E)) atomicAdd(&s_cnt[wid], 1); }
         for (int64_t p = a.D.rowptr[E] + lane; p < a.D.rowptr[E + 1]; p += 32)
             if (hs_insert(tab, a.D.col[p])) atomicAdd(&s_cnt[wid], 1);
-        if (a.form == 0) {
+        const int64_t cb = a.C.rowptr[E];
+        const int nf = (int)(a.C.rowptr[E + 1] - cb);
+        if (a.form == 0 && nf <= 32) {
+            // the cells of all faces' X~ rows at once (flattened, as in the
+            // numeric pass), not face after face
+            int64_t fb = 0;
+            int flen = 0;
+            if (lane < nf) {
+                const int f = a.C.col[cb + lane];
+                fb = a.xr_ptr[f];
+                flen = (int)(a.xr_ptr[f + 1] - fb);
+            }
+            int inc = flen;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const int fpre = inc - flen;
+            const int L = __shfl_sync(0xffffffffu, inc, 31);
+            for (int k0 = 0; k0 < L; k0 += 32) {
+                const int k = k0 + lane;
+                int lo = 0, hi = nf - 1;
+#pragma unroll
+                for (int step = 0; step < 5; ++step) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    const int pm = __shfl_sync(0xffffffffu, fpre, mid);
+                    if (lo < hi) {
+                        if (pm <= k) lo = mid; else hi = mid - 1;
+                    }
+                }
+                const int64_t ob = __shfl_sync(0xffffffffu, fb, lo);
+                const int op = __shfl_sync(0xffffffffu, fpre, lo);
+                if (k < L && hs_insert(tab, a.xr_cell[ob + (k - op)])) atomicAdd(&s_cnt[wid], 1);
+            }
+        } else if (a.form == 0) {
             for (int64_t p = a.C.rowptr[E]; p < a.C.rowptr[E + 1]; ++p) {
                 int f = a.C.col[p];
                 for (int64_t t = a.xr_ptr[f] + lane; t < a.xr_ptr[f + 1]; t += 32)
@@ -298,8 +335,10 @@ constexpr int kNumWarps = 8;  // rows (warps) per block of the numeric pass
 template <class T, int FORM>
 __host__ __device__ constexpr size_t num_warp_bytes(int hs)
 {
+    // one-sided form: also the flattened (cell, X~ value) list of the row's
+    // faces, hs entries
     return ((size_t)hs * sizeof(T) + (size_t)hs * 12 + (size_t)(FORM ? (hs > kHS ? hs : kHS) : hs) * 4 +
-            (FORM ? (size_t)kUCap * (4 + sizeof(T)) : 0) + 15) & ~(size_t)15;
+            (FORM ? (size_t)kUCap * (4 + sizeof(T)) : (size_t)hs * (4 + sizeof(T))) + 15) & ~(size_t)15;
 }
 
 template <class T, int FORM>
@@ -316,6 +355,12 @@ k_schur_num(SchurArgs<T> a, const T* __restrict__ xr_val, int hs)
     const int kc = FORM ? (hs > kHS ? hs : kHS) : hs;
     int* ul = key + kc;           // two-sided: faces g of G~_E A
     T* uv = (T*)(ul + kUCap);     // and their values u_g
+    T* flv = acc;                 // one-sided: X~ values of the flattened list [hs]
+    int* flc = ul;                // and their cells [hs]
+    if (FORM == 0) {
+        flv = (T*)(((uintptr_t)(key + kc) + 7) & ~(uintptr_t)7);
+        flc = (int*)(flv + hs);
+    }
     const int64_t nw = (int64_t)gridDim.x * kNumWarps;
     for (int64_t E = (int64_t)blockIdx.x * kNumWarps + wid; E < a.Ne; E += nw) {
         for (int i = lane; i < hs; i += 32) tab[i] = -1;
@@ -349,7 +394,56 @@ k_schur_num(SchurArgs<T> a, const T* __restrict__ xr_val, int hs)
         // columns: E, the row of D, every cell reached by a product term
         if (lane == 0) hsc_insert(tab, hs, (int)E);
         for (int64_t p = a.D.rowptr[E] + lane; p < a.D.rowptr[E + 1]; p += 32) hsc_insert(tab, hs, a.D.col[p]);
-        if (FORM == 0) {
+        // one-sided form, rows with at most 32 faces: lane j holds face j of the
+        // row of C (its value, the start and length of its X~ row, the prefix
+        // of the lengths), and the (cell, value) pairs of all faces are loaded
+        // at once, flattened, instead of face after face
+        const int64_t cb = a.C.rowptr[E];
+        const int nf = (int)(a.C.rowptr[E + 1] - cb);
+        bool flat = FORM == 0 && nf <= 32;
+        T fc = T(0);
+        int64_t fb = 0;
+        int flen = 0, fpre = 0, L = 0;
+        if (flat) {
+            if (lane < nf) {
+                const int f = a.C.col[cb + lane];
+                fc = a.C.val[cb + lane];
+                fb = a.xr_ptr[f];
+                flen = (int)(a.xr_ptr[f + 1] - fb);
+            }
+            int inc = flen;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            fpre = inc - flen;
+            L = __shfl_sync(0xffffffffu, inc, 31);
+            flat = L <= hs;
+        }
+        if (FORM == 0 && flat) {
+            for (int k0 = 0; k0 < L; k0 += 32) {
+                const int k = k0 + lane;
+                int lo = 0, hi = nf - 1;  // face of entry k: last j with fpre_j <= k
+#pragma unroll
+                for (int step = 0; step < 5; ++step) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    const int pm = __shfl_sync(0xffffffffu, fpre, mid);
+                    if (lo < hi) {
+                        if (pm <= k) lo = mid; else hi = mid - 1;
+                    }
+                }
+                const int64_t ob = __shfl_sync(0xffffffffu, fb, lo);
+                const int op = __shfl_sync(0xffffffffu, fpre, lo);
+                if (k < L) {
+                    const int64_t t = ob + (k - op);
+                    const int cell = a.xr_cell[t];
+                    flc[k] = cell;
+                    flv[k] = xr_val[t];
+                    hsc_insert(tab, hs, cell);
+                }
+            }
+        } else if (FORM == 0) {
             for (int64_t p = a.C.rowptr[E]; p < a.C.rowptr[E + 1]; ++p) {
                 const int f = a.C.col[p];
                 for (int64_t t = a.xr_ptr[f] + lane; t < a.xr_ptr[f + 1]; t += 32) hsc_insert(tab, hs, a.xr_cell[t]);
@@ -376,7 +470,20 @@ k_schur_num(SchurArgs<T> a, const T* __restrict__ xr_val, int hs)
         }
         __syncwarp();
         // Gustavson product, faces in ascending order
-        if (FORM == 0) {
+        if (FORM == 0 && flat) {
+            for (int j = 0; j < nf; ++j) {
+                const T c = __shfl_sync(0xffffffffu, fc, j);
+                const int pj = __shfl_sync(0xffffffffu, fpre, j);
+                const int lj = __shfl_sync(0xffffffffu, flen, j);
+                for (int k = pj + lane; k < pj + lj; k += 32) {
+                    const int sl = hsc_slot(tab, hs, flc[k]);
+                    if (sl < 0) continue;
+                    const int q = pos[sl];
+                    acc[q] = fma(c, flv[k], acc[q]);
+                }
+                __syncwarp();
+            }
+        } else if (FORM == 0) {
             for (int64_t p = a.C.rowptr[E]; p < a.C.rowptr[E + 1]; ++p) {
                 const int f = a.C.col[p];
                 const T c = a.C.val[p];
