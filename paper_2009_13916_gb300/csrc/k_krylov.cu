@@ -151,11 +151,11 @@ __device__ __forceinline__ double block_sum(double v)
 
 // part[i * nchunks + chunk] = V_i[chunk] . w[chunk] for i < nv; when with_self,
 // part[nv * nchunks + chunk] = w[chunk] . w[chunk].  Each thread keeps its
-// kPer elements of w in registers and takes four vectors at a time (4 kPer
-// independent loads in flight); a transposed butterfly reduces the four dot
-// products across the warp with 6 FP64 adds (instead of 4 x 5 for separate
-// reductions), and the cross-warp sums of all vectors are formed once at the
-// end.  When gate is non-null and *gate == 0 the kernel does nothing (the
+// kPer elements of w in registers and takes eight vectors at a time (8 kPer
+// independent loads in flight); a transposed butterfly reduces the eight dot
+// products across the warp with 9 FP64 adds (instead of 8 x 5 for separate
+// reductions; the FP64 pipe of this part makes every add count), and the
+// cross-warp sums of all vectors are formed once at the end.  When gate is non-null and *gate == 0 the kernel does nothing (the
 // second Gram-Schmidt pass was found unnecessary on the device).
 constexpr int kPer = kChunk / kKT;
 constexpr int kMaxVec = 128;
@@ -172,10 +172,11 @@ k_multidot(const double* __restrict__ V, int64_t ld, int nv, const double* __res
 #pragma unroll
     for (int k = 0; k < kPer; ++k) wr[k] = base + (int64_t)k * kKT < n ? w[base + (int64_t)k * kKT] : 0.0;
     const int nt = nv + with_self;
-    for (int i0 = 0; i0 < nt; i0 += 4) {
-        double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i0 = 0; i0 < nt; i0 += 8) {
+        double a[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < 8; ++j) {
+            a[j] = 0.0;
             const int i = i0 + j;
             if (i < nv) {
                 const double* vi = V + (int64_t)i * ld + base;
@@ -187,18 +188,23 @@ k_multidot(const double* __restrict__ V, int64_t ld, int nv, const double* __res
                 for (int k = 0; k < kPer; ++k) a[j] = fma(wr[k], wr[k], a[j]);
             }
         }
-        // transposed butterfly: the lower half of the warp keeps vectors 0, 1,
-        // the upper 2, 3; then lanes with bit 3 clear keep the first of the two
+        // transposed butterfly over eight vectors (9 FP64 adds): the lower half
+        // of the warp keeps vectors 0-3, the upper 4-7; then bit 3 of the lane
+        // halves that again, then bit 2; the last two steps sum within quads
         const bool up = lane >= 16;
-        const double b0 = (up ? a[2] : a[0]) + __shfl_xor_sync(0xffffffffu, up ? a[0] : a[2], 16);
-        const double b1 = (up ? a[3] : a[1]) + __shfl_xor_sync(0xffffffffu, up ? a[1] : a[3], 16);
-        const bool odd = (lane & 8) != 0;
-        double c = (odd ? b1 : b0) + __shfl_xor_sync(0xffffffffu, odd ? b0 : b1, 8);
-        c += __shfl_xor_sync(0xffffffffu, c, 4);
-        c += __shfl_xor_sync(0xffffffffu, c, 2);
-        c += __shfl_xor_sync(0xffffffffu, c, 1);
-        const int v = i0 + (up ? 2 : 0) + (odd ? 1 : 0);
-        if ((lane & 7) == 0 && v < nt) wp[v][wid] = c;
+        double b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            b[q] = (up ? a[4 + q] : a[q]) + __shfl_xor_sync(0xffffffffu, up ? a[q] : a[4 + q], 16);
+        const bool h8 = (lane & 8) != 0;
+        const double c0 = (h8 ? b[2] : b[0]) + __shfl_xor_sync(0xffffffffu, h8 ? b[0] : b[2], 8);
+        const double c1 = (h8 ? b[3] : b[1]) + __shfl_xor_sync(0xffffffffu, h8 ? b[1] : b[3], 8);
+        const bool h4 = (lane & 4) != 0;
+        double d = (h4 ? c1 : c0) + __shfl_xor_sync(0xffffffffu, h4 ? c0 : c1, 4);
+        d += __shfl_xor_sync(0xffffffffu, d, 2);
+        d += __shfl_xor_sync(0xffffffffu, d, 1);
+        const int v = i0 + (up ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);
+        if ((lane & 3) == 0 && v < nt) wp[v][wid] = d;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nt; i += kKT) {
