@@ -436,7 +436,7 @@ def variant_adjoint(P, torch, W):
             "converged": bool(fi.converged and bi.converged)}
 
 
-def variant_transient(P, torch, W, sysd, blocks, nsteps=5):
+def variant_transient(P, torch, W, sysd, blocks, nsteps=5, qmode="nbr", thresh=0.05, ordering=0, rebuild=True):
     """Transient sequence with Stage-2-only reuse on the bench workload: implicit-Euler steps
     with the adaptive step rule of Sec. 4 (Eq. delta_t_dyn); step 0 builds the preconditioner
     (Stage 1 + Stage 2), every later step only calls edfa_setup with the new D (Algorithm 2)
@@ -453,7 +453,7 @@ def variant_transient(P, torch, W, sysd, blocks, nsteps=5):
         dt = sysd.dt
         h = None
         st0 = torch.cuda.Event(enable_timing=True)
-        marks, its, setup_ms, solve_ms = [], [], [], []
+        marks, its, setup_ms, solve_ms, dens = [], [], [], [], []
         st0.record()
         for k in range(nsteps):
             dv = dbase.clone()
@@ -463,7 +463,8 @@ def variant_transient(P, torch, W, sysd, blocks, nsteps=5):
             if h is None or not reuse:
                 if h is not None:
                     h.close()
-                h = P.Edfa(A, B, C, (D[0], D[1], dv), sysd.Nf, sysd.Ne, qmode="nbr")
+                h = P.Edfa(A, B, C, (D[0], D[1], dv), sysd.Nf, sysd.Ne, qmode=qmode, thresh=thresh,
+                           ordering=ordering)
                 build_ms = h.stats().ms_qsets + h.stats().ms_local + h.stats().ms_schur + h.stats().ms_ilu_a
                 setup_ms.append(h.stats().ms_stage2)
             else:
@@ -472,6 +473,7 @@ def variant_transient(P, torch, W, sysd, blocks, nsteps=5):
             x, info = h.solve(b, restart=RESTART, rtol=RTOL, maxit=MAXIT)
             solve_ms.append(h.stats().ms_solve)
             its.append(info.iterations)
+            dens.append((h.stats().q_total / sysd.Ne, h.stats().s_nnz / sysd.Ne))
             ev = torch.cuda.Event(enable_timing=True)
             ev.record()
             marks.append(ev)
@@ -481,16 +483,34 @@ def variant_transient(P, torch, W, sysd, blocks, nsteps=5):
         torch.cuda.synchronize()
         h.close()
         step_s = [st0.elapsed_time(marks[0]) / 1e3] + [marks[k - 1].elapsed_time(marks[k]) / 1e3 for k in range(1, nsteps)]
-        return step_s, its, build_ms, setup_ms, solve_ms
+        return step_s, its, build_ms, setup_ms, solve_ms, dens
 
     run()
-    step_s, its, build_ms, setup_ms, solve_ms = run()
-    rb_s, rb_its, _, _, _ = run(reuse=False)
-    return {"steps": nsteps, "first_step_s": step_s[0], "later_step_mean_s": sum(step_s[1:]) / (nsteps - 1),
-            "stage1_ms": build_ms, "stage2_ms_mean": sum(setup_ms[1:]) / (nsteps - 1),
-            "solve_ms_mean": sum(solve_ms) / nsteps, "iterations": its,
-            "total_s": sum(step_s), "total_rebuilding_every_step_s": sum(rb_s),
-            "iterations_rebuilding": rb_its}
+    step_s, its, build_ms, setup_ms, solve_ms, dens = run()
+    out = {"qmode": qmode, "thresh": thresh if qmode == "thresh" else None, "ordering": ordering,
+           "steps": nsteps, "first_step_s": step_s[0], "later_step_mean_s": sum(step_s[1:]) / (nsteps - 1),
+           "stage1_ms": build_ms, "stage2_ms_mean": sum(setup_ms[1:]) / (nsteps - 1),
+           "solve_ms_mean": sum(solve_ms) / nsteps, "iterations": its, "total_s": sum(step_s),
+           "q_per_cell": dens[-1][0], "s_nnz_per_row": dens[-1][1]}
+    if rebuild:
+        rb_s, rb_its, _, _, _, _ = run(reuse=False)
+        out.update(total_rebuilding_every_step_s=sum(rb_s), iterations_rebuilding=rb_its)
+    return out
+
+
+def variant_static_patterns(P, torch, W, ordering, nsteps=5):
+    """Transient sequence (Stage-2 reuse) on a 128x128x16 channelised grid (diagonal K) with
+    the static patterns of Sec. 4 as read from the text (the figures are missing): the base
+    pattern (own faces), pattern A (the A-couplings of the own faces: on this grid the
+    neighbours' faces opposite the shared ones, an extension along the principal axes) and
+    pattern E (every face of the face-neighbours, for fluxes in all directions)."""
+    sysd = W.config3(128, 128, 16)
+    blocks = device_system(sysd)
+    res = {"workload": "128x128x16 layered channelised grid (262,144 cells), diagonal K, 5 implicit-Euler steps"}
+    for label, qm, th in (("base_own", "own", 0.05), ("A_axes", "thresh", 0.0), ("E_all_directions", "nbr", 0.05)):
+        res[label] = variant_transient(P, torch, W, sysd, blocks, nsteps, qmode=qm, thresh=th, ordering=ordering,
+                                       rebuild=False)
+    return res
 
 
 def variant_bicgstab(P, torch, sysd, blocks, b):
@@ -799,6 +819,7 @@ def main():
         extra["c2_64_post_h_filtration"] = variant_filtration(P, torch, c2, c2blocks, c2b)
         extra["c2_64_bicgstab"] = variant_bicgstab(P, torch, c2, c2blocks, c2b)
         extra["c2_64_transient_stage2_reuse"] = variant_transient(P, torch, W, c2, c2blocks)
+        extra["static_patterns_transient_128x128x16"] = variant_static_patterns(P, torch, W, args.ordering)
         del c2blocks, c2b
         extra["adjoint_c5"] = variant_adjoint(P, torch, W)
         extra["batched_c4_256"] = variant_batched(P, torch, W, orderings=sorted({0, args.ordering}))

@@ -102,6 +102,35 @@ def test_crow_and_thresh_sets():
     assert sets_of(qptr, qidx) == own
 
 
+def test_static_pattern_a_reading_is_the_axis_extension():
+    """Static pattern A (Sec. 4, Fig. static_patterns; the figure is missing):
+    read as the A-couplings of the own faces (qmode thresh, tau = 0).  With a
+    diagonal K every elemental matrix couples a face only to the opposite face
+    of its cell, so this adds, for every face-neighbour, the neighbour's face
+    opposite the shared one: the straight extension along the principal axes
+    that the text describes (flux along the principal conductivity axes), six
+    new faces for an interior cell."""
+    sysd = iso((5, 5, 4))
+    qptr, qidx = O.qsets("thresh", sysd.A, sysd.B, sysd.C, 0.0)
+    live = ~sysd.face_dir
+    cf, fc = np.asarray(sysd.cell_faces), np.asarray(sysd.face_cells)
+    ref = []
+    for m in range(sysd.Ne):
+        q = {f for f in cf[m] if live[f]}
+        for k in range(6):  # local faces x-, x+, y-, y+, z-, z+
+            f = cf[m][k]
+            for e2 in fc[f]:
+                if e2 >= 0 and e2 != m and live[f] and live[cf[e2][k]]:
+                    q.add(int(cf[e2][k]))
+        ref.append(sorted(q))
+    assert sets_of(qptr, qidx) == ref
+    centre = 2 + 5 * (2 + 5 * 1)
+    assert len(ref[centre]) == 12
+    # pattern E (all directions) reads as every face of the face-neighbours
+    qptr_e, _ = O.qsets("nbr", sysd.A, sysd.B, sysd.C)
+    assert np.diff(qptr_e)[centre] == 36
+
+
 # ------------------------------------------------------------ local solves
 @pytest.mark.parametrize("maker", [full_tensor, iso])
 def test_all_faces_restriction_is_exact(maker):
