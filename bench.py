@@ -71,6 +71,8 @@ def parse():
                     help="skip the FMA-rate probe (profiling runs: keeps its launches out of the launch list)")
     ap.add_argument("--ordering", type=int, default=2, choices=[0, 1, 2],
                     help="inner ILU(0) ordering of the timed path: 0 natural, 1 multicolour S~, 2 A~ and S~")
+    ap.add_argument("--s-block", type=int, default=4,
+                    help="with an ordering of S~: rows per block of its block multicolour ordering (1: point colouring)")
     return ap.parse_args()
 
 
@@ -177,7 +179,10 @@ def traffic_from_profile(profile: str, key: str, srcname: str):
     if vals.get(f"{srcname} sha256[:16]") != digest:
         return None
     v = vals.get(f"dram_bytes_per_launch {key}")
-    return int(v) if v else None
+    if v:
+        return int(v)
+    r = vals.get(f"dram_over_algorithmic {key}")
+    return ("ratio", float(r)) if r else None
 
 
 # per sweep kind: (name, committed profile, key, source file) by workload
@@ -196,11 +201,11 @@ def device_system(sysd):
     return P.system_to_device(sysd)
 
 
-def step_device(P, blocks, sysd, b, precision, wl, maxit, profile=True, ordering=0):
+def step_device(P, blocks, sysd, b, precision, wl, maxit, profile=True, ordering=0, s_block=1):
     """One step; `profile`: True (every timed kind), False, or a list of kinds."""
     A, B, C, D = blocks
     h = P.Edfa(A, B, C, D, sysd.Nf, sysd.Ne, qmode=wl["qmode"], thresh=wl["thresh"], precision=precision,
-               ordering=ordering)
+               ordering=ordering, s_block=s_block)
     if profile is True:
         h.set_profiling(True)
     elif profile:
@@ -209,7 +214,8 @@ def step_device(P, blocks, sysd, b, precision, wl, maxit, profile=True, ordering
     return h, x, info
 
 
-def run_device(P, torch, sysd, blocks, b, precision, steps, warmup, wl, maxit, profile=True, ordering=0):
+def run_device(P, torch, sysd, blocks, b, precision, steps, warmup, wl, maxit, profile=True, ordering=0,
+               s_block=1):
     """`steps` timed steps (CUDA events on the launching stream) after `warmup`
     untimed ones.  With profiling, the last warm-up step times every kind of
     launch (the per-kernel split of a step) and the timed steps time only the
@@ -219,7 +225,8 @@ def run_device(P, torch, sysd, blocks, b, precision, steps, warmup, wl, maxit, p
     warm_split, dom = None, None
     for w in range(warmup):
         last = w == warmup - 1
-        h, x, info = step_device(P, blocks, sysd, b, precision, wl, maxit, bool(profile) and last, ordering)
+        h, x, info = step_device(P, blocks, sysd, b, precision, wl, maxit, bool(profile) and last, ordering,
+                                 s_block)
         if profile and last:
             st = h.stats()
             tot = list(st.sweep_ms) + list(st.kry_ms)
@@ -239,7 +246,7 @@ def run_device(P, torch, sysd, blocks, b, precision, steps, warmup, wl, maxit, p
     l0 = P.launch_count()
     ev[0].record(stream)
     for k in range(steps):
-        h, x, info = step_device(P, blocks, sysd, b, precision, wl, maxit, profile, ordering)
+        h, x, info = step_device(P, blocks, sysd, b, precision, wl, maxit, profile, ordering, s_block)
         ev[k + 1].record(stream)
         st = h.stats()
         infos.append(info)
@@ -260,7 +267,7 @@ def run_device(P, torch, sysd, blocks, b, precision, steps, warmup, wl, maxit, p
                 kry_n=kry_n, kry_vecs=kry_vecs, launches=launches, x=x, handle=h, warm_split=warm_split)
 
 
-def run_e2e(P, torch, sysd, precision, steps, wl, maxit, ordering=0):
+def run_e2e(P, torch, sysd, precision, steps, wl, maxit, ordering=0, s_block=1):
     """Same metric through the C ABI from pinned HOST buffers: every step copies
     the CSR blocks and b host->device and reads x back."""
     import numpy as np
@@ -278,7 +285,7 @@ def run_e2e(P, torch, sysd, precision, steps, wl, maxit, ordering=0):
         dev = [tuple(t.to("cuda", non_blocking=True) for t in trip) for trip in host]
         db = hb.to("cuda", non_blocking=True)
         h = P.Edfa(*dev, sysd.Nf, sysd.Ne, qmode=wl["qmode"], thresh=wl["thresh"], precision=precision,
-                   ordering=ordering)
+                   ordering=ordering, s_block=s_block)
         x, info = h.solve(db, restart=RESTART, rtol=RTOL, maxit=maxit)
         hx.copy_(x, non_blocking=True)
         return h
@@ -378,16 +385,16 @@ def variant_batched(P, torch, W, nsys=256, orderings=(0,)):
     return out
 
 
-def variant_workload(P, torch, sysd, wl, maxit, ordering=0, blocks=None):
+def variant_workload(P, torch, sysd, wl, maxit, ordering=0, blocks=None, s_block=1):
     """Build + solve time of a workload, FP64 and FP32-mixed (one warm-up
     each, then one timed step)."""
     blocks = P.system_to_device(sysd) if blocks is None else blocks
     b = torch.as_tensor(sysd.b, device="cuda")
-    out = {"ordering": ordering}
+    out = {"ordering": ordering, "s_block": s_block if ordering >= 1 else None}
     for prec, name in ((0, "fp64"), (1, "fp32_mixed")):
         def step():
             h = P.Edfa(*blocks, sysd.Nf, sysd.Ne, qmode=wl["qmode"], thresh=wl["thresh"], precision=prec,
-                       ordering=ordering)
+                       ordering=ordering, s_block=s_block)
             x, info = h.solve(b, restart=RESTART, rtol=RTOL, maxit=maxit)
             return h, info
         h, _ = step()
@@ -530,7 +537,7 @@ def variant_bicgstab(P, torch, sysd, blocks, b):
             "true_rel": info.true_rel, "converged": bool(info.converged), "restarts": info.restarts}
 
 
-def oracle_sample(sysd, wl, iterations, threads=1, cycle_its=RESTART, per_it=None, ordering=0):
+def oracle_sample(sysd, wl, iterations, threads=1, cycle_its=RESTART, per_it=None, ordering=0, s_block=1):
     """The oracle on a bounded sample of the workload: its whole setup (sets,
     local solves, S~, both ILU(0)s) and one FGMRES restart cycle (`cycle_its`
     iterations, x0 = 0), timed on the host; the full solve is extrapolated to
@@ -545,7 +552,7 @@ def oracle_sample(sysd, wl, iterations, threads=1, cycle_its=RESTART, per_it=Non
         t1 = time.perf_counter()
         S = O.schur(0, sysd.A, sysd.C, sysd.D, *q, x)
         aperm = O.colour_order(sysd.A)[1] if ordering == 2 else None
-        sperm = O.colour_order(S)[1] if ordering >= 1 else None
+        sperm = O.colour_order(S, s_block)[1] if ordering >= 1 else None
         Pc = O.Prec(sysd.A, sysd.B, sysd.C, sysd.D, S=S, aperm=aperm, sperm=sperm)
         t2 = time.perf_counter()
         if per_it is None:
@@ -559,7 +566,7 @@ def oracle_sample(sysd, wl, iterations, threads=1, cycle_its=RESTART, per_it=Non
             "per_iteration_s": per_it, "sampled_s": t3 - t0}
 
 
-def oracle_iterations(name, sysd, ordering=0):
+def oracle_iterations(name, sysd, ordering=0, s_block=1):
     """The oracle's FGMRES(50) iteration count at rtol 1e-8 on these inputs (with
     the given ordering of the inner factorisations) when a committed oracle run
     for them exists (tests/golden, matched by the input digest), else None."""
@@ -575,6 +582,8 @@ def oracle_iterations(name, sysd, ordering=0):
     except OSError:
         return None
     key = "iterations" if ordering == 0 else f"iterations_ordering{ordering}"
+    if ordering >= 1 and s_block > 1:
+        key += f"_block{s_block}"
     if vals.get("inputs_sha256") != W.digest(sysd) or key not in vals:
         return None
     return int(vals[key])
@@ -595,14 +604,14 @@ def reference_arm(args, rank, world):
         O.edfa_pipeline(tiny, mode="nbr")
     wl = WORKLOADS[args.workload]
     sysd = make_workload(args.workload, args.n, args.nz)
-    iters = oracle_iterations(args.workload, sysd, args.ordering)
+    iters = oracle_iterations(args.workload, sysd, args.ordering, args.s_block)
     if iters is None:
         iters = O.edfa_pipeline(sysd, mode=wl["qmode"], restart=RESTART, rtol=RTOL, maxit=MAXIT,
-                                ordering=args.ordering)["iters"]
+                                ordering=args.ordering, s_block=args.s_block)["iters"]
     times = []
     t_start = time.perf_counter()
     for k in range(max(1, args.steps)):
-        times.append(oracle_sample(sysd, wl, iters, ordering=args.ordering)["value"])
+        times.append(oracle_sample(sysd, wl, iters, ordering=args.ordering, s_block=args.s_block)["value"])
         if time.perf_counter() - t_start > 150:
             break
     v = statistics.mean(times)
@@ -687,6 +696,8 @@ def kernel_roofline(args, r, sysd, st, peak, peak_src, nnz_l_s, nnz_l_a, fma64, 
         ach = fma / t if t > 0 else None
         prof = SWEEP_PROFILES.get((args.workload, args.ordering, dom))
         traffic = traffic_from_profile(*prof) if prof else None
+        if isinstance(traffic, tuple):  # measured DRAM / algorithmic bytes, per launch of this run
+            traffic = int(traffic[1] * byts / n_launch)
         pk, pk_src = fpk
         return {"bound": "alu", "kernel": names[dom], "achieved": ach, "peak": pk, "unit": "FP64 FMA/s",
                 "frac": ach / pk if ach and pk else None, "traffic": traffic,
@@ -779,7 +790,8 @@ def main():
     barrier()
     clk = ClockSampler(gpu_index)
     clk.start()
-    r64 = run_device(P, torch, sysd, blocks, b, 0, args.steps, args.warmup, wl, args.maxit, ordering=args.ordering)
+    r64 = run_device(P, torch, sysd, blocks, b, 0, args.steps, args.warmup, wl, args.maxit, ordering=args.ordering,
+                     s_block=args.s_block)
     barrier()
     clocks = clk.stop()
     h64 = r64["handle"]
@@ -794,12 +806,13 @@ def main():
     r32 = None
     if not args.no_fp32:
         r32 = run_device(P, torch, sysd, blocks, b, 1, args.steps, max(1, args.warmup // 2), wl, args.maxit,
-                         ordering=args.ordering)
+                         ordering=args.ordering, s_block=args.s_block)
         r32["handle"].close()
         barrier()
     e2e = None
     if not args.no_e2e:
-        e2e_s, h2d, d2h = run_e2e(P, torch, sysd, 0, max(1, min(args.steps, 3)), wl, args.maxit, args.ordering)
+        e2e_s, h2d, d2h = run_e2e(P, torch, sysd, 0, max(1, min(args.steps, 3)), wl, args.maxit, args.ordering,
+                                  args.s_block)
         e2e = {"value": max_over_ranks(e2e_s), "unit": "s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
         barrier()
@@ -808,6 +821,9 @@ def main():
         for o in (0, 1, 2):
             if o != args.ordering:
                 extra[f"ordering_{o}"] = variant_workload(P, torch, sysd, wl, args.maxit, ordering=o, blocks=blocks)
+        if args.ordering >= 1 and args.s_block > 1:
+            extra[f"ordering_{args.ordering}_point_colouring"] = variant_workload(
+                P, torch, sysd, wl, args.maxit, ordering=args.ordering, blocks=blocks, s_block=1)
         c2 = W.config2(64)
         c2blocks = device_system(c2)
         c2b = torch.as_tensor(c2.b, device="cuda")
@@ -853,6 +869,7 @@ def main():
         "config": {"workload": describe(args.workload, args.n, args.nz), "N_e": sysd.Ne, "N_f": sysd.Nf, "unknowns": sysd.Nf + sysd.Ne,
                    "restriction_sets": wl["qmode"], "restart": RESTART, "rtol": RTOL,
                    "ilu0_ordering": ["natural", "multicolour S~", "multicolour A~ and S~"][args.ordering],
+                   "s_block": args.s_block if args.ordering >= 1 else None,
                    "l2": "inputs larger than L2 (CSR blocks > 300 MB), no flush",
                    "parallelism": f"replicas x{world} (independent systems per GPU)"},
         "iterations": info.iterations, "true_rel": true_rel, "converged": bool(info.converged),
@@ -877,12 +894,13 @@ def main():
         out["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ncores = len(os.sched_getaffinity(0))
-        it_orc = oracle_iterations(args.workload, sysd, args.ordering)
+        it_orc = oracle_iterations(args.workload, sysd, args.ordering, args.s_block)
         it_src = "the oracle's" if it_orc is not None else "the GPU path's"
         if it_orc is None:
             it_orc = info.iterations
-        one = oracle_sample(sysd, wl, it_orc, threads=1, ordering=args.ordering)
-        allc = oracle_sample(sysd, wl, it_orc, threads=ncores, per_it=one["per_iteration_s"], ordering=args.ordering)
+        one = oracle_sample(sysd, wl, it_orc, threads=1, ordering=args.ordering, s_block=args.s_block)
+        allc = oracle_sample(sysd, wl, it_orc, threads=ncores, per_it=one["per_iteration_s"], ordering=args.ordering,
+                             s_block=args.s_block)
         out["cpu_baseline"] = {"value": one["value"], "unit": "s", "cores": 1, "kind": "oracle",
                                "sample": f"oracle setup (sets, local solves, S~, ILU(0)s) + one 50-iteration "
                                          f"FGMRES cycle on the same workload, {one['sampled_s']:.1f} s sampled; "

@@ -118,6 +118,13 @@ typedef struct {
                                colours.  With an ordering of S~ its sweeps always run on all SMs (the
                                single-cluster sweeps of sweep_mode 0 and 2 are for deep natural-order
                                factors); an ordered A~ is never chain-decomposed */
+    int32_t s_block;        /* with an ordering of S~: 0 or 1 = the colouring above; 2..16 = block
+                               multicolour ordering: blocks of s_block consecutive rows coloured as
+                               units (SplitMix64 priority of block + 1), row r of block B taking colour
+                               c(B) s_block + r - B s_block, so the rows of one block keep their
+                               natural order.  The ILU(0) then stays closer to the natural one (fewer
+                               FGMRES iterations) at s_block times the colours.  EDFA_ERR_BOUNDS when
+                               the colours exceed 256 */
 } edfa_options;
 
 /* Filtration of the approximate Schur complement (Algorithms 1 and 2). */

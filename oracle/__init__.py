@@ -94,6 +94,7 @@ def lib():
         L.orc_prec_setup_ordered.argtypes = [P(_Prec), P(_CSR), P(_CSR), P(_CSR), P(_CSR), P(_CSR),
                                              P(_CSR), C.c_int, C.c_int, C.c_void_p, C.c_void_p, P(C.c_int32)]
         L.orc_colour_order.argtypes = [P(_CSR), C.c_void_p, C.c_void_p, P(C.c_int32)]
+        L.orc_block_colour_order.argtypes = [P(_CSR), C.c_int32, C.c_void_p, C.c_void_p, P(C.c_int32)]
         L.orc_permute.argtypes = [P(_CSR), C.c_void_p, P(_CSR)]
         L.orc_prec_free.argtypes = [P(_Prec)]
         L.orc_prec_free.restype = None
@@ -101,7 +102,7 @@ def lib():
         L.orc_adjoint_grad.argtypes = [C.c_int32, C.c_int32] + [C.c_void_p] * 9
         for name in ("orc_qsets", "orc_qsets_dynamic", "orc_local_solves", "orc_schur",
                      "orc_ilu0", "orc_fgmres", "orc_prec_setup", "orc_adjoint_grad",
-                     "orc_prec_setup_ordered", "orc_colour_order", "orc_permute"):
+                     "orc_prec_setup_ordered", "orc_colour_order", "orc_block_colour_order", "orc_permute"):
             getattr(L, name).restype = C.c_int
         assert L.orc_prec_sizeof() == C.sizeof(_Prec)
         _lib = L
@@ -384,17 +385,19 @@ class Prec:
         return np.ctypeslib.as_array(C.cast(self.p.lus, C.POINTER(C.c_double)), shape=(self.S.nnz,)).copy()
 
 
-def colour_order(M):
+def colour_order(M, block=1):
     """Multicolour ordering of the graph of M + M^T (the oracle's colouring):
     returns (colour per row, perm with rows sorted by (colour, index), number
-    of colours)."""
+    of colours).  block > 1: the block multicolour ordering, blocks of `block`
+    consecutive rows coloured as units, row r of block B taking the colour
+    c(B) * block + (r - B * block)."""
     M = Mat.of(M)
     colour = np.empty(M.nrows, np.int32)
     perm = np.empty(M.nrows, np.int32)
     nc = C.c_int32(0)
-    rc = lib().orc_colour_order(C.byref(M.c), _ptr(colour), _ptr(perm), C.byref(nc))
+    rc = lib().orc_block_colour_order(C.byref(M.c), int(block), _ptr(colour), _ptr(perm), C.byref(nc))
     if rc:
-        raise RuntimeError("orc_colour_order failed")
+        raise RuntimeError("orc_block_colour_order failed")
     return colour, perm, int(nc.value)
 
 
@@ -470,10 +473,11 @@ def qsets_for(sysd, mode=None, thresh=None, dyn=None):
 
 
 def edfa_pipeline(sysd, mode=None, form=0, variant=0, restart=50, rtol=1e-8, maxit=2000, b=None,
-                  dyn=None, solve=True, filt="none", tau=0.0, ordering=0):
+                  dyn=None, solve=True, filt="none", tau=0.0, ordering=0, s_block=1):
     """The whole hot path on the CPU: Q sets, local solves, S~ (optionally
     filtered), ILU(0)s (ordering 0: natural; 1: multicolour ordering of S~;
-    2: multicolour orderings of A and S~), FGMRES."""
+    2: multicolour orderings of A and S~; s_block > 1: the block multicolour
+    ordering of S~ with blocks of s_block consecutive rows), FGMRES."""
     qptr, qidx = qsets_for(sysd, mode, dyn=dyn)
     xval, gval = local_solves(sysd.A, sysd.B, sysd.C, qptr, qidx, True, form == 1)
     if filt == "none":
@@ -481,7 +485,7 @@ def edfa_pipeline(sysd, mode=None, form=0, variant=0, restart=50, rtol=1e-8, max
     else:
         S, _ = schur_filtered(form, sysd.A, sysd.C, sysd.D, qptr, qidx, xval, gval, filt, tau)
     aperm = colour_order(sysd.A)[1] if ordering == 2 else None
-    sperm = colour_order(S)[1] if ordering >= 1 else None
+    sperm = colour_order(S, s_block)[1] if ordering >= 1 else None
     P = Prec(sysd.A, sysd.B, sysd.C, sysd.D, S=S, variant=variant, aperm=aperm, sperm=sperm)
     out = dict(qptr=qptr, qidx=qidx, xval=xval, gval=gval, S=S, prec=P, aperm=aperm, sperm=sperm)
     if solve:

@@ -1114,46 +1114,75 @@ static int cmp_pri_desc(const void* a, const void* b)
     return x->pri < y->pri ? 1 : (x->pri > y->pri ? -1 : 0);
 }
 
-ORC_EXPORT int orc_colour_order(const orc_csr* M, int32_t* colour, int32_t* perm, int32_t* ncolours)
+/* Block multicolour ordering (an opt-in variant of the above): the rows are
+ * grouped into blocks of b consecutive rows (the last block may be shorter),
+ * block B holding rows B b .. B b + b - 1.  Graph: vertices = blocks, an edge
+ * between blocks B != B' wherever M or M^T couples a row of B with a row of
+ * B'.  The blocks are coloured like the rows above (SplitMix64 priority of
+ * B + 1, every block takes the smallest colour not used by its neighbours of
+ * higher priority).  Inside a block the rows keep their order: row r of block
+ * B gets the colour c(B) b + (r - B b), so the rows of one colour are
+ * independent (blocks of one block colour are not coupled, and the rows of
+ * one block have distinct positions), and rows sorted by (colour, row index)
+ * list, for every block colour, position after position.  The ILU(0) of this
+ * ordering equals that of the ordering by (block colour, block, position):
+ * the two orders agree on every pair of coupled rows.  b = 1 is the ordering
+ * above. */
+ORC_EXPORT int orc_block_colour_order(const orc_csr* M, int32_t b, int32_t* colour, int32_t* perm, int32_t* ncolours)
 {
     const int32_t n = M->nrows;
+    if (b < 1) return -1;
+    const int32_t nb = n > 0 ? (int32_t)(((int64_t)n + b - 1) / b) : 0;
     orc_ocsr T = {0};
     if (csr_transpose(M, &T)) { orc_free_csr(&T); return -1; }
-    orc_pv* order = (orc_pv*)malloc((size_t)(n ? n : 1) * sizeof(orc_pv));
-    int32_t* stamp = (int32_t*)malloc((size_t)(n + 2) * sizeof(int32_t));
-    if (!order || !stamp) { free(order); free(stamp); orc_free_csr(&T); return -1; }
-    for (int32_t v = 0; v < n; ++v) { order[v].pri = orc_priority(v); order[v].v = v; colour[v] = -1; }
-    qsort(order, (size_t)n, sizeof(orc_pv), cmp_pri_desc);
-    for (int32_t c = 0; c < n + 2; ++c) stamp[c] = -1;
-    int32_t ncol = 0;
-    for (int32_t k = 0; k < n; ++k) {
-        const int32_t v = order[k].v;
-        /* colours of the neighbours coloured so far (those of higher priority) */
-        for (int64_t p = M->rowptr[v]; p < M->rowptr[v + 1]; ++p) {
-            int32_t u = M->col[p];
-            if (u != v && colour[u] >= 0) stamp[colour[u]] = v;
-        }
-        for (int64_t p = T.rowptr[v]; p < T.rowptr[v + 1]; ++p) {
-            int32_t u = T.col[p];
-            if (u != v && colour[u] >= 0) stamp[colour[u]] = v;
+    orc_pv* order = (orc_pv*)malloc((size_t)(nb ? nb : 1) * sizeof(orc_pv));
+    int32_t* bcol = (int32_t*)malloc((size_t)(nb ? nb : 1) * sizeof(int32_t));
+    int32_t* stamp = (int32_t*)malloc((size_t)(nb + 2) * sizeof(int32_t));
+    if (!order || !bcol || !stamp) { free(order); free(bcol); free(stamp); orc_free_csr(&T); return -1; }
+    for (int32_t B = 0; B < nb; ++B) { order[B].pri = orc_priority(B); order[B].v = B; bcol[B] = -1; }
+    qsort(order, (size_t)nb, sizeof(orc_pv), cmp_pri_desc);
+    for (int32_t c = 0; c < nb + 2; ++c) stamp[c] = -1;
+    for (int32_t k = 0; k < nb; ++k) {
+        const int32_t B = order[k].v;
+        const int32_t r1 = (int32_t)((int64_t)B * b + b < n ? (int64_t)B * b + b : n);
+        /* colours of the neighbouring blocks coloured so far (those of higher priority) */
+        for (int32_t v = B * b; v < r1; ++v) {
+            for (int64_t p = M->rowptr[v]; p < M->rowptr[v + 1]; ++p) {
+                const int32_t U = M->col[p] / b;
+                if (U != B && bcol[U] >= 0) stamp[bcol[U]] = B;
+            }
+            for (int64_t p = T.rowptr[v]; p < T.rowptr[v + 1]; ++p) {
+                const int32_t U = T.col[p] / b;
+                if (U != B && bcol[U] >= 0) stamp[bcol[U]] = B;
+            }
         }
         int32_t c = 0;
-        while (stamp[c] == v) ++c;
-        colour[v] = c;
-        if (c + 1 > ncol) ncol = c + 1;
+        while (stamp[c] == B) ++c;
+        bcol[B] = c;
+    }
+    int32_t ncol = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        colour[v] = bcol[v / b] * b + v % b;
+        if (colour[v] + 1 > ncol) ncol = colour[v] + 1;
     }
     /* rows sorted by (colour, index): counting sort, stable in the index */
     int64_t* start = (int64_t*)calloc((size_t)ncol + 1, sizeof(int64_t));
-    if (!start) { free(order); free(stamp); orc_free_csr(&T); return -1; }
+    if (!start) { free(order); free(bcol); free(stamp); orc_free_csr(&T); return -1; }
     for (int32_t v = 0; v < n; ++v) start[colour[v] + 1]++;
     for (int32_t c = 0; c < ncol; ++c) start[c + 1] += start[c];
     for (int32_t v = 0; v < n; ++v) perm[start[colour[v]]++] = v;
     *ncolours = ncol;
     free(start);
     free(order);
+    free(bcol);
     free(stamp);
     orc_free_csr(&T);
     return 0;
+}
+
+ORC_EXPORT int orc_colour_order(const orc_csr* M, int32_t* colour, int32_t* perm, int32_t* ncolours)
+{
+    return orc_block_colour_order(M, 1, colour, perm, ncolours);
 }
 
 /* P M P^T: row k is row perm[k] of M with every column j renamed to its

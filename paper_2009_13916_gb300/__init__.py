@@ -45,7 +45,8 @@ class Options(C.Structure):
                 ("qidx", C.c_void_p), ("schur_form", C.c_int32), ("variant", C.c_int32),
                 ("precision", C.c_int32), ("warps_per_block", C.c_int32),
                 ("sweep_warps_per_sm", C.c_int32), ("sweep_mode", C.c_int32),
-                ("filtration", C.c_int32), ("tau_filt", C.c_double), ("ordering", C.c_int32)]
+                ("filtration", C.c_int32), ("tau_filt", C.c_double), ("ordering", C.c_int32),
+                ("s_block", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -263,7 +264,7 @@ class Edfa:
 
     def __init__(self, A, B, C_, D, Nf: int, Ne: int, qmode="own", thresh=0.05, n_add=1, n_ent=4,
                  it_max=100, qsets=None, schur_form=0, variant=0, precision=0, warps_per_block=0,
-                 sweep_warps_per_sm=0, sweep_mode=0, filtration="none", tau_filt=0.0, ordering=0, stream=None):
+                 sweep_warps_per_sm=0, sweep_mode=0, filtration="none", tau_filt=0.0, ordering=0, s_block=0, stream=None):
         self._keep = [A, B, C_, D]
         self.Nf, self.Ne = int(Nf), int(Ne)
         opt = Options()
@@ -284,6 +285,7 @@ class Edfa:
         opt.filtration = FILTERS[filtration] if isinstance(filtration, str) else int(filtration)
         opt.tau_filt = float(tau_filt)
         opt.ordering = int(ordering)
+        opt.s_block = int(s_block)
         self.opt = opt
         self._D = D
         self.h = edfa_build(csr(*A, self.Nf), csr(*B, self.Ne), csr(*C_, self.Nf), csr(*D, self.Ne), opt,

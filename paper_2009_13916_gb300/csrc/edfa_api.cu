@@ -183,7 +183,7 @@ int edfa_build(edfa_handle* out, const edfa_csr* A, const edfa_csr* B, const edf
     if (o.filtration < EDFA_FILT_NONE || o.filtration > EDFA_FILT_POST_S || !(o.tau_filt >= 0.0) ||
         !std::isfinite(o.tau_filt))
         return EDFA_ERR_INVALID;
-    if (o.ordering < 0 || o.ordering > 2) return EDFA_ERR_INVALID;
+    if (o.ordering < 0 || o.ordering > 2 || o.s_block < 0 || o.s_block > 16) return EDFA_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
 
     edfa_handle_s* h = new (std::nothrow) edfa_handle_s();

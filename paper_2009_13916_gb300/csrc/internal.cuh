@@ -198,6 +198,15 @@ struct Ordering {
     // 32, 16, 8 and 4 rows (1, 2, 4, 8 lanes per row): [dir][lanes][ncolours + 1],
     // dir 0 forward (colours ascending), 1 backward (descending)
     int64_t* tstart_dev = nullptr;
+    // block multicolour ordering (block > 1): row r of block B has colour
+    // c(B) block + r - B block, so block colour c spans colours c block ..
+    // c block + block - 1; bstart_dev = first task (32 / block blocks) of
+    // every block colour in processing order, [dir][nbcolours + 1] (dir 0
+    // forward, 1 backward), for the sweeps that take whole blocks per warp
+    // (block 4 or 8)
+    int32_t block = 1;
+    int32_t nbcolours = 0;
+    int64_t* bstart_dev = nullptr;
 };
 
 // Up to six device buffers to fill with the all-ones pattern, in 32-bit words
@@ -382,7 +391,7 @@ int s_cluster_solve(edfa_handle_s* h, const double* rp, const int64_t* mptr, con
 int matvec(edfa_handle_s* h, const double* x, double* y, cudaStream_t s);
 // multicolour orderings (k_order.cu)
 int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr, const int32_t* col, int64_t nnz,
-                 cudaStream_t s);
+                 cudaStream_t s, int32_t block = 1);
 int order_matrix(edfa_handle_s* h, OrderedCsr& m, int32_t nrows, const int64_t* rowptr, const int32_t* col,
                  int64_t nnz, const int32_t* rperm, const int32_t* cmap, cudaStream_t s);
 int order_values(edfa_handle_s* h, OrderedCsr& m, const double* src64, const float* src32, cudaStream_t s);

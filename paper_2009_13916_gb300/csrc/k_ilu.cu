@@ -1271,6 +1271,155 @@ k_mc_sweep_df(int ncol, const int64_t* __restrict__ tstart, const int32_t* __res
     }
 }
 
+// Sweeps of a block multicolour ordering (blocks of NB rows, 32 / NB blocks per
+// warp, one lane per row).  Block j of block colour c holds the rows
+// i_k = cstart[c NB + k] + j at positions k = 0 .. NB - 1 (some may be absent
+// in the one short block).  Blocks of one block colour are not coupled, so a
+// row's entries split into external ones (other block colours: earlier in the
+// sweep, polled like the dataflow sweep's) and internal ones (the rows of its
+// own block, whose columns lie in the colour range of its block colour).  Every
+// lane walks its row, sums the external part and the coupling term and keeps
+// the internal coefficients in shared memory by position; then the warp solves
+// its blocks' small triangular systems in registers, position after position
+// (ascending forward, descending backward): the rows of that position are
+// final, are broadcast within their block, and the later rows add their term.
+// The internal chains cost shuffles, not memory round trips, and every warp-wide
+// FP64 instruction of that phase serves all the warp's blocks.  Tasks = groups
+// of 32 / NB blocks, dealt to the warps in processing order (block colours
+// ascending forward, descending backward); deadlock free like the dataflow
+// sweep.
+template <class T, class TB, class TO, int FWD, int NB>
+__global__ void __launch_bounds__(kMcAllThreads, 2)
+k_mc_sweep_blk(int ncol, int nbc, const int64_t* __restrict__ bstart, const int32_t* __restrict__ cstart,
+               const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const T* __restrict__ lu,
+               const int64_t* __restrict__ diag, const T* __restrict__ dinv, const TB* __restrict__ base,
+               const int32_t* __restrict__ bperm, const int64_t* __restrict__ mptr, const int32_t* __restrict__ mcol,
+               const T* __restrict__ mval, const TO* __restrict__ mv, TO* out, const int32_t* __restrict__ sperm,
+               double* scat, DevErr* err)
+{
+    constexpr int NBW = 32 / NB;  // blocks per warp
+    constexpr int U = 4;
+    __shared__ T wsh[kMcAllThreads / 32][32][NB + 1];  // [warp][lane = row][column position]
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int q = lane / NB, kown = lane % NB;
+    const int64_t warp = ((int64_t)blockIdx.x * kMcAllThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kMcAllThreads) >> 5;
+    const int64_t ntasks = bstart[nbc];
+    T* W = wsh[wl][lane];
+    for (int64_t t = warp; t < ntasks; t += nwarps) {
+        int lo = 0, hi = nbc - 1;  // block colour position: last l with bstart[l] <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bstart[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const int cb = FWD ? lo : nbc - 1 - lo;
+        const int64_t j = (t - bstart[lo]) * NBW + q;  // this lane's block within its block colour
+        const int c0 = cb * NB, c1 = c0 + NB < ncol ? c0 + NB : ncol;
+        const int64_t in_lo = cstart[c0], in_hi = cstart[c1];  // the block colour's rows
+#pragma unroll
+        for (int k = 0; k < NB; ++k) W[k] = T(0);
+        const int cp = c0 + kown;
+        int64_t i = -1;
+        bool live = false;
+        if (cp < c1) {
+            i = (int64_t)cstart[cp] + j;
+            live = i < cstart[cp + 1];
+        }
+        T acc = T(0), bi = T(0), di = T(1);
+        if (live) {
+            const int64_t rlo = FWD ? rowptr[i] : diag[i] + 1;
+            const int64_t rhi = FWD ? diag[i] : rowptr[i + 1];
+            bi = (T)to_d(base[bperm ? bperm[i] : i]);
+            if (!FWD) di = dinv[i];
+            if (mptr) {
+                const int64_t mb = mptr[i], me = mptr[i + 1];
+                for (int64_t p0 = mb; p0 < me; p0 += U) {
+                    int cc[U];
+                    T w[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int64_t p = p0 + u;
+                        cc[u] = p < me ? mcol[p] : -1;
+                        w[u] = p < me ? mval[p] : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (cc[u] >= 0) acc = fma(w[u], (T)mv[cc[u]], acc);
+                }
+            }
+            for (int64_t p0 = rlo; p0 < rhi; p0 += U) {
+                int cc[U];
+                T w[U], x[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t p = p0 + u;
+                    cc[u] = p < rhi ? col[p] : -1;
+                    w[u] = p < rhi ? lu[p] : T(0);
+                }
+                // internal entries: coefficient by position (the position of
+                // column cc is the k with cstart[c0 + k] + j == cc)
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (cc[u] >= in_lo && cc[u] < in_hi) {
+                        bool found = false;
+                        for (int k = 0; k < NB && c0 + k < c1; ++k)
+                            if ((int64_t)cstart[c0 + k] + j == cc[u]) { W[k] = w[u]; found = true; break; }
+                        if (!found) raise_err(err, EDFA_ERR_BOUNDS, i);  // not a block colouring
+                        cc[u] = -1;
+                    }
+                unsigned pending = 0;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    x[u] = T(0);
+                    if (cc[u] >= 0 && !poll_ready(out + cc[u], x[u])) pending |= 1u << u;
+                }
+                unsigned it = 0;
+                while (pending && it < (kSpinLimit << 2)) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (((pending >> u) & 1u) && poll_ready(out + cc[u], x[u])) pending &= ~(1u << u);
+                    ++it;
+                    if ((it & 255u) == 0u && err_set(err)) break;
+                }
+                if (pending) {
+                    raise_err(err, EDFA_ERR_TIMEOUT, i);
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if ((pending >> u) & 1u) x[u] = T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (cc[u] >= 0) acc = fma(w[u], x[u], acc);
+            }
+        }
+        // the blocks' triangular systems, position after position (backward:
+        // in the scaled form x = d bi - d acc, d = 1/U_ii, with the internal
+        // coefficients scaled by d once, so a position costs one add and one
+        // FMA on the FP64 pipe, forward and backward)
+        if (!FWD) {
+            bi *= di;
+            acc *= di;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) W[k] *= di;
+        }
+        T xv = T(0);
+#pragma unroll
+        for (int s2 = 0; s2 < NB; ++s2) {
+            const int k = FWD ? s2 : NB - 1 - s2;
+            const T r = bi - acc;
+            const int src = q * NB + k;
+            const T xk = __shfl_sync(0xffffffffu, r, src);
+            const int kl = __shfl_sync(0xffffffffu, live ? 1 : 0, src);
+            if (kown == k) xv = r;
+            if (kl) acc = fma(W[k], xk, acc);
+        }
+        if (live) {
+            if (sperm) scat[sperm[i]] = (double)xv;
+            st_relaxed(out + i, (TO)xv);
+        }
+    }
+}
+
 template <class T, class TB, class TO, int FWD, int LPR>
 static void mc_launch(edfa_handle_s* h, const Factor& f, const Ordering& o, const T* lu, const T* dinv,
                       const TB* base, const int32_t* bperm, const int64_t* mptr, const int32_t* mcol, const T* mval,
@@ -1325,6 +1474,35 @@ static void mc_launch(edfa_handle_s* h, const Factor& f, const Ordering& o, cons
     }
 }
 
+// one cooperative launch of the block sweep; false when that is not possible
+template <class T, class TB, class TO, int FWD, int NB>
+static bool blk_launch(edfa_handle_s* h, const Factor& f, const Ordering& o, const T* lu, const T* dinv,
+                       const TB* base, const int32_t* bperm, const int64_t* mptr, const int32_t* mcol, const T* mval,
+                       const TO* mv, TO* out, const int32_t* sperm, double* scat, bool prefilled, cudaStream_t s)
+{
+    auto fb = k_mc_sweep_blk<T, TB, TO, FWD, NB>;
+    static thread_local int per_dev = -1, per_sm = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != per_dev) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fb, kMcAllThreads, 0);
+        per_dev = dev;
+    }
+    if (per_sm < 1) return false;
+    const int64_t* bs = o.bstart_dev + (int64_t)(FWD ? 0 : 1) * (o.nbcolours + 1);
+    if (!prefilled) cudaMemsetAsync(out, 0xFF, (size_t)f.n * sizeof(TO), s);
+    int ncol = o.ncolours, nbc = o.nbcolours;
+    void* args[] = {(void*)&ncol, (void*)&nbc, (void*)&bs, (void*)&o.cstart_dev, (void*)&f.rowptr, (void*)&f.col,
+                    (void*)&lu, (void*)&f.diag, (void*)&dinv, (void*)&base, (void*)&bperm, (void*)&mptr,
+                    (void*)&mcol, (void*)&mval, (void*)&mv, (void*)&out, (void*)&sperm, (void*)&scat, (void*)&h->err};
+    edfa::count_launch();
+    if (cudaLaunchCooperativeKernel((const void*)fb, dim3((unsigned)(h->nsm * per_sm)), dim3(kMcAllThreads), args, 0,
+                                    s) == cudaSuccess)
+        return true;
+    cudaGetLastError();
+    return false;
+}
+
 // lanes per row from the average length of the rows' halves plus the coupling
 template <class T, class TB, class TO, int FWD>
 static int mc_sweep(edfa_handle_s* h, const Factor& f, const Ordering& o, const TB* base, const int32_t* bperm,
@@ -1338,6 +1516,18 @@ static int mc_sweep(edfa_handle_s* h, const Factor& f, const Ordering& o, const 
     else { lu = (const T*)f.lu32; dinv = (const T*)f.dinv32; }
     const double avg = ((double)(f.nnz - f.n) / 2.0 + (mptr ? (double)mnnz : 0.0)) / (double)f.n;
     cudaEvent_t* pe = prof_begin(h, (&f == &h->fs ? 2 : 0) + (FWD ? 0 : 1), s);
+    if (o.bstart_dev && h->coop_ok) {
+        // block multicolour ordering: one block per warp
+        bool ok = false;
+        if (o.block == 4) ok = blk_launch<T, TB, TO, FWD, 4>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out,
+                                                             sperm, scat, prefilled, s);
+        else if (o.block == 8) ok = blk_launch<T, TB, TO, FWD, 8>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv,
+                                                                  out, sperm, scat, prefilled, s);
+        if (ok) {
+            if (pe) cudaEventRecord(pe[1], s);
+            return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;
+        }
+    }
     if (avg <= 4.0)
         mc_launch<T, TB, TO, FWD, 1>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm, scat,
                                        prefilled, s);

@@ -63,40 +63,66 @@ __device__ __forceinline__ unsigned long long grp_or(unsigned long long x, int G
     return x;
 }
 
-// some neighbour u of v (in M and M^T) has higher priority and no colour yet
-__device__ __forceinline__ bool jp_blocked(int32_t v, unsigned long long pv, const int64_t* rp, const int32_t* cl,
-                                           const unsigned long long* prio, const int* colour, int gl, int G)
+// The vertices of the colouring are blocks of b consecutive rows (b = 1: the
+// rows themselves); the entries of block B's rows are the contiguous range
+// rp[B b] .. rp[min(B b + b, n)) of the CSR arrays, and entry u belongs to
+// block u / b.
+
+// some neighbouring block of B (in M and M^T) has higher priority and no colour yet
+__device__ __forceinline__ bool jp_blocked(int32_t B, unsigned long long pv, const int64_t* rp, const int32_t* cl,
+                                           const unsigned long long* prio, const int* colour, int gl, int G, int b,
+                                           int32_t n)
 {
-    for (int64_t p = rp[v] + gl; p < rp[v + 1]; p += G) {
-        const int32_t u = cl[p];
-        if (u != v && __ldcg(colour + u) < 0 && prio[u] > pv) return true;
+    const int64_t r0 = (int64_t)B * b, r1 = r0 + b < n ? r0 + b : n;
+    for (int64_t p = rp[r0] + gl; p < rp[r1]; p += G) {
+        const int32_t U = cl[p] / b;
+        if (U != B && __ldcg(colour + U) < 0 && prio[U] > pv) return true;
     }
     return false;
 }
 
-// colours below 64 of the higher-priority neighbours, as a bit set
-__device__ __forceinline__ unsigned long long jp_used(int32_t v, unsigned long long pv, const int64_t* rp,
+// colours below 64 of the higher-priority neighbouring blocks, as a bit set
+__device__ __forceinline__ unsigned long long jp_used(int32_t B, unsigned long long pv, const int64_t* rp,
                                                       const int32_t* cl, const unsigned long long* prio,
-                                                      const int* colour, int gl, int G)
+                                                      const int* colour, int gl, int G, int b, int32_t n)
 {
     unsigned long long used = 0ull;
-    for (int64_t p = rp[v] + gl; p < rp[v + 1]; p += G) {
-        const int32_t u = cl[p];
-        if (u == v) continue;
-        const int c = __ldcg(colour + u);
-        if (c >= 0 && c < 64 && prio[u] > pv) used |= 1ull << c;
+    const int64_t r0 = (int64_t)B * b, r1 = r0 + b < n ? r0 + b : n;
+    for (int64_t p = rp[r0] + gl; p < rp[r1]; p += G) {
+        const int32_t U = cl[p] / b;
+        if (U == B) continue;
+        const int c = __ldcg(colour + U);
+        if (c >= 0 && c < 64 && prio[U] > pv) used |= 1ull << c;
     }
     return used;
 }
 
-__device__ __forceinline__ bool jp_uses(int32_t v, unsigned long long pv, const int64_t* rp, const int32_t* cl,
-                                        const unsigned long long* prio, const int* colour, int c, int gl, int G)
+__device__ __forceinline__ bool jp_uses(int32_t B, unsigned long long pv, const int64_t* rp, const int32_t* cl,
+                                        const unsigned long long* prio, const int* colour, int c, int gl, int G, int b,
+                                        int32_t n)
 {
-    for (int64_t p = rp[v] + gl; p < rp[v + 1]; p += G) {
-        const int32_t u = cl[p];
-        if (u != v && __ldcg(colour + u) == c && prio[u] > pv) return true;
+    const int64_t r0 = (int64_t)B * b, r1 = r0 + b < n ? r0 + b : n;
+    for (int64_t p = rp[r0] + gl; p < rp[r1]; p += G) {
+        const int32_t U = cl[p] / b;
+        if (U != B && __ldcg(colour + U) == c && prio[U] > pv) return true;
     }
     return false;
+}
+
+// row r of block B: colour c(B) b + r - B b
+__global__ void k_block_row_colours(int32_t n, int b, const int* bcolour, int* colour, int* maxcol)
+{
+    int m = -1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = bcolour[i / b] * b + (int)(i % b);
+        colour[i] = c;
+        m = c > m ? c : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const int y = __shfl_xor_sync(0xffffffffu, m, o);
+        m = y > m ? y : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(maxcol, m);
 }
 
 __global__ void k_jp_iota(int32_t n, int32_t* wl)
@@ -119,7 +145,7 @@ __global__ void k_jp_iota(int32_t n, int32_t* wl)
 __global__ void k_jp_round(const int64_t* __restrict__ rp, const int32_t* __restrict__ cl,
                            const int64_t* __restrict__ tp, const int32_t* __restrict__ tc,
                            const unsigned long long* __restrict__ prio, int* colour, const int32_t* __restrict__ wl_in,
-                           int32_t* wl_out, unsigned* wcnt, int r, int gwide, int* maxcol)
+                           int32_t* wl_out, unsigned* wcnt, int r, int gwide, int* maxcol, int b, int32_t n)
 {
     const unsigned m = wcnt[r % 3];
     unsigned* out_cnt = wcnt + (r + 1) % 3;
@@ -131,17 +157,17 @@ __global__ void k_jp_round(const int64_t* __restrict__ rp, const int32_t* __rest
     const int lane = threadIdx.x & 31;
     const int gi = lane / G, gl = lane % G;
     const unsigned gm = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gi * G));
-    for (int64_t b = warp * VPW; b < m; b += nwarps * VPW) {
-        const int64_t i = b + gi;
+    for (int64_t w0 = warp * VPW; w0 < m; w0 += nwarps * VPW) {
+        const int64_t i = w0 + gi;
         const bool live = i < m;
         const int32_t v = live ? wl_in[i] : 0;
         const unsigned long long pv = live ? prio[v] : 0ull;
-        bool blk = live && (jp_blocked(v, pv, rp, cl, prio, colour, gl, G) ||
-                            jp_blocked(v, pv, tp, tc, prio, colour, gl, G));
+        bool blk = live && (jp_blocked(v, pv, rp, cl, prio, colour, gl, G, b, n) ||
+                            jp_blocked(v, pv, tp, tc, prio, colour, gl, G, b, n));
         blk = grp_any(blk, gm);
         const bool go = live && !blk;
         unsigned long long used = 0ull;
-        if (go) used = jp_used(v, pv, rp, cl, prio, colour, gl, G) | jp_used(v, pv, tp, tc, prio, colour, gl, G);
+        if (go) used = jp_used(v, pv, rp, cl, prio, colour, gl, G, b, n) | jp_used(v, pv, tp, tc, prio, colour, gl, G, b, n);
         used = grp_or(used, G);
         int c = 0;
         if (go) {
@@ -152,8 +178,8 @@ __global__ void k_jp_round(const int64_t* __restrict__ rp, const int32_t* __rest
         // below 64 (every lane of the warp takes part in the group votes)
         bool more = go && c >= 64;
         while (__any_sync(0xffffffffu, more)) {
-            bool hit = more && (jp_uses(v, pv, rp, cl, prio, colour, c, gl, G) ||
-                                jp_uses(v, pv, tp, tc, prio, colour, c, gl, G));
+            bool hit = more && (jp_uses(v, pv, rp, cl, prio, colour, c, gl, G, b, n) ||
+                                jp_uses(v, pv, tp, tc, prio, colour, c, gl, G, b, n));
             hit = grp_any(hit, gm);
             if (more && hit) ++c;
             else more = false;
@@ -315,8 +341,9 @@ static unsigned grid_for(edfa_handle_s* h, int64_t n, int threads = 256)
 
 // ------------------------------------------------------------ host side
 int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr, const int32_t* col, int64_t nnz,
-                 cudaStream_t s)
+                 cudaStream_t s, int32_t block)
 {
+    const int b = block > 1 ? block : 1;
     o.on = 0;
     o.n = n;
     o.ncolours = 0;
@@ -334,6 +361,7 @@ int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr
     int64_t *tp = nullptr, *cur = nullptr, *cnt = nullptr;
     int32_t* tc = nullptr;
     int* colour = nullptr;
+    int* bcolour = nullptr;  // colours of the blocks (b > 1; the row colours follow from them)
     unsigned long long* misc = nullptr;  // [0] vertices left uncoloured by a round, [1] max colour (int)
     unsigned long long* prio = nullptr;
     int32_t* wl = nullptr;  // [2 n] worklists of uncoloured vertices
@@ -342,16 +370,19 @@ int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr
         cudaFreeAsync(tp, s); cudaFreeAsync(cur, s); cudaFreeAsync(tc, s); cudaFreeAsync(colour, s);
         cudaFreeAsync(misc, s); cudaFreeAsync(cnt, s); cudaFreeAsync(prio, s); cudaFreeAsync(wl, s);
         cudaFreeAsync(wcnt, s);
+        if (bcolour) cudaFreeAsync(bcolour, s);
         return code;
     };
+    const int32_t nb = (int32_t)(((int64_t)n + b - 1) / b);  // vertices of the colouring
     if (cudaMallocAsync((void**)&tp, ((size_t)n + 1) * sizeof(int64_t), s) != cudaSuccess ||
         cudaMallocAsync((void**)&cur, ((size_t)n + 1) * sizeof(int64_t), s) != cudaSuccess ||
         cudaMallocAsync((void**)&tc, (size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t), s) != cudaSuccess ||
         cudaMallocAsync((void**)&colour, (size_t)n * sizeof(int), s) != cudaSuccess ||
         cudaMallocAsync((void**)&misc, 2 * sizeof(unsigned long long), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&prio, (size_t)n * sizeof(unsigned long long), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&wl, (size_t)2 * n * sizeof(int32_t), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&wcnt, 3 * sizeof(unsigned), s) != cudaSuccess) {
+        cudaMallocAsync((void**)&prio, (size_t)nb * sizeof(unsigned long long), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&wl, (size_t)2 * nb * sizeof(int32_t), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&wcnt, 3 * sizeof(unsigned), s) != cudaSuccess ||
+        (b > 1 && cudaMallocAsync((void**)&bcolour, (size_t)nb * sizeof(int), s) != cudaSuccess)) {
         cudaGetLastError();
         return done(EDFA_ERR_OOM);
     }
@@ -361,33 +392,39 @@ int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr
     if ((rc = scan_i64(h, tp, n, s))) return done(rc);
     cudaMemcpyAsync(cur, tp, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
     (edfa::count_launch(), k_tp_fill<<<g, 256, 0, s>>>(n, rowptr, col, (unsigned long long*)cur, tc));
-    (edfa::count_launch(), k_jp_prio<<<g, 256, 0, s>>>(n, prio));
-    cudaMemsetAsync(colour, 0xFF, (size_t)n * sizeof(int), s);
+    int* vcol = b > 1 ? bcolour : colour;  // colours of the vertices of the colouring
+    (edfa::count_launch(), k_jp_prio<<<g, 256, 0, s>>>(nb, prio));
+    cudaMemsetAsync(vcol, 0xFF, (size_t)nb * sizeof(int), s);
     cudaMemsetAsync(misc, 0, 2 * sizeof(unsigned long long), s);
     // rounds until a round leaves no vertex uncoloured; every round colours at
     // least the uncoloured vertex of highest priority, so n rounds always end it
-    (edfa::count_launch(), k_jp_iota<<<g, 256, 0, s>>>(n, wl));
+    (edfa::count_launch(), k_jp_iota<<<g, 256, 0, s>>>(nb, wl));
     {
-        const unsigned init[3] = {(unsigned)n, 0u, 0u};
+        const unsigned init[3] = {(unsigned)nb, 0u, 0u};
         cudaMemcpyAsync(wcnt, init, sizeof init, cudaMemcpyHostToDevice, s);
     }
     int64_t rounds = 0;
     int per_check = 8;
     unsigned left = 1;
-    const unsigned gr = grid_for(h, n, 128);
+    const unsigned gr = grid_for(h, nb, 128);
     // lanes per vertex from the mean number of entries of its rows in M and M^T
-    const bool wide = n > 0 && 2.0 * (double)nnz / (double)n > 48.0;
+    const bool wide = nb > 0 && 2.0 * (double)nnz / (double)nb > 48.0;
     while (left > 0) {
-        if (rounds > (int64_t)n + 1) return done(EDFA_ERR_TIMEOUT);
+        if (rounds > (int64_t)nb + 1) return done(EDFA_ERR_TIMEOUT);
         for (int k = 0; k < per_check; ++k, ++rounds) {
-            const int32_t* win = wl + (rounds & 1) * (int64_t)n;
-            int32_t* wout = wl + ((rounds + 1) & 1) * (int64_t)n;
-            (edfa::count_launch(), k_jp_round<<<gr, 128, 0, s>>>(rowptr, col, tp, tc, prio, colour, win, wout, wcnt,
-                                                                 (int)(rounds % 3), wide ? 32 : 8, (int*)(misc + 1)));
+            const int32_t* win = wl + (rounds & 1) * (int64_t)nb;
+            int32_t* wout = wl + ((rounds + 1) & 1) * (int64_t)nb;
+            (edfa::count_launch(), k_jp_round<<<gr, 128, 0, s>>>(rowptr, col, tp, tc, prio, vcol, win, wout, wcnt,
+                                                                 (int)(rounds % 3), wide ? 32 : 8, (int*)(misc + 1), b,
+                                                                 n));
         }
         if (per_check < 64) per_check *= 2;
         cudaMemcpyAsync(&left, wcnt + rounds % 3, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return done(EDFA_ERR_CUDA);
+    }
+    if (b > 1) {
+        cudaMemsetAsync(misc + 1, 0, sizeof(unsigned long long), s);
+        (edfa::count_launch(), k_block_row_colours<<<g, 256, 0, s>>>(n, b, bcolour, colour, (int*)(misc + 1)));
     }
     int maxcol = 0;
     cudaMemcpyAsync(&maxcol, (int*)(misc + 1), sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -428,6 +465,26 @@ int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr
             }
         if ((rc = dalloc_t(h, &o.tstart_dev, ts.size()))) return done(rc);
         cudaMemcpyAsync(o.tstart_dev, ts.data(), ts.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+        // blocks per block colour (every block has a row at position 0)
+        o.block = b;
+        o.nbcolours = 0;
+        o.bstart_dev = nullptr;
+        if (b == 4 || b == 8) {
+            const int nbc = (ncol + b - 1) / b;
+            const int bpw = 32 / b;  // blocks per warp of the block sweeps
+            std::vector<int64_t> bs((size_t)2 * (nbc + 1), 0);
+            for (int dir = 0; dir < 2; ++dir) {
+                int64_t* t = bs.data() + (size_t)dir * (nbc + 1);
+                for (int l = 0; l < nbc; ++l) {
+                    const int c = dir == 0 ? l : nbc - 1 - l;
+                    const int64_t nblk = (int64_t)o.cstart[(size_t)c * b + 1] - o.cstart[(size_t)c * b];
+                    t[l + 1] = t[l] + (nblk + bpw - 1) / bpw;  // tasks of 32 / b blocks
+                }
+            }
+            if ((rc = dalloc_t(h, &o.bstart_dev, bs.size()))) return done(rc);
+            cudaMemcpyAsync(o.bstart_dev, bs.data(), bs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+            o.nbcolours = nbc;
+        }
         if (cudaStreamSynchronize(s) != cudaSuccess) return done(EDFA_ERR_CUDA);
     }
     int coop = 0;
@@ -569,7 +626,7 @@ int order_stage2_symbolic(edfa_handle_s* h, cudaStream_t s)
 {
     int rc;
     const int32_t Ne = h->Ne, Nf = h->Nf;
-    if ((rc = order_colour(h, h->os, Ne, h->sf_ptr, h->sf_col, h->sf_nnz, s))) return rc;
+    if ((rc = order_colour(h, h->os, Ne, h->sf_ptr, h->sf_col, h->sf_nnz, s, h->opt.s_block))) return rc;
     if ((rc = order_matrix(h, h->so, Ne, h->sf_ptr, h->sf_col, h->sf_nnz, h->os.perm, h->os.iperm, s))) return rc;
     const int32_t* ap = h->oa.on ? h->oa.perm : nullptr;
     const int32_t* aip = h->oa.on ? h->oa.iperm : nullptr;

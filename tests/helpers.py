@@ -15,7 +15,8 @@ TOL_FP64 = 1e-10
 TOL_FP32 = 1e-5
 
 
-def gpu_handle(sysd, mode=None, form=0, variant=0, precision=0, thresh=None, dyn=None, qsets=None, ordering=0):
+def gpu_handle(sysd, mode=None, form=0, variant=0, precision=0, thresh=None, dyn=None, qsets=None, ordering=0,
+               s_block=0):
     import torch
 
     import paper_2009_13916_gb300 as P
@@ -29,7 +30,7 @@ def gpu_handle(sysd, mode=None, form=0, variant=0, precision=0, thresh=None, dyn
                        torch.as_tensor(qsets[1], dtype=torch.int32, device="cuda"))
     h = P.Edfa(A, B, C, D, sysd.Nf, sysd.Ne, qmode=mode,
                thresh=thresh if thresh is not None else sysd.extra.get("thresh", 0.05),
-               schur_form=form, variant=variant, precision=precision, ordering=ordering, **kw)
+               schur_form=form, variant=variant, precision=precision, ordering=ordering, s_block=s_block, **kw)
     return h
 
 

@@ -93,9 +93,11 @@ def test_inputs_identical_on_this_host():
     assert W.digest(W.config3(16, 12, 6)) == DIGEST_C3_SMALL
 
 
-def test_config3_full_size_multicolour_ordering():
+@pytest.mark.parametrize("s_block", [1, 4])
+def test_config3_full_size_multicolour_ordering(s_block):
     """The same workload with multicolour orderings of both inner factors
-    (ordering 2, the benchmark's configuration): colourings and orderings
+    (ordering 2; with the point colouring of S~ and with the block colouring
+    in blocks of 4 rows, the benchmark's configuration): colourings and orderings
     bit-exact, ordered factor patterns bit-exact and values within 1e-10 of
     the oracle's ILU(0) of the ordered matrices, one application within 1e-9,
     FGMRES converged to 1e-8 with the first cycle's residual estimates within
@@ -110,13 +112,13 @@ def test_config3_full_size_multicolour_ordering():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     sysd = W.config3()
-    h = gpu_handle(sysd, mode="thresh", thresh=0.05, ordering=2)
+    h = gpu_handle(sysd, mode="thresh", thresh=0.05, ordering=2, s_block=s_block)
     f = h.factors()
     qptr, qidx = O.qsets("thresh", sysd.A, sysd.B, sysd.C, 0.05)
     x, _ = O.local_solves(sysd.A, sysd.B, sysd.C, qptr, qidx)
     S = O.schur(0, sysd.A, sysd.C, sysd.D, qptr, qidx, x)
     _, aperm, nca = O.colour_order(sysd.A)
-    _, sperm, ncs = O.colour_order(S)
+    _, sperm, ncs = O.colour_order(S, s_block)
     assert np.array_equal(f["a_perm"].cpu().numpy(), aperm) and f["a_ncolours"] == nca
     assert np.array_equal(f["s_perm"].cpu().numpy(), sperm) and f["s_ncolours"] == ncs
     Pc = O.Prec(sysd.A, sysd.B, sysd.C, sysd.D, S=S, aperm=aperm, sperm=sperm)
@@ -134,14 +136,15 @@ def test_config3_full_size_multicolour_ordering():
     res = np.linalg.norm(sysd.full_scipy() @ xg.cpu().numpy() - sysd.b) / np.linalg.norm(sysd.b)
     assert info.converged and res <= 1.05e-8
     g = golden()
-    if g.get("inputs_sha256") == W.digest(sysd) and "iterations_ordering2" in g:
-        it_orc = int(g["iterations_ordering2"])
+    suffix = "_ordering2" + ("" if s_block == 1 else f"_block{s_block}")
+    if g.get("inputs_sha256") == W.digest(sysd) and "iterations" + suffix in g:
+        it_orc = int(g["iterations" + suffix])
     else:
         it_orc = O.fgmres(Pc, sysd.b, 50, 1e-8, 3000)["iters"]
     assert abs(info.iterations - it_orc) <= max(1, 0.005 * it_orc), (info.iterations, it_orc)
-    check_first_cycle(h, "_ordering2", sysd)
+    check_first_cycle(h, suffix, sysd)
     h.close()
-    h32 = gpu_handle(sysd, mode="thresh", thresh=0.05, precision=1, ordering=2)
+    h32 = gpu_handle(sysd, mode="thresh", thresh=0.05, precision=1, ordering=2, s_block=s_block)
     x32, info32 = h32.solve(b, restart=50, rtol=1e-8, maxit=3000)
     res32 = np.linalg.norm(sysd.full_scipy() @ x32.cpu().numpy() - sysd.b) / np.linalg.norm(sysd.b)
     assert info32.converged and res32 <= 1.05e-8

@@ -1,6 +1,6 @@
 """Multicolour orderings of the inner ILU(0) factorisations (edfa_options
-.ordering; 1 = S~, 2 = A~ and S~) on the GPU against the oracle with the same
-orderings: colourings and orderings bit-exact, the ordered factor patterns
+.ordering; 1 = S~, 2 = A~ and S~; edfa_options.s_block: block multicolour
+ordering of S~) on the GPU against the oracle with the same orderings: colourings and orderings bit-exact, the ordered factor patterns
 bit-exact, the factor values within 1e-10 (normwise per row), one application
 of the preconditioner within 1e-9 and FGMRES within one iteration of the
 oracle, converged at 1e-8.  The paper leaves the inner preconditioners and
@@ -82,6 +82,43 @@ def test_ordered_factors_apply_and_fgmres(case, ordering, variant):
     res = np.linalg.norm(sysd.full_scipy() @ x.cpu().numpy() - sysd.b) / np.linalg.norm(sysd.b)
     assert res <= 1.05e-8
     h.close()
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("s_block", [3, 4, 8, 16])
+def test_block_ordered_factors_apply_and_fgmres(case, s_block):
+    """Block multicolour ordering of S~ (blocks of s_block consecutive rows
+    coloured as units; A~ point-coloured): colours, ordering, factors,
+    application and FGMRES against the oracle with the same orderings; FP32-mixed
+    converges."""
+    torch = _torch()
+    make, mode = CASES[case]
+    sysd = make()
+    ref = O.edfa_pipeline(sysd, mode=mode, ordering=2, s_block=s_block, solve=True)
+    h = gpu_handle(sysd, mode=mode, ordering=2, s_block=s_block)
+    g = h.factors()
+    P = ref["prec"]
+    pat_s, lu_s = P.ordered_factor("s")
+    factor_check(g, "fs", "s_perm", ref["sperm"], pat_s, lu_s, sysd.Ne)
+    assert g["s_ncolours"] == O.colour_order(ref["S"], s_block)[2]
+    pat_a, lu_a = P.ordered_factor("a")
+    factor_check(g, "fa", "a_perm", ref["aperm"], pat_a, lu_a, sysd.Nf)
+    r = W.Stream(78).normal(sysd.n)
+    z_ref = P.apply(r)
+    z = h.apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    err = np.abs(z - z_ref).max() / np.abs(z_ref).max()
+    assert err <= 1e-9, f"apply error {err:.3e}"
+    b = torch.as_tensor(sysd.b, device="cuda")
+    x, info = h.solve(b, restart=50, rtol=1e-8, maxit=2000)
+    assert info.converged and abs(info.iterations - ref["iters"]) <= 1, (info.iterations, ref["iters"])
+    res = np.linalg.norm(sysd.full_scipy() @ x.cpu().numpy() - sysd.b) / np.linalg.norm(sysd.b)
+    assert res <= 1.05e-8
+    h.close()
+    h32 = gpu_handle(sysd, mode=mode, ordering=2, s_block=s_block, precision=1)
+    x32, info32 = h32.solve(b, restart=50, rtol=1e-8, maxit=2000)
+    res32 = np.linalg.norm(sysd.full_scipy() @ x32.cpu().numpy() - sysd.b) / np.linalg.norm(sysd.b)
+    assert info32.converged and res32 <= 1.05e-8
+    h32.close()
 
 
 @pytest.mark.parametrize("ordering", [1, 2])

@@ -636,6 +636,54 @@ def test_multicolour_ordering_is_the_jones_plassmann_colouring():
         assert lev.max() + 1 <= nc
 
 
+@pytest.mark.parametrize("block", [2, 3, 8])
+def test_block_multicolour_ordering(block):
+    """Blocks of `block` consecutive rows coloured as units: every block has the
+    smallest colour none of its higher-priority neighbouring blocks has (the
+    block graph and the greedy rule restated here with scipy), row r of block B
+    has colour c(B) * block + r - B * block, and rows are sorted by (colour,
+    index).  The rows of one colour are then independent, and the ILU(0) of
+    this ordering equals (to rounding) the ILU(0) of the ordering by (block
+    colour, block, position): the two orders agree on every coupled pair."""
+    import scipy.sparse as sp
+    for name, M in _ordering_cases():
+        n = M.shape[0]
+        colour, perm, nc = O.colour_order(M, block)
+        nb = (n + block - 1) // block
+        blk = np.arange(n) // block
+        Pm = sp.csr_matrix((np.ones(n), (blk, np.arange(n))), shape=(nb, n))
+        G = ((abs(M) + abs(M.T)) != 0).astype(np.int8)
+        Q = (Pm @ G @ Pm.T).tocsr()
+        pri = [_splitmix_finaliser(B) for B in range(nb)]
+        bcol = np.full(nb, -1)
+        for B in sorted(range(nb), key=lambda x: -pri[x]):
+            used = {int(bcol[U]) for U in Q.indices[Q.indptr[B]:Q.indptr[B + 1]] if U != B and bcol[U] >= 0}
+            c = 0
+            while c in used:
+                c += 1
+            bcol[B] = c
+        ref = bcol[blk] * block + np.arange(n) % block
+        assert np.array_equal(colour, ref), name
+        assert nc == colour.max() + 1
+        assert np.array_equal(perm, np.lexsort((np.arange(n), colour)))
+        Gc = G.tocsr()
+        rows = np.repeat(np.arange(n), np.diff(Gc.indptr))
+        off = rows != Gc.indices
+        assert not np.any(colour[rows[off]] == colour[Gc.indices[off]]), name
+        # the same preconditioner as the (block colour, block, position) order
+        p1 = np.lexsort((np.arange(n), blk, bcol[blk])).astype(np.int32)
+        M1 = O.permute(M, p1)
+        M2 = O.permute(M, perm)
+        lu1 = sp.csr_matrix((O.ilu0(M1), M1.col, M1.rowptr), shape=(n, n))
+        lu2 = sp.csr_matrix((O.ilu0(M2), M2.col, M2.rowptr), shape=(n, n))
+        back = np.empty(n, np.int64)
+        back[p1] = np.arange(n)
+        to1 = back[perm]  # position in order 1 of the k-th row of order 2
+        lu2_in1 = sp.csr_matrix(lu2)[np.argsort(to1)][:, np.argsort(to1)].toarray()
+        d1 = lu1.toarray()
+        assert np.abs(d1 - lu2_in1).max() <= 1e-12 * np.abs(d1).max(), name
+
+
 def test_permute_matches_scipy_fancy_indexing():
     for name, M in _ordering_cases():
         _, perm, _ = O.colour_order(M)
