@@ -200,10 +200,10 @@ struct Ordering {
     int64_t* tstart_dev = nullptr;
     // block multicolour ordering (block > 1): row r of block B has colour
     // c(B) block + r - B block, so block colour c spans colours c block ..
-    // c block + block - 1; bstart_dev = first task (32 / block blocks) of
-    // every block colour in processing order, [dir][nbcolours + 1] (dir 0
-    // forward, 1 backward), for the sweeps that take whole blocks per warp
-    // (block 4 or 8)
+    // c block + block - 1; bstart_dev = first task (32 / (block lanes)
+    // blocks) of every block colour in processing order, [dir][lanes][nbcolours
+    // + 1] (dir 0 forward, 1 backward; 1 or 2 lanes per row), for the sweeps
+    // that take whole blocks per warp (block 4 or 8)
     int32_t block = 1;
     int32_t nbcolours = 0;
     int64_t* bstart_dev = nullptr;

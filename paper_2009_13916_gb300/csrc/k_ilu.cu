@@ -1288,7 +1288,7 @@ k_mc_sweep_df(int ncol, const int64_t* __restrict__ tstart, const int32_t* __res
 // of 32 / NB blocks, dealt to the warps in processing order (block colours
 // ascending forward, descending backward); deadlock free like the dataflow
 // sweep.
-template <class T, class TB, class TO, int FWD, int NB>
+template <class T, class TB, class TO, int FWD, int NB, int LPR>
 __global__ void __launch_bounds__(kMcAllThreads, 2)
 k_mc_sweep_blk(int ncol, int nbc, const int64_t* __restrict__ bstart, const int32_t* __restrict__ cstart,
                const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const T* __restrict__ lu,
@@ -1297,15 +1297,17 @@ k_mc_sweep_blk(int ncol, int nbc, const int64_t* __restrict__ bstart, const int3
                const T* __restrict__ mval, const TO* __restrict__ mv, TO* out, const int32_t* __restrict__ sperm,
                double* scat, DevErr* err)
 {
-    constexpr int NBW = 32 / NB;  // blocks per warp
+    constexpr int RPW = 32 / LPR;  // rows per warp
+    constexpr int NBW = RPW / NB;  // blocks per warp
     constexpr int U = 4;
-    __shared__ T wsh[kMcAllThreads / 32][32][NB + 1];  // [warp][lane = row][column position]
+    __shared__ T wsh[kMcAllThreads / 32][RPW][NB + 1];  // [warp][row][column position]
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int q = lane / NB, kown = lane % NB;
+    const int g = lane / LPR, gl = lane % LPR;  // row of the warp, lane within the row
+    const int q = g / NB, kown = g % NB;
     const int64_t warp = ((int64_t)blockIdx.x * kMcAllThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kMcAllThreads) >> 5;
     const int64_t ntasks = bstart[nbc];
-    T* W = wsh[wl][lane];
+    T* W = wsh[wl][g];
     for (int64_t t = warp; t < ntasks; t += nwarps) {
         int lo = 0, hi = nbc - 1;  // block colour position: last l with bstart[l] <= t
         while (lo < hi) {
@@ -1316,8 +1318,11 @@ k_mc_sweep_blk(int ncol, int nbc, const int64_t* __restrict__ bstart, const int3
         const int64_t j = (t - bstart[lo]) * NBW + q;  // this lane's block within its block colour
         const int c0 = cb * NB, c1 = c0 + NB < ncol ? c0 + NB : ncol;
         const int64_t in_lo = cstart[c0], in_hi = cstart[c1];  // the block colour's rows
+        if (gl == 0) {
 #pragma unroll
-        for (int k = 0; k < NB; ++k) W[k] = T(0);
+            for (int k = 0; k < NB; ++k) W[k] = T(0);
+        }
+        __syncwarp();
         const int cp = c0 + kown;
         int64_t i = -1;
         bool live = false;
@@ -1333,12 +1338,12 @@ k_mc_sweep_blk(int ncol, int nbc, const int64_t* __restrict__ bstart, const int3
             if (!FWD) di = dinv[i];
             if (mptr) {
                 const int64_t mb = mptr[i], me = mptr[i + 1];
-                for (int64_t p0 = mb; p0 < me; p0 += U) {
+                for (int64_t p0 = mb; p0 < me; p0 += U * LPR) {
                     int cc[U];
                     T w[U];
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        const int64_t p = p0 + u;
+                        const int64_t p = p0 + gl + u * LPR;
                         cc[u] = p < me ? mcol[p] : -1;
                         w[u] = p < me ? mval[p] : T(0);
                     }
@@ -1347,12 +1352,12 @@ k_mc_sweep_blk(int ncol, int nbc, const int64_t* __restrict__ bstart, const int3
                         if (cc[u] >= 0) acc = fma(w[u], (T)mv[cc[u]], acc);
                 }
             }
-            for (int64_t p0 = rlo; p0 < rhi; p0 += U) {
+            for (int64_t p0 = rlo; p0 < rhi; p0 += U * LPR) {
                 int cc[U];
                 T w[U], x[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int64_t p = p0 + u;
+                    const int64_t p = p0 + gl + u * LPR;
                     cc[u] = p < rhi ? col[p] : -1;
                     w[u] = p < rhi ? lu[p] : T(0);
                 }
@@ -1392,6 +1397,9 @@ k_mc_sweep_blk(int ncol, int nbc, const int64_t* __restrict__ bstart, const int3
                     if (cc[u] >= 0) acc = fma(w[u], x[u], acc);
             }
         }
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        __syncwarp();
         // the blocks' triangular systems, position after position (backward:
         // in the scaled form x = d bi - d acc, d = 1/U_ii, with the internal
         // coefficients scaled by d once, so a position costs one add and one
@@ -1399,24 +1407,28 @@ k_mc_sweep_blk(int ncol, int nbc, const int64_t* __restrict__ bstart, const int3
         if (!FWD) {
             bi *= di;
             acc *= di;
+            if (gl == 0) {
 #pragma unroll
-            for (int k = 0; k < NB; ++k) W[k] *= di;
+                for (int k = 0; k < NB; ++k) W[k] *= di;
+            }
+            __syncwarp();
         }
         T xv = T(0);
 #pragma unroll
         for (int s2 = 0; s2 < NB; ++s2) {
             const int k = FWD ? s2 : NB - 1 - s2;
             const T r = bi - acc;
-            const int src = q * NB + k;
+            const int src = (q * NB + k) * LPR;
             const T xk = __shfl_sync(0xffffffffu, r, src);
             const int kl = __shfl_sync(0xffffffffu, live ? 1 : 0, src);
             if (kown == k) xv = r;
             if (kl) acc = fma(W[k], xk, acc);
         }
-        if (live) {
+        if (live && gl == 0) {
             if (sperm) scat[sperm[i]] = (double)xv;
             st_relaxed(out + i, (TO)xv);
         }
+        __syncwarp();
     }
 }
 
@@ -1475,12 +1487,12 @@ static void mc_launch(edfa_handle_s* h, const Factor& f, const Ordering& o, cons
 }
 
 // one cooperative launch of the block sweep; false when that is not possible
-template <class T, class TB, class TO, int FWD, int NB>
+template <class T, class TB, class TO, int FWD, int NB, int LPR>
 static bool blk_launch(edfa_handle_s* h, const Factor& f, const Ordering& o, const T* lu, const T* dinv,
                        const TB* base, const int32_t* bperm, const int64_t* mptr, const int32_t* mcol, const T* mval,
                        const TO* mv, TO* out, const int32_t* sperm, double* scat, bool prefilled, cudaStream_t s)
 {
-    auto fb = k_mc_sweep_blk<T, TB, TO, FWD, NB>;
+    auto fb = k_mc_sweep_blk<T, TB, TO, FWD, NB, LPR>;
     static thread_local int per_dev = -1, per_sm = 0;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1489,7 +1501,7 @@ static bool blk_launch(edfa_handle_s* h, const Factor& f, const Ordering& o, con
         per_dev = dev;
     }
     if (per_sm < 1) return false;
-    const int64_t* bs = o.bstart_dev + (int64_t)(FWD ? 0 : 1) * (o.nbcolours + 1);
+    const int64_t* bs = o.bstart_dev + ((int64_t)(FWD ? 0 : 1) * 2 + (LPR == 1 ? 0 : 1)) * (o.nbcolours + 1);
     if (!prefilled) cudaMemsetAsync(out, 0xFF, (size_t)f.n * sizeof(TO), s);
     int ncol = o.ncolours, nbc = o.nbcolours;
     void* args[] = {(void*)&ncol, (void*)&nbc, (void*)&bs, (void*)&o.cstart_dev, (void*)&f.rowptr, (void*)&f.col,
@@ -1519,10 +1531,22 @@ static int mc_sweep(edfa_handle_s* h, const Factor& f, const Ordering& o, const 
     if (o.bstart_dev && h->coop_ok) {
         // block multicolour ordering: one block per warp
         bool ok = false;
-        if (o.block == 4) ok = blk_launch<T, TB, TO, FWD, 4>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out,
-                                                             sperm, scat, prefilled, s);
-        else if (o.block == 8) ok = blk_launch<T, TB, TO, FWD, 8>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv,
-                                                                  out, sperm, scat, prefilled, s);
+        // one lane per row for short rows, two for longer ones; in FP64 the
+        // block solve's instructions weigh more (they serve half the blocks
+        // with two lanes per row), so the rows must be longer to gain
+        const bool two = avg > (sizeof(T) == 8 ? 12.0 : 8.0);
+        if (o.block == 4 && two)
+            ok = blk_launch<T, TB, TO, FWD, 4, 2>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm,
+                                                  scat, prefilled, s);
+        else if (o.block == 4)
+            ok = blk_launch<T, TB, TO, FWD, 4, 1>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm,
+                                                  scat, prefilled, s);
+        else if (o.block == 8 && two)
+            ok = blk_launch<T, TB, TO, FWD, 8, 2>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm,
+                                                  scat, prefilled, s);
+        else if (o.block == 8)
+            ok = blk_launch<T, TB, TO, FWD, 8, 1>(h, f, o, lu, dinv, base, bperm, mptr, mcol, mval, mv, out, sperm,
+                                                  scat, prefilled, s);
         if (ok) {
             if (pe) cudaEventRecord(pe[1], s);
             return cudaGetLastError() == cudaSuccess ? EDFA_OK : EDFA_ERR_CUDA;

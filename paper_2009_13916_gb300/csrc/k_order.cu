@@ -471,16 +471,17 @@ int order_colour(edfa_handle_s* h, Ordering& o, int32_t n, const int64_t* rowptr
         o.bstart_dev = nullptr;
         if (b == 4 || b == 8) {
             const int nbc = (ncol + b - 1) / b;
-            const int bpw = 32 / b;  // blocks per warp of the block sweeps
-            std::vector<int64_t> bs((size_t)2 * (nbc + 1), 0);
-            for (int dir = 0; dir < 2; ++dir) {
-                int64_t* t = bs.data() + (size_t)dir * (nbc + 1);
-                for (int l = 0; l < nbc; ++l) {
-                    const int c = dir == 0 ? l : nbc - 1 - l;
-                    const int64_t nblk = (int64_t)o.cstart[(size_t)c * b + 1] - o.cstart[(size_t)c * b];
-                    t[l + 1] = t[l] + (nblk + bpw - 1) / bpw;  // tasks of 32 / b blocks
+            std::vector<int64_t> bs((size_t)2 * 2 * (nbc + 1), 0);
+            for (int dir = 0; dir < 2; ++dir)
+                for (int li = 0; li < 2; ++li) {
+                    const int bpw = 32 / (b << li);  // blocks per warp with 1 or 2 lanes per row
+                    int64_t* t = bs.data() + ((size_t)dir * 2 + li) * (nbc + 1);
+                    for (int l = 0; l < nbc; ++l) {
+                        const int c = dir == 0 ? l : nbc - 1 - l;
+                        const int64_t nblk = (int64_t)o.cstart[(size_t)c * b + 1] - o.cstart[(size_t)c * b];
+                        t[l + 1] = t[l] + (nblk + bpw - 1) / bpw;  // tasks of bpw blocks
+                    }
                 }
-            }
             if ((rc = dalloc_t(h, &o.bstart_dev, bs.size()))) return done(rc);
             cudaMemcpyAsync(o.bstart_dev, bs.data(), bs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
             o.nbcolours = nbc;
