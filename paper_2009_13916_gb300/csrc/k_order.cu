@@ -14,6 +14,10 @@
 // are all coloured takes its colour; a colour, once written, is final, so
 // whatever a round reads (a final colour or "not yet") the result is that
 // fixed point, whatever the timing.  Ordering: rows sorted by (colour, index).
+// Block variant (edfa_options.s_block = b > 1): the vertices are the blocks of
+// b consecutive rows (priority of block + 1; an edge where M + M^T couples two
+// blocks), and row r of block B takes colour c(B) b + r - B b, so the rows of
+// one colour stay independent and a block keeps its rows' natural order.
 // The ordered matrices P M Q^T are built once per pattern with a map to the
 // original entries, so new values only need a gather.
 #include "internal.cuh"
