@@ -621,7 +621,8 @@ def reference_arm(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": describe(args.workload, args.n, args.nz), "N_e": sysd.Ne, "N_f": sysd.Nf,
                    "solver": "oracle (plain C, FP64)",
-                   "ilu0_ordering": ["natural", "multicolour S~", "multicolour A~ and S~"][args.ordering]},
+                   "ilu0_ordering": ["natural", "multicolour S~", "multicolour A~ and S~"][args.ordering],
+                   "s_block": args.s_block if args.ordering >= 1 else None},
         "iterations": iters,
         "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
                          "sample": f"whole setup + one 50-iteration FGMRES cycle per step, solve extrapolated to "
