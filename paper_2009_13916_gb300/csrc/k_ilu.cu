@@ -1529,7 +1529,9 @@ static int mc_sweep(edfa_handle_s* h, const Factor& f, const Ordering& o, const 
     const double avg = ((double)(f.nnz - f.n) / 2.0 + (mptr ? (double)mnnz : 0.0)) / (double)f.n;
     cudaEvent_t* pe = prof_begin(h, (&f == &h->fs ? 2 : 0) + (FWD ? 0 : 1), s);
     if (o.bstart_dev && h->coop_ok) {
-        // block multicolour ordering: one block per warp
+        // block multicolour ordering: whole blocks per warp, one or two lanes
+        // per row (with long rows this still beats the dataflow sweep over
+        // block size times the colours: 64^3 full tensor, rows of ~60)
         bool ok = false;
         // one lane per row for short rows, two for longer ones; in FP64 the
         // block solve's instructions weigh more (they serve half the blocks

@@ -73,7 +73,10 @@ k_block_spmv(int32_t Nf, int32_t Ne, Csr<double> A, Csr<double> B, Csr<double> C
         spmv_rows<LC>(Nf, Ne, ((int64_t)blockIdx.x - nbf) * kKT + threadIdx.x, C, x, D, xp, y);
 }
 
-static int lanes_for(double avg) { return avg <= 6.0 ? 1 : avg <= 12.0 ? 2 : avg <= 32.0 ? 4 : 8; }
+// lanes per row from the mean row length: a row shared by more lanes costs
+// log2(lanes) FP64 adds to reduce, and on this part an FP64 instruction costs
+// its share of the pipe whatever the number of active lanes
+static int lanes_for(double avg) { return avg <= 6.0 ? 1 : avg <= 16.0 ? 2 : avg <= 40.0 ? 4 : 8; }
 
 template <int LF, int LC>
 static void spmv_launch(edfa_handle_s* h, const Csr<double>* M, const double* x, double* y, cudaStream_t s)
