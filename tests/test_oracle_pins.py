@@ -717,6 +717,33 @@ def test_ordered_apply_is_the_natural_apply_of_the_permuted_system():
         assert np.abs(z - zr).max() <= 1e-12 * np.abs(zr).max(), variant
 
 
+def test_fgmres_on_the_permuted_system_is_the_same_iteration():
+    """FGMRES with the ordered preconditioner on the natural system and FGMRES on
+    the permuted system (blocks and right-hand side permuted, the natural-order
+    preconditioner of the permuted blocks) take the same iterations: inner
+    products and norms are permutation invariant, so the residual estimates
+    agree to rounding and the solutions are permutations of each other."""
+    s = W.config3(16, 12, 6)
+    q = O.qsets("thresh", s.A, s.B, s.C, 0.05)
+    x, _ = O.local_solves(s.A, s.B, s.C, *q)
+    S = O.schur(0, s.A, s.C, s.D, *q, x)
+    _, pa, _ = O.colour_order(s.A)
+    _, ps, _ = O.colour_order(S, 4)
+    r1 = O.fgmres(O.Prec(s.A, s.B, s.C, s.D, S=S, aperm=pa, sperm=ps), s.b, 50, 1e-8, 2000)
+    A, B, C_, D, Ss = (M.to_scipy().tocsr() for M in (s.A, s.B, s.C, s.D, S))
+    Pq = O.Prec(A[pa][:, pa], B[pa][:, ps], C_[ps][:, pa], D[ps][:, ps], S=Ss[ps][:, ps])
+    bq = np.concatenate([s.b[:s.Nf][pa], s.b[s.Nf:][ps]])
+    r2 = O.fgmres(Pq, bq, 50, 1e-8, 2000)
+    assert r1["converged"] and r2["converged"]
+    assert abs(r1["iters"] - r2["iters"]) <= 1
+    k = min(len(r1["hist"]), len(r2["hist"]), 51)
+    assert np.allclose(r1["hist"][:k], r2["hist"][:k], rtol=1e-8, atol=0)
+    xb = np.empty_like(r2["x"])
+    xb[pa] = r2["x"][:s.Nf]
+    xb[s.Nf + ps] = r2["x"][s.Nf:]
+    assert np.linalg.norm(xb - r1["x"]) <= 1e-6 * np.linalg.norm(r1["x"])
+
+
 def test_ordered_preconditioner_fgmres_converges():
     for sysd, mode in ((W.config2(10), "nbr"), (W.config3(16, 12, 6), "thresh")):
         for ordering in (1, 2):
