@@ -71,9 +71,14 @@ def parse():
                     help="skip the FMA-rate probe (profiling runs: keeps its launches out of the launch list)")
     ap.add_argument("--ordering", type=int, default=2, choices=[0, 1, 2],
                     help="inner ILU(0) ordering of the timed path: 0 natural, 1 multicolour S~, 2 A~ and S~")
-    ap.add_argument("--s-block", type=int, default=4,
-                    help="with an ordering of S~: rows per block of its block multicolour ordering (1: point colouring)")
-    return ap.parse_args()
+    ap.add_argument("--s-block", type=int, default=None,
+                    help="with an ordering of S~: rows per block of its block multicolour ordering (1: point "
+                         "colouring; default 4 on the channelised workload, whose S~ rows are short, 1 on the "
+                         "full-tensor one)")
+    args = ap.parse_args()
+    if args.s_block is None:
+        args.s_block = 4 if args.workload == "c3" else 1
+    return args
 
 
 def make_workload(name, n=64, nz=64):
