@@ -1271,21 +1271,21 @@ k_mc_sweep_df(int ncol, const int64_t* __restrict__ tstart, const int32_t* __res
     }
 }
 
-// Sweeps of a block multicolour ordering (blocks of NB rows, 32 / NB blocks per
-// warp, one lane per row).  Block j of block colour c holds the rows
+// Sweeps of a block multicolour ordering (blocks of NB rows, LPR lanes per row,
+// 32 / (NB LPR) blocks per warp).  Block j of block colour c holds the rows
 // i_k = cstart[c NB + k] + j at positions k = 0 .. NB - 1 (some may be absent
 // in the one short block).  Blocks of one block colour are not coupled, so a
 // row's entries split into external ones (other block colours: earlier in the
 // sweep, polled like the dataflow sweep's) and internal ones (the rows of its
-// own block, whose columns lie in the colour range of its block colour).  Every
-// lane walks its row, sums the external part and the coupling term and keeps
+// own block, whose columns lie in the colour range of its block colour).  The
+// lanes of a row walk it, sum the external part and the coupling term and keep
 // the internal coefficients in shared memory by position; then the warp solves
 // its blocks' small triangular systems in registers, position after position
 // (ascending forward, descending backward): the rows of that position are
 // final, are broadcast within their block, and the later rows add their term.
 // The internal chains cost shuffles, not memory round trips, and every warp-wide
 // FP64 instruction of that phase serves all the warp's blocks.  Tasks = groups
-// of 32 / NB blocks, dealt to the warps in processing order (block colours
+// of 32 / (NB LPR) blocks, dealt to the warps in processing order (block colours
 // ascending forward, descending backward); deadlock free like the dataflow
 // sweep.
 template <class T, class TB, class TO, int FWD, int NB, int LPR>
