@@ -34,6 +34,7 @@ def full_tensor(n, seed=11):
 CASES = {
     "full": (lambda: full_tensor((12, 10, 8)), "nbr"),
     "c3_small": (lambda: W.config3(24, 20, 6), "thresh"),
+    "c3_ragged": (lambda: W.config3(13, 11, 5), "thresh"),  # 715 cells: a short last block
     "dome8": (lambda: W.dome(8), "nbr"),
     "c5_small": (lambda: W.config5(10), "crow"),
 }
